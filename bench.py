@@ -1,0 +1,393 @@
+"""Throughput benchmark: leapfrog site-steps/s of the HS-field HMC.
+
+Workload (the paper's 2D periodic square lattice, Sec. 4): L = 256 and
+L = 1024, nearest-neighbour J = 1, h = 0, beta swept over 16 values in
+[0.38, 0.50] with 256 independent chains per beta (4096 chains per L),
+C = 4 beta + 0.1, N_md = 20 leapfrog steps, eps tuned per beta for ~80%
+acceptance during an untimed equilibration phase.  FP32 state and force, FP64
+action, dH and Metropolis test.
+
+One step = one full trajectory (momenta, N_md leapfrog steps, action, dH,
+accept, measurement) of every chain of both lattices.  A site-step is one psi
+component of one chain advanced one leapfrog step.
+
+Reported next to it: the plain FP64 form (one chain per launch, unfused) on
+the same GPU, the dominant kernel's HBM roofline fraction, an end-to-end
+number through the public C ABI with host buffers, and the FP64 CPU oracle on
+the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "leapfrog site-steps/s chosen vs plain form, same GPU; %roofline; serve p50/p99"
+UNIT = "site-steps/s"
+LS = (256, 1024)
+N_MD = 20
+EPS0 = {256: 0.04, 1024: 0.02, 64: 0.07, 128: 0.05}
+TARGET_ACC = 0.80
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chains-per-beta", type=int, default=256)
+    ap.add_argument("--L", type=str, default="256,1024")
+    ap.add_argument("--tune-rounds", type=int, default=6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1912_03278_gb300", "csrc", "fused_lattice.cu")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        rec = d.get(kernel, {}).get(workload)
+        if rec and rec.get("source_sha") == h:
+            return rec.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- reference ----
+def cpu_sample_rate(n_threads, L=1024, n_traj=1, seed=5):
+    """FP64 oracle, one chain per thread, one trajectory each: site-steps/s."""
+    import oracle
+    betas = workloads.beta_sweep()
+    b = betas[np.arange(n_threads) % len(betas)]
+    model = oracle.Model(dim=2, L=(L, L), beta=float(b[0]))
+    t0 = time.perf_counter()
+    oracle.run_chains(model, n_threads, oracle.FORM_FP32, seed, eps=EPS0.get(L, 0.02), n_md=N_MD,
+                      n=n_traj, beta=b, C=workloads.lattice_C(b, 2), n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    return n_threads * L * L * N_MD * n_traj / dt, dt
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_sample_rate(cores, L=256)
+    t0 = time.perf_counter()
+    work = 0.0
+    for _ in range(args.steps):
+        r, dt = cpu_sample_rate(cores, L=1024)
+        work += r * dt
+    el = time.perf_counter() - t0
+    val = work / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2D periodic square lattice, L=1024 sample of the L=256/1024 "
+                               "16-beta x 256-chain batch, N_md=20", "parallelism": "host threads"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d chains (one per core) of L=1024, 1 trajectory each per step"
+                                   % cores},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm ----
+def tune_eps(sims, betas_per_chain, rounds, seed):
+    """Robbins-Monro on log eps per beta group toward TARGET_ACC (equilibration only)."""
+    import paper_1912_03278_gb300 as pkg
+    ub = np.unique(betas_per_chain)
+    for L, sim in sims.items():
+        eps = np.full(len(betas_per_chain), EPS0.get(L, 0.02))
+        for r in range(rounds):
+            sim.trajectories(1, seed + 1000 + r)
+            acc = sim.records()[:, 2]
+            for b in ub:
+                sel = betas_per_chain == b
+                a = acc[sel].mean()
+                eps[sel] *= math.exp(0.8 * (a - TARGET_ACC))
+            sim.set_eps(eps)
+        sim._eps = eps.copy()
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1912_03278_gb300 as pkg
+    pkg.build()
+    stream = torch.cuda.Stream()
+    Ls = tuple(int(x) for x in args.L.split(","))
+    betas = np.repeat(workloads.beta_sweep(), args.chains_per_beta)
+    n_chains = len(betas)
+    C = workloads.lattice_C(betas, 2)
+    sims = {}
+    for L in Ls:
+        sims[L] = pkg.IsingHMC(dim=2, L=(L, L), beta=betas, C=C, eps=EPS0.get(L, 0.02), n_md=N_MD,
+                               n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
+                               stream=stream.cuda_stream)
+    seed = 1234 + 7919 * rank
+    tune_eps(sims, betas, args.tune_rounds, seed)
+    for L in Ls:
+        sims[L].reset_sums()
+
+    def step(k):
+        for L in Ls:
+            sims[L].trajectories(1, seed)
+
+    for k in range(args.warmup):
+        step(k)
+    for s in sims.values():
+        s.sync()
+    big = max(Ls)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = sum(s.launches for s in sims.values())
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            for L in Ls:
+                if L == big:
+                    ev[k][0].record(stream)
+                sims[L].trajectories(1, seed)
+                if L == big:
+                    ev[k][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    launches = sum(s.launches for s in sims.values()) - launches0
+    big_ms = [a.elapsed_time(b) for a, b in ev]
+    obs = {L: sims[L].observables() for L in Ls}
+    if ws > 1:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    site_steps = sum(L * L for L in Ls) * n_chains * N_MD * args.steps * ws
+    value = site_steps / elapsed
+
+    # dominant kernel: one launch = one trajectory of all chains of the largest lattice
+    alg_bytes = 16.0 * N_MD * big * big * n_chains
+    dur = float(np.mean(big_ms)) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / dur / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": traffic_record("fused_lattice_kernel", "2d_L%d_B%d" % (big, n_chains)),
+                "kernel": "fused_lattice_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                "ms_per_launch": dur * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "2D periodic square lattice L=%s, 16 betas in [0.38,0.50] x %d "
+                                   "chains, J=1, h=0, C=4beta+0.1, N_md=%d, eps tuned to ~80%% "
+                                   "acceptance; FP32 force and state, FP64 action/dH/accept"
+                                   % ("+".join(map(str, Ls)), args.chains_per_beta, N_MD),
+                       "global_batch": n_chains * len(Ls) * ws, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (state %.1f GB)"
+                             % (16 * sum(L * L for L in Ls) * n_chains / 1e9)},
+            "acceptance": {str(L): obs[L]["acceptance"] for L in Ls},
+            "roofline": roofline,
+            "gpu_launches": int(launches)}
+
+    if rank == 0:
+        line["clocks"] = clk.summary()
+        if not args.no_plain:
+            line["plain_form"] = plain_rate(pkg, big, betas, C, sims[big], stream)
+            line["speedup_vs_plain"] = value / ws / line["plain_form"]["value"]
+        if not args.no_e2e:
+            line["e2e"] = e2e_rate(pkg, sims, Ls, n_chains, seed, stream)
+        if not args.no_cpu:
+            import oracle
+            oracle.build()
+            cores = os.cpu_count() or 1
+            r, dt = cpu_sample_rate(cores, L=big)
+            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": "%d chains of L=%d (one per core), 1 trajectory, "
+                                              "N_md=%d, %.1f s" % (cores, big, N_MD, dt)}
+        print(json.dumps(line), flush=True)
+    for s in sims.values():
+        s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def plain_rate(pkg, L, betas, C, tuned, stream):
+    """Plain FP64 form (one chain per launch, unfused kernels) on a sample of chains
+    with the tuned step sizes."""
+    import torch
+    idx = np.array([0, len(betas) // 2, len(betas) - 1])
+    eps = tuned._eps[idx]
+    sim = pkg.IsingHMC(dim=2, L=(L, L), beta=betas[idx], C=C[idx], eps=eps, n_md=N_MD,
+                       n_chains=len(idx), precision=pkg.ISING_PREC_PLAIN_FP64,
+                       stream=stream.cuda_stream)
+    try:
+        sim.trajectories(1, 77)
+        sim.sync()
+        n = 2
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        l0 = sim.launches
+        t0.record(stream)
+        sim.trajectories(n, 77)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        dt = t0.elapsed_time(t1) / 1e3
+        acc = sim.observables()["acceptance"]
+        return {"value": len(idx) * L * L * N_MD * n / dt, "unit": UNIT, "chains": len(idx),
+                "L": L, "trajectories": n, "launches": sim.launches - l0, "dtype": "f64",
+                "acceptance_sample": acc}
+    finally:
+        sim.close()
+
+
+def e2e_rate(pkg, sims, Ls, n_chains, seed, stream, steps=3):
+    """Through the public C ABI with host buffers: each step uploads every chain's
+    configuration from pinned host memory, runs one trajectory and reads the
+    observables back."""
+    import torch
+    host = {}
+    for L in Ls:
+        host[L] = torch.empty(n_chains * L * L, dtype=torch.float32, pin_memory=True)
+        pkg.ising_hmc_get_state_native(sims[L].h, host[L].data_ptr())
+    h2d = sum(host[L].numel() * 4 for L in Ls)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        for L in Ls:
+            traj = sims[L].traj_index
+            pkg.ising_hmc_set_state_native(sims[L].h, host[L].data_ptr(), traj)
+            sims[L].trajectories(1, seed)
+            sims[L].observables()
+    dt = time.perf_counter() - t0
+    site_steps = sum(L * L for L in Ls) * n_chains * N_MD * steps
+    # observables() copies the per-chain state records (sums, record, scalars) back
+    d2h = len(Ls) * n_chains * 8 * (5 + 10 + 8 + 1)
+    return {"value": site_steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * ising_hmc.h -- C ABI of the GB300 (sm_103a) Hybrid Monte Carlo library for
+ * the Ising model in its Hubbard-Stratonovich (HS) auxiliary-field form
+ * (Ostmeyer, Berkowitz, Luu, Petschlies, Pittler, "The Ising Model with Hybrid
+ * Monte Carlo", arXiv:1912.03278).
+ *
+ * The method (Sec. 2, Eqs. absorb_beta .. phi_psi_substitution; Sec. 3):
+ * with A = beta*J*K + C*1 positive definite (K the connectivity, C the shift of
+ * Sec. 2) and h' = beta*h, the spins are summed out and the field psi carries
+ *     S(psi) = 1/2 psi.A.psi - sum_i log 2cosh((A psi)_i + h'_i).
+ * A trajectory draws momenta p ~ N(0,1) (Sec. 3, Eq. momentum distribution),
+ * integrates dpsi/dt = p, dp/dt = F(psi) = A (tanh(A psi + h') - psi) with a
+ * symmetric symplectic integrator for one unit of MD time, and accepts the end
+ * point with probability min(1, exp(-dH)), H = 1/2 p.p + S(psi) (Sec. 3).
+ *
+ * Parametrisation.  The paper writes Kt = K + C_p*1 and phi = sqrt(J') Kt psi_p
+ * - h' with J' = beta*J.  This library uses phi = A psi, i.e. C = J'*C_p,
+ * psi = psi_p/sqrt(J') - A^-1 h', eps = eps_p/sqrt(J'); the two generate the
+ * same Markov chain (equal dH, equal accept decisions).
+ *
+ * Conventions for every entry point:
+ *  - No call aborts, prints or throws.  Each returns an ising_status; on error
+ *    ising_hmc_last_error(handle) describes it (handle-less errors of
+ *    ising_hmc_create are reported by ising_hmc_last_create_error()).
+ *  - Host pointers are only read during the call (inputs are copied); the
+ *    caller keeps ownership of everything it passes.  The handle owns all the
+ *    device memory it allocates and frees it in ising_hmc_destroy.
+ *  - Work is queued on the handle's CUDA stream (the caller's stream if one was
+ *    given).  Calls that return host data synchronise that stream.
+ *  - Arrays of chain state are chain-major: element [c*N + i] is site i of
+ *    chain c; lattice site i = x + L0*(y + L1*z).
+ *  - Philox4x32-10 (Salmon et al., SC'11) supplies every random number from a
+ *    counter (index, trajectory, chain, purpose) and the key (seed lo, seed hi),
+ *    so results depend only on (seed, chain, trajectory index), never on the
+ *    launch shape or on how trajectories are split across calls.
+ */
+#ifndef ISING_HMC_H
+#define ISING_HMC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISING_OK = 0,
+    ISING_EINVAL = 1,   /* invalid argument or configuration                 */
+    ISING_ENOTPD = 2,   /* C too small: A not positive definite (Sec. 2)     */
+    ISING_ENOMEM = 3,   /* device or host allocation failed                  */
+    ISING_ECUDA = 4,    /* a CUDA runtime call failed                        */
+    ISING_ETIMEOUT = 5, /* a bounded device-side wait gave up                */
+    ISING_EBUSY = 6     /* resource in use (e.g. a group already running)    */
+} ising_status;
+
+enum { ISING_KIND_LATTICE = 0, ISING_KIND_DENSE = 1 };
+
+enum {
+    ISING_PREC_PLAIN_FP64 = 0, /* FP64 state and force, one chain per launch, unfused */
+    ISING_PREC_FP32 = 1,       /* FP32 state and force, fused, FP64-accurate action  */
+    ISING_PREC_BF16 = 2,       /* dense only: BF16 tensor-core force, FP32 state      */
+    ISING_PREC_FP8 = 3         /* dense only: FP8 e4m3 force with per-row scales      */
+};
+
+enum { ISING_INTEGRATOR_LEAPFROG = 0, ISING_INTEGRATOR_OMELYAN = 1 };
+
+typedef struct {
+    int kind;             /* ISING_KIND_LATTICE or ISING_KIND_DENSE                    */
+    int dim;              /* lattice: 1..3                                              */
+    int L[3];             /* lattice extents, each >= 3 (L = 2 would double the bonds)  */
+    int64_t n_sites;      /* dense: N (ignored for lattices)                            */
+    const double *J;      /* dense: host N*N row-major, symmetric, J_ii = 0; copied     */
+    double Jnn;           /* lattice nearest-neighbour coupling J (Sec. 2)              */
+    const double *h;      /* host per-site field h_i (N values) or NULL; copied         */
+    double h0;            /* uniform field when h == NULL                               */
+    double beta, C, eps;  /* defaults for every chain; C in the units of A above        */
+    const double *beta_chain; /* optional host arrays of n_chains values overriding    */
+    const double *C_chain;    /*   beta, C, eps and h0 per chain (NULL = use the scalar) */
+    const double *eps_chain;
+    const double *h0_chain;
+    int n_md;             /* MD steps per trajectory (leapfrog: n_md drifts)            */
+    int n_chains;         /* independent Markov chains                                  */
+    int n_therm;          /* trajectories with index < n_therm are not measured (Sec. 3) */
+    int precision;        /* ISING_PREC_*                                               */
+    int integrator;       /* ISING_INTEGRATOR_*                                         */
+    int flip_every;       /* >0: global sign-flip proposal after every k-th trajectory  */
+    void *stream;         /* cudaStream_t to queue work on, or NULL for an own stream   */
+} ising_hmc_config;
+
+/* Per-chain sums, chain-major, ISING_NSUMS doubles per chain, in this order. */
+enum {
+    ISING_SUM_NMEAS = 0, ISING_SUM_NACC, ISING_SUM_M, ISING_SUM_M2, ISING_SUM_E, ISING_SUM_E2,
+    ISING_SUM_ABSM, ISING_SUM_ABSM2, ISING_SUM_DH, ISING_SUM_EXPMDH, ISING_NSUMS
+};
+
+/* Record of a chain's most recent trajectory, ISING_NREC doubles per chain. */
+enum {
+    ISING_REC_DH = 0, ISING_REC_LOGU, ISING_REC_ACCEPTED, ISING_REC_K0, ISING_REC_S0,
+    ISING_REC_K1, ISING_REC_S1, ISING_REC_FLIPPED, ISING_NREC
+};
+
+typedef struct {
+    double m, m_err;          /* <m>, Sec. 4 (E[s|psi] estimator, mean tanh(A psi + h'))  */
+    double abs_m, abs_m_err;  /* <|m|> from one conditional spin draw per configuration   */
+    double E, E_err;          /* <beta*eps> = C/2 - <a.t>/(2N) - <h'.t>/N (Sec. 4)        */
+    double acceptance;
+    double mean_dH;
+    double mean_exp_mdH, exp_mdH_err; /* Creutz: <exp(-dH)> = 1                            */
+    int64_t n_traj;           /* trajectories run so far (per chain)                      */
+    int64_t n_meas;           /* measured trajectories, summed over chains                */
+} ising_obs;
+
+typedef struct ising_hmc ising_hmc_t;
+
+/* Create a simulation: validates the model, allocates device state for
+ * n_chains chains, uploads couplings and fields, and sets psi = 0 with its
+ * action S(0) computed on the device.
+ * Validation (Sec. 2, spectrum bound and shift): lattice requires
+ * C > beta*|J|*2*dim for every chain; dense requires C > beta*|lambda_min(J)|,
+ * with lambda_min from a Lanczos estimate on the host (ENOTPD otherwise).
+ * Errors: EINVAL (bad sizes/kinds/precision for the kind), ENOTPD, ENOMEM, ECUDA. */
+ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out);
+
+/* Run n trajectories on every chain (Sec. 3 algorithm: momentum refresh, MD,
+ * Metropolis test, optional sign flip, measurement after n_therm).  The
+ * trajectory counter persists: trajectories(a, s) then trajectories(b, s)
+ * equals trajectories(a + b, s) bit for bit.  Asynchronous: returns once the
+ * work is queued.  Errors: EINVAL (n < 0), ECUDA. */
+ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed);
+
+/* Observables averaged over all chains of the handle (Sec. 4 estimators);
+ * errors are the standard error of the per-chain means when n_chains > 1, and
+ * the naive sigma/sqrt(n) of the single chain otherwise (no autocorrelation
+ * correction).  Synchronises.  Errors: ECUDA, ETIMEOUT. */
+ising_status ising_hmc_observables(ising_hmc_t *h, ising_obs *out);
+
+/* Per-chain sums (ISING_NSUMS doubles per chain) into out[n_chains*ISING_NSUMS]. */
+ising_status ising_hmc_chain_sums(ising_hmc_t *h, double *out);
+
+/* Per-chain record of the most recent trajectory (ISING_NREC doubles per chain). */
+ising_status ising_hmc_last_records(ising_hmc_t *h, double *out);
+
+/* Zero the per-chain sums (e.g. after an equilibration phase). */
+ising_status ising_hmc_reset_sums(ising_hmc_t *h);
+
+enum { ISING_STATE_PSI = 0, ISING_STATE_PSI_PROPOSAL = 1, ISING_STATE_P_END = 2 };
+
+/* Copy chain state to host out[n_chains*N] as FP64: the current configuration,
+ * the most recent proposal (end of the last trajectory, accepted or not), or
+ * the momenta at the end of the last trajectory.  Synchronises. */
+ising_status ising_hmc_get_state(ising_hmc_t *h, int which, double *out);
+
+/* Same for chains [chain0, chain0+count) only, into host out[count*N]. */
+ising_status ising_hmc_get_chains(ising_hmc_t *h, int which, int chain0, int count, double *out);
+
+/* Set every chain's configuration from host psi[n_chains*N] (rounded to the
+ * state precision), set the index of the next trajectory, and recompute S and
+ * the observables of the new configurations on the device.  Checkpoint /
+ * resume: get_state + the trajectory index + the sums restore a run exactly. */
+ising_status ising_hmc_set_state(ising_hmc_t *h, const double *psi, int64_t next_traj);
+
+/* Same from a buffer in the state precision (FP64 for the plain form, FP32
+ * otherwise), chain-major, in device memory or in (preferably pinned) host
+ * memory: the copy uses unified addressing.  Bytes read:
+ * n_chains*N*ising_hmc_state_elem_bytes(h). */
+ising_status ising_hmc_set_state_native(ising_hmc_t *h, const void *psi, int64_t next_traj);
+
+/* Copy the current configurations, in the state precision, to a device or
+ * host buffer of n_chains*N elements.  Synchronises. */
+ising_status ising_hmc_get_state_native(ising_hmc_t *h, void *out);
+
+/* Bytes per state element: 8 (plain FP64 form) or 4. */
+int ising_hmc_state_elem_bytes(const ising_hmc_t *h);
+
+/* Restore per-chain sums (checkpoint/resume), host in[n_chains*ISING_NSUMS]. */
+ising_status ising_hmc_set_sums(ising_hmc_t *h, const double *in);
+
+/* The momenta the library draws for trajectory traj (Sec. 3, momentum
+ * refresh), computed by the same device code as the trajectories, for chains
+ * [chain0, chain0+count) into host out[count*N] as FP64.  Overwrites the
+ * stored end-of-trajectory momenta.  For checks on the GPU's own MD end points. */
+ising_status ising_hmc_momenta(ising_hmc_t *h, uint64_t seed, int64_t traj, int chain0, int count,
+                               double *out);
+
+/* Replace the per-chain step sizes (host eps[n_chains]); used by the step-size
+ * tuner during equilibration only. */
+ising_status ising_hmc_set_eps(ising_hmc_t *h, const double *eps);
+
+/* Index of the next trajectory. */
+int64_t ising_hmc_traj_index(const ising_hmc_t *h);
+
+/* Number of sites per chain and number of chains. */
+int64_t ising_hmc_n_sites(const ising_hmc_t *h);
+int ising_hmc_n_chains(const ising_hmc_t *h);
+
+/* Bytes of device memory the handle holds. */
+int64_t ising_hmc_device_bytes(const ising_hmc_t *h);
+
+/* Device memory a configuration would need, without creating it (admission). */
+int64_t ising_hmc_estimate_bytes(const ising_hmc_config *cfg);
+
+/* Kernel launches queued by this handle so far (for launch accounting). */
+int64_t ising_hmc_launch_count(const ising_hmc_t *h);
+
+/* Synchronise the handle's stream; ETIMEOUT if a device wait gave up. */
+ising_status ising_hmc_sync(ising_hmc_t *h);
+
+void ising_hmc_destroy(ising_hmc_t *h);
+const char *ising_hmc_last_error(const ising_hmc_t *h);
+const char *ising_hmc_last_create_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -340,13 +340,15 @@ void or_measure(const or_model *m, const double *psi, int form, uint64_t seed, u
 /* ------------------------------------------------------------------------ */
 /* The HMC algorithm (Sec. 3).                                               */
 /* ------------------------------------------------------------------------ */
-/* psi starts at zero; its observables use the spin draw of trajectory
- * index 0xffffffff. */
+/* psi starts at zero (or the caller's psi); the observables of that start
+ * configuration use the spin draw of trajectory index 0xffffffff under key 0,
+ * so they do not depend on the run's seed. */
 void or_chain_init(const or_model *m, or_chain *c, int form, uint64_t seed, uint32_t chain) {
     int64_t N = or_num_sites(m);
     if (!c->psi) c->psi = (double *)calloc((size_t)N, sizeof(double));
     c->S = or_action(m, c->psi, NULL, NULL);
-    or_measure(m, c->psi, form, seed, chain, 0xffffffffu, &c->obs);
+    (void)seed;
+    or_measure(m, c->psi, form, 0, chain, 0xffffffffu, &c->obs);
     c->traj = 0;
     c->n_meas = c->n_acc = c->n_traj = 0;
     c->sum_m = c->sum_m2 = c->sum_E = c->sum_E2 = c->sum_am = c->sum_am2 = 0;

@@ -1,0 +1,366 @@
+"""ctypes binding of the C ABI in include/ising_hmc.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all work runs
+in the CUDA library.  The library is loaded from this package's ``lib/``
+directory; if it is missing the import of a function raises, there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_uint64, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libising_hmc.so")
+
+# status codes
+ISING_OK, ISING_EINVAL, ISING_ENOTPD, ISING_ENOMEM, ISING_ECUDA, ISING_ETIMEOUT, ISING_EBUSY = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOTPD", "ENOMEM", "ECUDA", "ETIMEOUT", "EBUSY"]
+ISING_KIND_LATTICE, ISING_KIND_DENSE = 0, 1
+ISING_PREC_PLAIN_FP64, ISING_PREC_FP32, ISING_PREC_BF16, ISING_PREC_FP8 = 0, 1, 2, 3
+ISING_INTEGRATOR_LEAPFROG, ISING_INTEGRATOR_OMELYAN = 0, 1
+ISING_STATE_PSI, ISING_STATE_PSI_PROPOSAL, ISING_STATE_P_END = 0, 1, 2
+SUM_NAMES = ["n_meas", "n_acc", "sum_m", "sum_m2", "sum_E", "sum_E2", "sum_am", "sum_am2",
+             "sum_dH", "sum_expmdH"]
+ISING_NSUMS = len(SUM_NAMES)
+REC_NAMES = ["dH", "logu", "accepted", "K0", "S0", "K1", "S1", "flipped"]
+ISING_NREC = len(REC_NAMES)
+
+
+class IsingError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+class ising_hmc_config(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("dim", c_int), ("L", c_int * 3), ("n_sites", c_int64),
+                ("J", c_void_p), ("Jnn", c_double), ("h", c_void_p), ("h0", c_double),
+                ("beta", c_double), ("C", c_double), ("eps", c_double),
+                ("beta_chain", c_void_p), ("C_chain", c_void_p), ("eps_chain", c_void_p),
+                ("h0_chain", c_void_p), ("n_md", c_int), ("n_chains", c_int), ("n_therm", c_int),
+                ("precision", c_int), ("integrator", c_int), ("flip_every", c_int),
+                ("stream", c_void_p)]
+
+
+class ising_obs(ctypes.Structure):
+    _fields_ = [("m", c_double), ("m_err", c_double), ("abs_m", c_double),
+                ("abs_m_err", c_double), ("E", c_double), ("E_err", c_double),
+                ("acceptance", c_double), ("mean_dH", c_double), ("mean_exp_mdH", c_double),
+                ("exp_mdH_err", c_double), ("n_traj", c_int64), ("n_meas", c_int64)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError("libising_hmc.so not built (%s); run paper_1912_03278_gb300.build" % p)
+    lib = ctypes.CDLL(p)
+    P = c_void_p
+    sig = {
+        "ising_hmc_create": (c_int, [P, P]),
+        "ising_hmc_trajectories": (c_int, [P, c_int64, c_uint64]),
+        "ising_hmc_observables": (c_int, [P, P]),
+        "ising_hmc_chain_sums": (c_int, [P, P]),
+        "ising_hmc_last_records": (c_int, [P, P]),
+        "ising_hmc_reset_sums": (c_int, [P]),
+        "ising_hmc_get_state": (c_int, [P, c_int, P]),
+        "ising_hmc_set_state": (c_int, [P, P, c_int64]),
+        "ising_hmc_set_state_native": (c_int, [P, P, c_int64]),
+        "ising_hmc_get_state_native": (c_int, [P, P]),
+        "ising_hmc_state_elem_bytes": (c_int, [P]),
+        "ising_hmc_set_sums": (c_int, [P, P]),
+        "ising_hmc_momenta": (c_int, [P, c_uint64, c_int64, c_int, c_int, P]),
+        "ising_hmc_get_chains": (c_int, [P, c_int, c_int, c_int, P]),
+        "ising_hmc_set_eps": (c_int, [P, P]),
+        "ising_hmc_traj_index": (c_int64, [P]),
+        "ising_hmc_n_sites": (c_int64, [P]),
+        "ising_hmc_n_chains": (c_int, [P]),
+        "ising_hmc_device_bytes": (c_int64, [P]),
+        "ising_hmc_estimate_bytes": (c_int64, [P]),
+        "ising_hmc_launch_count": (c_int64, [P]),
+        "ising_hmc_sync": (c_int, [P]),
+        "ising_hmc_destroy": (None, [P]),
+        "ising_hmc_last_error": (c_char_p, [P]),
+        "ising_hmc_last_create_error": (c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(h, st):
+    if st != ISING_OK:
+        lib = load()
+        msg = lib.ising_hmc_last_error(h) if h else lib.ising_hmc_last_create_error()
+        raise IsingError(st, (msg or b"").decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_config(kind="lattice", dim=2, L=(4, 4), n_sites=0, J=None, Jnn=1.0, h=0.0, beta=0.44,
+                C=None, eps=0.1, n_md=10, n_chains=1, n_therm=0, precision=ISING_PREC_FP32,
+                integrator=ISING_INTEGRATOR_LEAPFROG, flip_every=0, stream=None):
+    """Build an ising_hmc_config; array arguments may be per chain (beta, C, eps)
+    or per site (h).  Returns (config, keepalive) -- keep both alive until the
+    create call returns."""
+    cfg = ising_hmc_config()
+    keep = []
+    cfg.kind = ISING_KIND_DENSE if kind == "dense" else ISING_KIND_LATTICE
+    cfg.dim = dim
+    Lt = tuple(L) + (1,) * (3 - len(L))
+    for i in range(3):
+        cfg.L[i] = int(Lt[i])
+    if kind == "dense":
+        Jm = _f64(J)
+        keep.append(Jm)
+        cfg.J = Jm.ctypes.data
+        cfg.n_sites = Jm.shape[0]
+    cfg.Jnn = Jnn
+    if np.isscalar(h):
+        cfg.h = None
+        cfg.h0 = float(h)
+    else:
+        hv = _f64(h)
+        keep.append(hv)
+        cfg.h = hv.ctypes.data
+        cfg.h0 = 0.0
+
+    def per_chain(name, v):
+        if v is None:
+            return
+        if np.isscalar(v):
+            setattr(cfg, name, float(v))
+        else:
+            arr = _f64(v)
+            if arr.shape != (n_chains,):
+                raise ValueError("%s must have one value per chain" % name)
+            keep.append(arr)
+            setattr(cfg, name + "_chain", arr.ctypes.data)
+            setattr(cfg, name, float(arr[0]))
+
+    per_chain("beta", beta)
+    if C is None:
+        bmax = float(np.max(beta))
+        if kind == "dense":
+            C = bmax * abs(np.linalg.eigvalsh(_f64(J))[0]) + 0.1
+        else:
+            C = np.asarray(beta) * abs(Jnn) * 2 * dim + 0.1
+            if np.ndim(C) == 0:
+                C = float(C)
+    per_chain("C", C)
+    per_chain("eps", eps)
+    cfg.n_md = n_md
+    cfg.n_chains = n_chains
+    cfg.n_therm = n_therm
+    cfg.precision = precision
+    cfg.integrator = integrator
+    cfg.flip_every = flip_every
+    cfg.stream = stream
+    return cfg, keep
+
+
+def ising_hmc_create(cfg: ising_hmc_config) -> int:
+    lib = load()
+    out = c_void_p()
+    _check(None, lib.ising_hmc_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def ising_hmc_trajectories(h, n, seed):
+    _check(h, load().ising_hmc_trajectories(h, int(n), int(seed)))
+
+
+def ising_hmc_observables(h) -> dict:
+    o = ising_obs()
+    _check(h, load().ising_hmc_observables(h, ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in ising_obs._fields_}
+
+
+def ising_hmc_chain_sums(h) -> np.ndarray:
+    n = load().ising_hmc_n_chains(h)
+    out = np.zeros((n, ISING_NSUMS))
+    _check(h, load().ising_hmc_chain_sums(h, out.ctypes.data))
+    return out
+
+
+def ising_hmc_last_records(h) -> np.ndarray:
+    n = load().ising_hmc_n_chains(h)
+    out = np.zeros((n, ISING_NREC))
+    _check(h, load().ising_hmc_last_records(h, out.ctypes.data))
+    return out
+
+
+def ising_hmc_reset_sums(h):
+    _check(h, load().ising_hmc_reset_sums(h))
+
+
+def ising_hmc_set_sums(h, sums):
+    s = _f64(sums)
+    _check(h, load().ising_hmc_set_sums(h, s.ctypes.data))
+
+
+def ising_hmc_get_state(h, which=ISING_STATE_PSI) -> np.ndarray:
+    lib = load()
+    n, N = lib.ising_hmc_n_chains(h), lib.ising_hmc_n_sites(h)
+    out = np.zeros((n, N))
+    _check(h, lib.ising_hmc_get_state(h, which, out.ctypes.data))
+    return out
+
+
+def ising_hmc_set_state(h, psi, next_traj):
+    lib = load()
+    n, N = lib.ising_hmc_n_chains(h), lib.ising_hmc_n_sites(h)
+    arr = _f64(psi).reshape(n, N)
+    _check(h, lib.ising_hmc_set_state(h, arr.ctypes.data, int(next_traj)))
+
+
+def ising_hmc_set_state_native(h, ptr, next_traj):
+    """psi as a raw pointer (int) to n_chains*N elements in the state precision,
+    device or host memory."""
+    _check(h, load().ising_hmc_set_state_native(h, c_void_p(ptr), int(next_traj)))
+
+
+def ising_hmc_get_state_native(h, ptr):
+    _check(h, load().ising_hmc_get_state_native(h, c_void_p(ptr)))
+
+
+def ising_hmc_state_elem_bytes(h) -> int:
+    return load().ising_hmc_state_elem_bytes(h)
+
+
+def ising_hmc_momenta(h, seed, traj, chain0=0, count=None) -> np.ndarray:
+    lib = load()
+    n, N = lib.ising_hmc_n_chains(h), lib.ising_hmc_n_sites(h)
+    count = n - chain0 if count is None else count
+    out = np.zeros((count, N))
+    _check(h, lib.ising_hmc_momenta(h, int(seed), int(traj), chain0, count, out.ctypes.data))
+    return out
+
+
+def ising_hmc_get_chains(h, which, chain0, count) -> np.ndarray:
+    lib = load()
+    N = lib.ising_hmc_n_sites(h)
+    out = np.zeros((count, N))
+    _check(h, lib.ising_hmc_get_chains(h, which, chain0, count, out.ctypes.data))
+    return out
+
+
+def ising_hmc_set_eps(h, eps):
+    e = _f64(eps)
+    _check(h, load().ising_hmc_set_eps(h, e.ctypes.data))
+
+
+def ising_hmc_traj_index(h) -> int:
+    return load().ising_hmc_traj_index(h)
+
+
+def ising_hmc_device_bytes(h) -> int:
+    return load().ising_hmc_device_bytes(h)
+
+
+def ising_hmc_estimate_bytes(cfg) -> int:
+    return load().ising_hmc_estimate_bytes(ctypes.byref(cfg))
+
+
+def ising_hmc_launch_count(h) -> int:
+    return load().ising_hmc_launch_count(h)
+
+
+def ising_hmc_sync(h):
+    _check(h, load().ising_hmc_sync(h))
+
+
+def ising_hmc_destroy(h):
+    if h:
+        load().ising_hmc_destroy(h)
+
+
+def ising_hmc_last_error(h) -> str:
+    return (load().ising_hmc_last_error(h) or b"").decode()
+
+
+class IsingHMC:
+    """Owning wrapper around a handle: IsingHMC(**make_config kwargs)."""
+
+    def __init__(self, **kw):
+        cfg, keep = make_config(**kw)
+        self.h = ising_hmc_create(cfg)
+        self.kw = kw
+        del keep
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def close(self):
+        if self.h:
+            ising_hmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def trajectories(self, n, seed):
+        ising_hmc_trajectories(self.h, n, seed)
+
+    def observables(self):
+        return ising_hmc_observables(self.h)
+
+    def chain_sums(self):
+        return ising_hmc_chain_sums(self.h)
+
+    def records(self):
+        return ising_hmc_last_records(self.h)
+
+    def state(self, which=ISING_STATE_PSI):
+        return ising_hmc_get_state(self.h, which)
+
+    def set_state(self, psi, next_traj):
+        ising_hmc_set_state(self.h, psi, next_traj)
+
+    def momenta(self, seed, traj, chain0=0, count=None):
+        return ising_hmc_momenta(self.h, seed, traj, chain0, count)
+
+    def chains(self, which, chain0, count):
+        return ising_hmc_get_chains(self.h, which, chain0, count)
+
+    def set_eps(self, eps):
+        ising_hmc_set_eps(self.h, eps)
+
+    def reset_sums(self):
+        ising_hmc_reset_sums(self.h)
+
+    def sync(self):
+        ising_hmc_sync(self.h)
+
+    @property
+    def traj_index(self):
+        return ising_hmc_traj_index(self.h)
+
+    @property
+    def launches(self):
+        return ising_hmc_launch_count(self.h)
+
+    @property
+    def device_bytes(self):
+        return ising_hmc_device_bytes(self.h)

@@ -1,0 +1,103 @@
+// internal.h -- structures shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ising_hmc.h"
+
+namespace ihmc {
+
+// Per-chain parameters (device).  hp = beta*h0 is the uniform part of h'.
+struct ChainParams {
+    double beta, bJ, C, eps, hp;
+    float betaf, bJf, Cf, epsf, hpf;
+    float pad[3];
+};
+
+// Per-chain Markov-chain state (device).
+struct ChainState {
+    double S;                   // action of the current configuration
+    double obs[4];              // m, E, |m| (spin draw), |mean t| of the current configuration
+    double sums[ISING_NSUMS];   // running sums over measured trajectories
+    double rec[ISING_NREC];     // record of the most recent trajectory
+    int start;                  // state-buffer index holding the current configuration
+    int prop;                   // state-buffer index holding the most recent proposal
+};
+
+// Integrator schedule: force evaluation j kicks p by kick[j]*eps and, unless it
+// is the last one, drifts psi by drift[j]*eps.
+constexpr int MAX_PASSES = 129;
+struct Schedule {
+    int n_pass;
+    double kick[MAX_PASSES];
+    double drift[MAX_PASSES];
+};
+
+// Geometry of a periodic lattice as streamed plane by plane.  The plane is the
+// set of sites with equal slowest coordinate: a row (2D), an xy-slab (3D), the
+// whole ring (1D).
+struct Geometry {
+    int dim;
+    int X, Y, Z;        // extents; unused ones are 1
+    int P;              // sites per plane
+    int nplanes;        // planes per chain
+    int64_t N;          // sites per chain
+};
+
+// Arguments of the fused FP32 lattice trajectory kernel.
+struct FusedArgs {
+    float *psi[3];           // three state buffers, chain-major
+    float *p;                // momenta, chain-major
+    const float *h32;        // per-site h_i (not scaled by beta), or null
+    const double *h64;
+    const ChainParams *params;
+    ChainState *state;
+    Geometry g;
+    uint64_t seed;
+    uint32_t traj0;          // index of the first trajectory of this launch
+    int n_traj;              // trajectories per chain in this launch
+    int n_therm;             // trajectories with index < n_therm are not measured
+    int flip_every;
+    int mode;                // 0 trajectories, 1 evaluate current state, 2 write momenta
+    int chain0;              // first chain of this launch
+    int n_chains;
+    int *err;
+};
+
+enum { MODE_TRAJ = 0, MODE_EVAL = 1, MODE_MOMENTA = 2 };
+
+// Trajectory index of the spin draw that measures a configuration set from
+// outside (creation, set_state); drawn under key 0.
+constexpr uint32_t TRAJ_INIT_INDEX = 0xffffffffu;
+
+// Error bits written by kernels into the handle's error word.
+enum { KERR_TIMEOUT = 1, KERR_BOUNDS = 2 };
+
+cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
+                                 int depth, cudaStream_t s);
+int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec);
+int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
+
+// Plain FP64 form: one chain per launch, unfused kernels.
+struct PlainArgs {
+    double *psi_cur, *psi, *p, *a, *u, *F;   // per-chain views (N doubles each)
+    double *partials;                         // scratch, per-chain view
+    const double *h64;                        // per-site h_i or null
+    const double *J;                          // dense couplings or null
+    const ChainParams *params;                // this chain's parameters
+    ChainState *state;                        // this chain's state
+    int *flag;                                // this chain's accept/flip flag
+    Geometry g;
+    int kind;
+    uint32_t chain;
+};
+
+cudaError_t plain_trajectory(const PlainArgs &a, const Schedule &sched, uint64_t seed,
+                             uint32_t traj, int measure, int flip, cudaStream_t s,
+                             int64_t *launches);
+cudaError_t plain_eval(const PlainArgs &a, cudaStream_t s, int64_t *launches);
+cudaError_t plain_momenta(const PlainArgs &a, uint64_t seed, uint32_t traj, cudaStream_t s,
+                          int64_t *launches);
+int plain_partial_blocks(int64_t N);
+
+}  // namespace ihmc

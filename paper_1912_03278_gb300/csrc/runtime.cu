@@ -1,0 +1,774 @@
+// runtime.cu -- host runtime of the C ABI declared in include/ising_hmc.h.
+// Owns the device state of a simulation handle and queues the kernels of the
+// HMC algorithm (Sec. 3) on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ihmc;
+
+struct ising_hmc {
+    // configuration
+    int kind = 0, dim = 0, L[3] = {1, 1, 1};
+    int64_t N = 0;
+    int n_chains = 0, n_md = 0, n_therm = 0, prec = 0, integrator = 0, flip_every = 0;
+    Geometry g{};
+    Schedule sched{};
+    std::vector<ChainParams> params;
+    bool has_h = false;
+    // device
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *psi[3] = {nullptr, nullptr, nullptr};  // FP32 lattice: 3 buffers; plain: psi_cur, psi
+    void *p = nullptr;
+    double *plain_a = nullptr, *plain_u = nullptr, *plain_F = nullptr, *partials = nullptr;
+    int *flags = nullptr;
+    ChainParams *d_params = nullptr;
+    ChainState *d_state = nullptr;
+    float *d_h32 = nullptr;
+    double *d_h64 = nullptr;
+    double *d_J = nullptr;
+    int *d_err = nullptr;
+    // launch shape of the fused kernel
+    int threads = 0, depth = 0;
+    // counters
+    int64_t traj = 0;
+    int64_t launches = 0;
+    int64_t bytes = 0;
+    char err[512] = {0};
+};
+
+static thread_local char g_create_err[512];
+
+static ising_status fail(ising_hmc *h, ising_status st, const char *fmt, ...) {
+    char *buf = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_OR_FAIL(h, call)                                                           \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail((h), ISING_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+static bool is_fp32_lattice(const ising_hmc *h) {
+    return h->kind == ISING_KIND_LATTICE && h->prec == ISING_PREC_FP32;
+}
+
+static size_t state_elem(const ising_hmc *h) {
+    return h->prec == ISING_PREC_PLAIN_FP64 ? sizeof(double) : sizeof(float);
+}
+
+// Integrator schedules (Sec. 3: symmetric symplectic integrators).
+static void make_schedule(int integrator, int n_md, Schedule &s) {
+    if (integrator == ISING_INTEGRATOR_OMELYAN) {
+        // Omelyan-Mryglod-Folk second-order minimum-norm scheme, kicks merged
+        // between consecutive steps: lam, (1-2lam), 2lam, ..., (1-2lam), lam.
+        const double lam = 0.1931833275037836;
+        s.n_pass = 2 * n_md + 1;
+        for (int j = 0; j < s.n_pass; ++j) {
+            if (j == 0 || j == s.n_pass - 1) s.kick[j] = lam;
+            else s.kick[j] = (j & 1) ? (1.0 - 2.0 * lam) : 2.0 * lam;
+            s.drift[j] = (j == s.n_pass - 1) ? 0.0 : 0.5;
+        }
+    } else {
+        // kick-drift-kick leapfrog with n_md drifts
+        s.n_pass = n_md + 1;
+        for (int j = 0; j < s.n_pass; ++j) {
+            s.kick[j] = (j == 0 || j == s.n_pass - 1) ? 0.5 : 1.0;
+            s.drift[j] = (j == s.n_pass - 1) ? 0.0 : 1.0;
+        }
+    }
+}
+
+// Smallest eigenvalue of a dense symmetric matrix by Lanczos with full
+// reorthogonalisation (Lanczos 1950), then Sturm-sequence bisection on the
+// tridiagonal matrix.  Used only to validate the shift C (Sec. 2).
+static double lanczos_lambda_min(const double *J, int64_t N, int steps) {
+    steps = (int)std::min<int64_t>(steps, N);
+    std::vector<double> Q((size_t)steps * N), w(N), alpha(steps), beta(steps);
+    // deterministic start vector
+    double nrm = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        Q[i] = 1.0 + 0.37 * std::sin(0.71 * (double)i + 0.3);
+        nrm += Q[i] * Q[i];
+    }
+    nrm = std::sqrt(nrm);
+    for (int64_t i = 0; i < N; ++i) Q[i] /= nrm;
+    int k = 0;
+    for (; k < steps; ++k) {
+        const double *q = &Q[(size_t)k * N];
+        for (int64_t i = 0; i < N; ++i) {
+            double s = 0;
+            const double *row = J + i * N;
+            for (int64_t j = 0; j < N; ++j) s += row[j] * q[j];
+            w[i] = s;
+        }
+        double a = 0;
+        for (int64_t i = 0; i < N; ++i) a += w[i] * q[i];
+        alpha[k] = a;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int j = 0; j <= k; ++j) {
+                const double *qj = &Q[(size_t)j * N];
+                double d = 0;
+                for (int64_t i = 0; i < N; ++i) d += w[i] * qj[i];
+                for (int64_t i = 0; i < N; ++i) w[i] -= d * qj[i];
+            }
+        }
+        double b = 0;
+        for (int64_t i = 0; i < N; ++i) b += w[i] * w[i];
+        b = std::sqrt(b);
+        beta[k] = b;
+        if (k + 1 >= steps || b < 1e-12) {
+            ++k;
+            break;
+        }
+        double *qn = &Q[(size_t)(k + 1) * N];
+        for (int64_t i = 0; i < N; ++i) qn[i] = w[i] / b;
+    }
+    const int m = k;
+    // bisection for the smallest eigenvalue of T (alpha, beta[0..m-2])
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::fabs(beta[i - 1]) : 0) + (i + 1 < m ? std::fabs(beta[i]) : 0);
+        lo = std::min(lo, alpha[i] - r);
+        hi = std::max(hi, alpha[i] + r);
+    }
+    auto count_below = [&](double x) {
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < m; ++i) {
+            const double b2 = i > 0 ? beta[i - 1] * beta[i - 1] : 0.0;
+            d = alpha[i] - x - (i > 0 ? b2 / d : 0.0);
+            if (d == 0.0) d = 1e-300;
+            if (d < 0) ++c;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_below(mid) >= 1) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static void free_all(ising_hmc *h) {
+    for (auto &b : h->psi) {
+        if (b) cudaFree(b);
+        b = nullptr;
+    }
+    void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
+                    h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_err};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    h->p = nullptr;
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+}
+
+static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_h) {
+    const int64_t C = n_chains;
+    int64_t b = 0;
+    if (prec == ISING_PREC_PLAIN_FP64) {
+        b += 6 * C * N * (int64_t)sizeof(double);
+        b += C * 7 * (int64_t)plain_partial_blocks(N) * (int64_t)sizeof(double);
+    } else {
+        b += 4 * C * N * (int64_t)sizeof(float);
+    }
+    b += C * (int64_t)(sizeof(ChainParams) + sizeof(ChainState) + 2 * sizeof(int));
+    if (has_h) b += N * (int64_t)(sizeof(float) + sizeof(double));
+    if (kind == ISING_KIND_DENSE) b += N * N * (int64_t)sizeof(double);
+    return b;
+}
+
+template <typename T>
+static ising_status dalloc(ising_hmc *h, T **ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)ptr, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, ISING_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->bytes += (int64_t)bytes;
+    return ISING_OK;
+}
+
+static PlainArgs plain_args(ising_hmc *h, int c) {
+    PlainArgs a{};
+    const int64_t N = h->N;
+    a.psi_cur = (double *)h->psi[0] + (int64_t)c * N;
+    a.psi = (double *)h->psi[1] + (int64_t)c * N;
+    a.p = (double *)h->p + (int64_t)c * N;
+    a.a = h->plain_a + (int64_t)c * N;
+    a.u = h->plain_u + (int64_t)c * N;
+    a.F = h->plain_F + (int64_t)c * N;
+    a.partials = h->partials + (int64_t)c * 7 * plain_partial_blocks(N);
+    a.h64 = h->has_h ? h->d_h64 : nullptr;
+    a.J = h->d_J;
+    a.params = h->d_params + c;
+    a.state = h->d_state + c;
+    a.flag = h->flags + 2 * c;
+    a.g = h->g;
+    a.kind = h->kind;
+    a.chain = (uint32_t)c;
+    return a;
+}
+
+static FusedArgs fused_args(ising_hmc *h) {
+    FusedArgs a{};
+    for (int i = 0; i < 3; ++i) a.psi[i] = (float *)h->psi[i];
+    a.p = (float *)h->p;
+    a.h32 = h->has_h ? h->d_h32 : nullptr;
+    a.h64 = h->has_h ? h->d_h64 : nullptr;
+    a.params = h->d_params;
+    a.state = h->d_state;
+    a.g = h->g;
+    a.n_therm = h->n_therm;
+    a.flip_every = h->flip_every;
+    a.chain0 = 0;
+    a.n_chains = h->n_chains;
+    a.err = h->d_err;
+    return a;
+}
+
+// Recompute S and the observables of the current configurations.
+static ising_status eval_current(ising_hmc *h) {
+    if (is_fp32_lattice(h)) {
+        FusedArgs a = fused_args(h);
+        a.mode = MODE_EVAL;
+        a.seed = 0;
+        a.traj0 = TRAJ_INIT_INDEX;
+        a.n_traj = 0;
+        CUDA_OR_FAIL(h, launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream));
+        h->launches += 1;
+    } else {
+        for (int c = 0; c < h->n_chains; ++c) {
+            PlainArgs a = plain_args(h, c);
+            CUDA_OR_FAIL(h, plain_eval(a, h->stream, &h->launches));
+        }
+    }
+    return ISING_OK;
+}
+
+static ising_status upload_params(ising_hmc *h) {
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_params, h->params.data(),
+                                    sizeof(ChainParams) * h->n_chains, cudaMemcpyHostToDevice,
+                                    h->stream));
+    return cudaStreamSynchronize(h->stream) == cudaSuccess
+               ? ISING_OK
+               : fail(h, ISING_ECUDA, "parameter upload failed");
+}
+
+extern "C" {
+
+const char *ising_hmc_last_create_error(void) { return g_create_err; }
+
+int64_t ising_hmc_estimate_bytes(const ising_hmc_config *cfg) {
+    if (!cfg) return -1;
+    int64_t N = 0;
+    if (cfg->kind == ISING_KIND_DENSE) N = cfg->n_sites;
+    else {
+        N = 1;
+        for (int d = 0; d < cfg->dim && d < 3; ++d) N *= cfg->L[d];
+    }
+    return plan_bytes(cfg->kind, cfg->precision, N, cfg->n_chains, cfg->h != nullptr);
+}
+
+ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
+    g_create_err[0] = 0;
+    if (!cfg || !out) return fail(nullptr, ISING_EINVAL, "null config or output pointer");
+    *out = nullptr;
+    ising_hmc *h = new (std::nothrow) ising_hmc();
+    if (!h) return fail(nullptr, ISING_ENOMEM, "host allocation failed");
+    auto bail = [&](ising_status st) {
+        std::snprintf(g_create_err, sizeof g_create_err, "%s", h->err);
+        free_all(h);
+        delete h;
+        return st;
+    };
+    h->kind = cfg->kind;
+    h->prec = cfg->precision;
+    h->n_chains = cfg->n_chains;
+    h->n_md = cfg->n_md;
+    h->n_therm = cfg->n_therm;
+    h->integrator = cfg->integrator;
+    h->flip_every = cfg->flip_every;
+    if (h->n_chains < 1) return bail(fail(h, ISING_EINVAL, "n_chains must be >= 1"));
+    if (h->n_md < 1) return bail(fail(h, ISING_EINVAL, "n_md must be >= 1"));
+    if (h->integrator != ISING_INTEGRATOR_LEAPFROG && h->integrator != ISING_INTEGRATOR_OMELYAN)
+        return bail(fail(h, ISING_EINVAL, "unknown integrator %d", h->integrator));
+    const int passes = h->integrator == ISING_INTEGRATOR_OMELYAN ? 2 * h->n_md + 1 : h->n_md + 1;
+    if (passes > MAX_PASSES) return bail(fail(h, ISING_EINVAL, "n_md too large (%d)", h->n_md));
+    if (h->flip_every < 0) return bail(fail(h, ISING_EINVAL, "flip_every must be >= 0"));
+    if (cfg->kind == ISING_KIND_LATTICE) {
+        if (cfg->dim < 1 || cfg->dim > 3) return bail(fail(h, ISING_EINVAL, "dim must be 1..3"));
+        h->dim = cfg->dim;
+        int64_t N = 1;
+        for (int d = 0; d < 3; ++d) {
+            h->L[d] = d < cfg->dim ? cfg->L[d] : 1;
+            if (d < cfg->dim && cfg->L[d] < 3)
+                return bail(fail(h, ISING_EINVAL, "lattice extent L[%d]=%d < 3", d, cfg->L[d]));
+            N *= h->L[d];
+        }
+        if (N > (int64_t)1 << 31) return bail(fail(h, ISING_EINVAL, "too many sites per chain"));
+        h->N = N;
+        Geometry &g = h->g;
+        g.dim = h->dim;
+        g.X = h->L[0];
+        g.Y = h->L[1];
+        g.Z = h->L[2];
+        g.N = N;
+        if (h->dim == 1) { g.P = g.X; g.nplanes = 1; }
+        else if (h->dim == 2) { g.P = g.X; g.nplanes = g.Y; }
+        else { g.P = g.X * g.Y; g.nplanes = g.Z; }
+        if (h->prec != ISING_PREC_PLAIN_FP64 && h->prec != ISING_PREC_FP32)
+            return bail(fail(h, ISING_EINVAL, "precision %d not available for lattices", h->prec));
+    } else if (cfg->kind == ISING_KIND_DENSE) {
+        if (cfg->n_sites < 1 || cfg->n_sites > 65536 || !cfg->J)
+            return bail(fail(h, ISING_EINVAL, "dense model needs 1 <= n_sites <= 65536 and J"));
+        h->dim = 0;
+        h->N = cfg->n_sites;
+        h->g.dim = 0;
+        h->g.X = (int)h->N; h->g.Y = 1; h->g.Z = 1; h->g.P = (int)h->N; h->g.nplanes = 1;
+        h->g.N = h->N;
+        if (h->prec != ISING_PREC_PLAIN_FP64)
+            return bail(fail(h, ISING_EINVAL, "precision %d not available for dense couplings in this build",
+                             h->prec));
+    } else {
+        return bail(fail(h, ISING_EINVAL, "unknown kind %d", cfg->kind));
+    }
+    const int64_t N = h->N;
+    // per-chain parameters and the positive-definiteness check (Sec. 2)
+    double lam_min = 0.0;
+    if (h->kind == ISING_KIND_DENSE) {
+        for (int64_t i = 0; i < N; ++i) {
+            if (cfg->J[i * N + i] != 0.0) return bail(fail(h, ISING_EINVAL, "J_ii must be 0"));
+            for (int64_t j = 0; j < i; ++j)
+                if (cfg->J[i * N + j] != cfg->J[j * N + i])
+                    return bail(fail(h, ISING_EINVAL, "J must be symmetric"));
+        }
+        lam_min = lanczos_lambda_min(cfg->J, N, (int)std::min<int64_t>(N, 96));
+    }
+    h->params.resize(h->n_chains);
+    for (int c = 0; c < h->n_chains; ++c) {
+        ChainParams &p = h->params[c];
+        const double beta = cfg->beta_chain ? cfg->beta_chain[c] : cfg->beta;
+        const double C = cfg->C_chain ? cfg->C_chain[c] : cfg->C;
+        const double eps = cfg->eps_chain ? cfg->eps_chain[c] : cfg->eps;
+        const double h0 = cfg->h0_chain ? cfg->h0_chain[c] : cfg->h0;
+        if (!(beta > 0) || !(eps > 0) || !std::isfinite(C) || !std::isfinite(h0))
+            return bail(fail(h, ISING_EINVAL, "chain %d: need beta > 0, eps > 0, finite C and h0", c));
+        if (h->kind == ISING_KIND_LATTICE) {
+            const double bound = beta * std::fabs(cfg->Jnn) * 2 * h->dim;
+            if (!(C > bound))
+                return bail(fail(h, ISING_ENOTPD,
+                                 "chain %d: C=%g must exceed beta*|J|*2*dim=%g (Sec. 2)", c, C, bound));
+        } else {
+            const double bound = beta * std::fabs(lam_min);
+            if (!(C > bound * (1.0 + 1e-9) + 1e-12))
+                return bail(fail(h, ISING_ENOTPD,
+                                 "chain %d: C=%g must exceed beta*|lambda_min(J)|=%g (Sec. 2)", c, C,
+                                 bound));
+        }
+        p.beta = beta;
+        p.bJ = beta * (h->kind == ISING_KIND_LATTICE ? cfg->Jnn : 1.0);
+        p.C = C;
+        p.eps = eps;
+        p.hp = beta * h0;
+        p.betaf = (float)p.beta;
+        p.bJf = (float)p.bJ;
+        p.Cf = (float)p.C;
+        p.epsf = (float)p.eps;
+        p.hpf = (float)p.hp;
+    }
+    make_schedule(h->integrator, h->n_md, h->sched);
+    h->has_h = cfg->h != nullptr;
+    if (is_fp32_lattice(h)) {
+        if (fused_lattice_pick(h->g, &h->threads, &h->depth) < 0)
+            return bail(fail(h, ISING_EINVAL, "lattice plane of %d sites does not fit on chip", h->g.P));
+    }
+    // device state
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return bail(fail(h, ISING_ECUDA, "no CUDA device"));
+    if (cfg->stream) {
+        h->stream = (cudaStream_t)cfg->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "stream creation failed"));
+        h->own_stream = true;
+    }
+    const size_t elem = state_elem(h);
+    const size_t sbytes = (size_t)h->n_chains * N * elem;
+    ising_status st;
+    const int nbuf = is_fp32_lattice(h) ? 3 : 2;
+    for (int i = 0; i < nbuf; ++i)
+        if ((st = dalloc(h, &h->psi[i], sbytes)) != ISING_OK) return bail(st);
+    if ((st = dalloc(h, &h->p, sbytes)) != ISING_OK) return bail(st);
+    if (h->prec == ISING_PREC_PLAIN_FP64) {
+        const size_t nb = (size_t)h->n_chains * N * sizeof(double);
+        if ((st = dalloc(h, &h->plain_a, nb)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->plain_u, nb)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->plain_F, nb)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->partials,
+                         (size_t)h->n_chains * 7 * plain_partial_blocks(N) * sizeof(double))) != ISING_OK)
+            return bail(st);
+    }
+    if ((st = dalloc(h, &h->flags, (size_t)h->n_chains * 2 * sizeof(int))) != ISING_OK) return bail(st);
+    if ((st = dalloc(h, &h->d_params, sizeof(ChainParams) * h->n_chains)) != ISING_OK) return bail(st);
+    if ((st = dalloc(h, &h->d_state, sizeof(ChainState) * h->n_chains)) != ISING_OK) return bail(st);
+    if ((st = dalloc(h, &h->d_err, sizeof(int))) != ISING_OK) return bail(st);
+    if (h->has_h) {
+        std::vector<float> h32(N);
+        for (int64_t i = 0; i < N; ++i) h32[i] = (float)cfg->h[i];
+        if ((st = dalloc(h, &h->d_h32, N * sizeof(float))) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->d_h64, N * sizeof(double))) != ISING_OK) return bail(st);
+        if (cudaMemcpy(h->d_h32, h32.data(), N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->d_h64, cfg->h, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "field upload failed"));
+    }
+    if (h->kind == ISING_KIND_DENSE) {
+        if ((st = dalloc(h, &h->d_J, (size_t)N * N * sizeof(double))) != ISING_OK) return bail(st);
+        if (cudaMemcpy(h->d_J, cfg->J, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "coupling upload failed"));
+    }
+    // zero state, psi = 0
+    std::vector<ChainState> hs(h->n_chains);
+    std::memset(hs.data(), 0, sizeof(ChainState) * h->n_chains);
+    for (auto &s : hs) { s.start = 0; s.prop = 0; }
+    if (cudaMemcpy(h->d_state, hs.data(), sizeof(ChainState) * h->n_chains, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemsetAsync(h->psi[0], 0, sbytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->p, 0, sbytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->flags, 0, (size_t)h->n_chains * 2 * sizeof(int), h->stream) != cudaSuccess)
+        return bail(fail(h, ISING_ECUDA, "state initialisation failed"));
+    if ((st = upload_params(h)) != ISING_OK) return bail(st);
+    if ((st = eval_current(h)) != ISING_OK) return bail(st);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return bail(fail(h, ISING_ECUDA, "initial evaluation failed: %s",
+                         cudaGetErrorString(cudaGetLastError())));
+    *out = h;
+    return ISING_OK;
+}
+
+ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
+    if (!h) return ISING_EINVAL;
+    if (n < 0) return fail(h, ISING_EINVAL, "n must be >= 0");
+    if (n == 0) return ISING_OK;
+    if (h->traj + n > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "trajectory counter overflow");
+    if (is_fp32_lattice(h)) {
+        // trajectories per launch: keep each launch to a bounded amount of work
+        const double work = (double)h->N * h->n_chains * h->sched.n_pass;
+        int64_t per = (int64_t)std::max(1.0, std::floor(4.0e9 / std::max(work, 1.0)));
+        per = std::min<int64_t>(per, 4096);
+        int64_t done = 0;
+        while (done < n) {
+            const int64_t k = std::min(per, n - done);
+            FusedArgs a = fused_args(h);
+            a.mode = MODE_TRAJ;
+            a.seed = seed;
+            a.traj0 = (uint32_t)(h->traj + done);
+            a.n_traj = (int)k;
+            CUDA_OR_FAIL(h, launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream));
+            h->launches += 1;
+            done += k;
+        }
+    } else {
+        for (int64_t t = 0; t < n; ++t) {
+            const uint32_t tr = (uint32_t)(h->traj + t);
+            const int measure = (int64_t)tr >= (int64_t)h->n_therm;
+            const int flip = h->flip_every > 0 && ((tr + 1) % (uint32_t)h->flip_every) == 0;
+            for (int c = 0; c < h->n_chains; ++c) {
+                PlainArgs a = plain_args(h, c);
+                CUDA_OR_FAIL(h, plain_trajectory(a, h->sched, seed, tr, measure, flip, h->stream,
+                                                 &h->launches));
+            }
+        }
+    }
+    h->traj += n;
+    return ISING_OK;
+}
+
+ising_status ising_hmc_sync(ising_hmc_t *h) {
+    if (!h) return ISING_EINVAL;
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    int err = 0;
+    CUDA_OR_FAIL(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & KERR_TIMEOUT) return fail(h, ISING_ETIMEOUT, "a device-side wait gave up");
+    if (err) return fail(h, ISING_ECUDA, "device error word %d", err);
+    return ISING_OK;
+}
+
+static ising_status fetch_states(ising_hmc *h, std::vector<ChainState> &hs) {
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    hs.resize(h->n_chains);
+    CUDA_OR_FAIL(h, cudaMemcpy(hs.data(), h->d_state, sizeof(ChainState) * h->n_chains,
+                               cudaMemcpyDeviceToHost));
+    return ISING_OK;
+}
+
+ising_status ising_hmc_chain_sums(ising_hmc_t *h, double *out) {
+    if (!h || !out) return ISING_EINVAL;
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    for (int c = 0; c < h->n_chains; ++c)
+        std::memcpy(out + (size_t)c * ISING_NSUMS, hs[c].sums, sizeof(double) * ISING_NSUMS);
+    return ISING_OK;
+}
+
+ising_status ising_hmc_last_records(ising_hmc_t *h, double *out) {
+    if (!h || !out) return ISING_EINVAL;
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    for (int c = 0; c < h->n_chains; ++c)
+        std::memcpy(out + (size_t)c * ISING_NREC, hs[c].rec, sizeof(double) * ISING_NREC);
+    return ISING_OK;
+}
+
+ising_status ising_hmc_reset_sums(ising_hmc_t *h) {
+    if (!h) return ISING_EINVAL;
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    for (auto &s : hs) std::memset(s.sums, 0, sizeof(s.sums));
+    CUDA_OR_FAIL(h, cudaMemcpy(h->d_state, hs.data(), sizeof(ChainState) * h->n_chains,
+                               cudaMemcpyHostToDevice));
+    return ISING_OK;
+}
+
+ising_status ising_hmc_set_sums(ising_hmc_t *h, const double *in) {
+    if (!h || !in) return ISING_EINVAL;
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    for (int c = 0; c < h->n_chains; ++c)
+        std::memcpy(hs[c].sums, in + (size_t)c * ISING_NSUMS, sizeof(double) * ISING_NSUMS);
+    CUDA_OR_FAIL(h, cudaMemcpy(h->d_state, hs.data(), sizeof(ChainState) * h->n_chains,
+                               cudaMemcpyHostToDevice));
+    return ISING_OK;
+}
+
+ising_status ising_hmc_observables(ising_hmc_t *h, ising_obs *out) {
+    if (!h || !out) return ISING_EINVAL;
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    const int C = h->n_chains;
+    double nmeas = 0, nacc = 0, sdh = 0, sexp = 0;
+    std::vector<double> cm(C), ca(C), ce(C), cx(C);
+    double vm = 0, va = 0, ve = 0, vx = 0;
+    for (int c = 0; c < C; ++c) {
+        const double *s = hs[c].sums;
+        const double n = s[ISING_SUM_NMEAS];
+        nmeas += n;
+        nacc += s[ISING_SUM_NACC];
+        sdh += s[ISING_SUM_DH];
+        sexp += s[ISING_SUM_EXPMDH];
+        const double inv = n > 0 ? 1.0 / n : 0.0;
+        cm[c] = s[ISING_SUM_M] * inv;
+        ca[c] = s[ISING_SUM_ABSM] * inv;
+        ce[c] = s[ISING_SUM_E] * inv;
+        cx[c] = s[ISING_SUM_EXPMDH] * inv;
+        if (C == 1 && n > 1) {
+            vm = (s[ISING_SUM_M2] * inv - cm[c] * cm[c]) / (n - 1);
+            va = (s[ISING_SUM_ABSM2] * inv - ca[c] * ca[c]) / (n - 1);
+            ve = (s[ISING_SUM_E2] * inv - ce[c] * ce[c]) / (n - 1);
+        }
+    }
+    auto mean = [&](const std::vector<double> &v) {
+        double s = 0;
+        for (double x : v) s += x;
+        return s / (double)v.size();
+    };
+    auto sem = [&](const std::vector<double> &v, double mu) {
+        if (v.size() < 2) return 0.0;
+        double s = 0;
+        for (double x : v) s += (x - mu) * (x - mu);
+        return std::sqrt(s / ((double)v.size() - 1) / (double)v.size());
+    };
+    out->m = mean(cm);
+    out->abs_m = mean(ca);
+    out->E = mean(ce);
+    out->mean_exp_mdH = nmeas > 0 ? sexp / nmeas : 0;
+    if (C > 1) {
+        out->m_err = sem(cm, out->m);
+        out->abs_m_err = sem(ca, out->abs_m);
+        out->E_err = sem(ce, out->E);
+        out->exp_mdH_err = sem(cx, mean(cx));
+    } else {
+        out->m_err = std::sqrt(std::max(vm, 0.0));
+        out->abs_m_err = std::sqrt(std::max(va, 0.0));
+        out->E_err = std::sqrt(std::max(ve, 0.0));
+    }
+    out->acceptance = nmeas > 0 ? nacc / nmeas : 0;
+    out->mean_dH = nmeas > 0 ? sdh / nmeas : 0;
+    out->n_traj = h->traj;
+    out->n_meas = (int64_t)nmeas;
+    return ISING_OK;
+}
+
+ising_status ising_hmc_get_chains(ising_hmc_t *h, int which, int chain0, int count, double *out) {
+    if (!h || !out) return ISING_EINVAL;
+    if (which < 0 || which > 2) return fail(h, ISING_EINVAL, "unknown state %d", which);
+    if (chain0 < 0 || count < 0 || chain0 + count > h->n_chains)
+        return fail(h, ISING_EINVAL, "chain range [%d, %d) out of [0, %d)", chain0, chain0 + count,
+                    h->n_chains);
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    const int64_t N = h->N;
+    std::vector<float> tmp;
+    for (int k = 0; k < count; ++k) {
+        const int c = chain0 + k;
+        const void *src;
+        if (which == ISING_STATE_P_END) src = (const char *)h->p + (size_t)c * N * state_elem(h);
+        else if (is_fp32_lattice(h)) {
+            const int b = which == ISING_STATE_PSI ? hs[c].start : hs[c].prop;
+            src = (const char *)h->psi[b] + (size_t)c * N * sizeof(float);
+        } else {
+            src = (const char *)h->psi[which == ISING_STATE_PSI ? 0 : 1] + (size_t)c * N * sizeof(double);
+        }
+        if (state_elem(h) == sizeof(double)) {
+            CUDA_OR_FAIL(h, cudaMemcpy(out + (size_t)k * N, src, N * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            tmp.resize(N);
+            CUDA_OR_FAIL(h, cudaMemcpy(tmp.data(), src, N * sizeof(float), cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < N; ++i) out[(size_t)k * N + i] = tmp[i];
+        }
+    }
+    return ISING_OK;
+}
+
+ising_status ising_hmc_get_state(ising_hmc_t *h, int which, double *out) {
+    if (!h) return ISING_EINVAL;
+    return ising_hmc_get_chains(h, which, 0, h->n_chains, out);
+}
+
+static ising_status after_set_state(ising_hmc_t *h, int64_t next_traj) {
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    for (auto &s : hs) { s.start = 0; s.prop = 0; }
+    CUDA_OR_FAIL(h, cudaMemcpy(h->d_state, hs.data(), sizeof(ChainState) * h->n_chains,
+                               cudaMemcpyHostToDevice));
+    h->traj = next_traj;
+    st = eval_current(h);
+    if (st != ISING_OK) return st;
+    return ising_hmc_sync(h);
+}
+
+ising_status ising_hmc_set_state(ising_hmc_t *h, const double *psi, int64_t next_traj) {
+    if (!h || !psi) return ISING_EINVAL;
+    if (next_traj < 0 || next_traj > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "bad trajectory index");
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    const size_t total = (size_t)h->n_chains * h->N;
+    if (state_elem(h) == sizeof(double)) {
+        CUDA_OR_FAIL(h, cudaMemcpy(h->psi[0], psi, total * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> tmp(total);
+        for (size_t i = 0; i < total; ++i) tmp[i] = (float)psi[i];
+        CUDA_OR_FAIL(h, cudaMemcpy(h->psi[0], tmp.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return after_set_state(h, next_traj);
+}
+
+ising_status ising_hmc_set_state_native(ising_hmc_t *h, const void *psi_dev, int64_t next_traj) {
+    if (!h || !psi_dev) return ISING_EINVAL;
+    if (next_traj < 0 || next_traj > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "bad trajectory index");
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    const size_t bytes = (size_t)h->n_chains * h->N * state_elem(h);
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->psi[0], psi_dev, bytes, cudaMemcpyDefault, h->stream));
+    return after_set_state(h, next_traj);
+}
+
+ising_status ising_hmc_momenta(ising_hmc_t *h, uint64_t seed, int64_t traj, int chain0, int count,
+                               double *out) {
+    if (!h || !out) return ISING_EINVAL;
+    if (traj < 0 || traj > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "bad trajectory index");
+    if (chain0 < 0 || count < 0 || chain0 + count > h->n_chains)
+        return fail(h, ISING_EINVAL, "chain range out of bounds");
+    if (is_fp32_lattice(h)) {
+        FusedArgs a = fused_args(h);
+        a.mode = MODE_MOMENTA;
+        a.seed = seed;
+        a.traj0 = (uint32_t)traj;
+        a.chain0 = chain0;
+        a.n_chains = chain0 + count;
+        CUDA_OR_FAIL(h, launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream));
+        h->launches += 1;
+    } else {
+        for (int c = chain0; c < chain0 + count; ++c) {
+            PlainArgs a = plain_args(h, c);
+            CUDA_OR_FAIL(h, plain_momenta(a, seed, (uint32_t)traj, h->stream, &h->launches));
+        }
+    }
+    return ising_hmc_get_chains(h, ISING_STATE_P_END, chain0, count, out);
+}
+
+ising_status ising_hmc_set_eps(ising_hmc_t *h, const double *eps) {
+    if (!h || !eps) return ISING_EINVAL;
+    for (int c = 0; c < h->n_chains; ++c) {
+        if (!(eps[c] > 0)) return fail(h, ISING_EINVAL, "eps[%d] must be > 0", c);
+        h->params[c].eps = eps[c];
+        h->params[c].epsf = (float)eps[c];
+    }
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    return upload_params(h);
+}
+
+ising_status ising_hmc_get_state_native(ising_hmc_t *h, void *out) {
+    if (!h || !out) return ISING_EINVAL;
+    std::vector<ChainState> hs;
+    ising_status st = fetch_states(h, hs);
+    if (st != ISING_OK) return st;
+    const size_t cb = (size_t)h->N * state_elem(h);
+    for (int c = 0; c < h->n_chains; ++c) {
+        const int b = is_fp32_lattice(h) ? hs[c].start : 0;
+        CUDA_OR_FAIL(h, cudaMemcpyAsync((char *)out + c * cb, (const char *)h->psi[b] + c * cb, cb,
+                                        cudaMemcpyDefault, h->stream));
+    }
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    return ISING_OK;
+}
+
+int ising_hmc_state_elem_bytes(const ising_hmc_t *h) { return h ? (int)state_elem(h) : -1; }
+
+int64_t ising_hmc_traj_index(const ising_hmc_t *h) { return h ? h->traj : -1; }
+int64_t ising_hmc_n_sites(const ising_hmc_t *h) { return h ? h->N : -1; }
+int ising_hmc_n_chains(const ising_hmc_t *h) { return h ? h->n_chains : -1; }
+int64_t ising_hmc_device_bytes(const ising_hmc_t *h) { return h ? h->bytes : -1; }
+int64_t ising_hmc_launch_count(const ising_hmc_t *h) { return h ? h->launches : -1; }
+
+void ising_hmc_destroy(ising_hmc_t *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+const char *ising_hmc_last_error(const ising_hmc_t *h) { return h ? h->err : g_create_err; }
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every entry point declared in include/ising_hmc.h; the Python binding
+mirrors the header's structures; invalid configurations are rejected before
+any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1912_03278_gb300 as pkg
+from paper_1912_03278_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ising_hmc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return pkg.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ising_hmc_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (ising_hmc_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_binding_covers_every_entry_point(lib):
+    for n in declared_functions():
+        assert hasattr(binding, n) or n in ("ising_hmc_n_sites", "ising_hmc_n_chains",
+                                            "ising_hmc_last_create_error"), n
+
+
+def _struct_size_from_c(name):
+    """Compile a tiny host program against the header to get sizeof/offsets."""
+    import tempfile
+    code = """
+#include <stdio.h>
+#include <stddef.h>
+#include "ising_hmc.h"
+int main(void) {
+  printf("%%zu %%zu %%zu %%zu\\n", sizeof(%s), offsetof(ising_hmc_config, n_md),
+         offsetof(ising_hmc_config, stream), sizeof(ising_obs));
+  return 0;
+}
+""" % name
+    d = tempfile.mkdtemp()
+    src = os.path.join(d, "t.c")
+    exe = os.path.join(d, "t")
+    open(src, "w").write(code)
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), src, "-o", exe])
+    return [int(x) for x in subprocess.check_output([exe]).split()]
+
+
+def test_ctypes_structs_match_header():
+    size, off_nmd, off_stream, obs_size = _struct_size_from_c("ising_hmc_config")
+    assert ctypes.sizeof(binding.ising_hmc_config) == size
+    assert binding.ising_hmc_config.n_md.offset == off_nmd
+    assert binding.ising_hmc_config.stream.offset == off_stream
+    assert ctypes.sizeof(binding.ising_obs) == obs_size
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(dim=2, L=(2, 4)), binding.ISING_EINVAL),          # L < 3 would double the bonds
+    (dict(dim=4, L=(4, 4)), binding.ISING_EINVAL),
+    (dict(dim=2, L=(4, 4), n_chains=0), binding.ISING_EINVAL),
+    (dict(dim=2, L=(4, 4), n_md=0), binding.ISING_EINVAL),
+    (dict(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44), binding.ISING_ENOTPD),  # C must exceed 2d beta J
+    (dict(dim=2, L=(4, 4), eps=-0.1), binding.ISING_EINVAL),
+    (dict(dim=2, L=(4, 4), precision=binding.ISING_PREC_BF16), binding.ISING_EINVAL),
+])
+def test_invalid_configurations_rejected(lib, kw, status):
+    cfg, keep = binding.make_config(**kw)
+    with pytest.raises(binding.IsingError) as ei:
+        binding.ising_hmc_create(cfg)
+    assert ei.value.status == status
+    assert len(binding.load().ising_hmc_last_create_error()) > 0
+
+
+def test_dense_not_positive_definite_rejected(lib):
+    import workloads
+    J = workloads.dense_couplings(40, seed=3)
+    lam = np.linalg.eigvalsh(J)[0]
+    cfg, keep = binding.make_config(kind="dense", J=J, beta=0.5, C=0.5 * abs(lam) * 0.99,
+                                    precision=binding.ISING_PREC_PLAIN_FP64)
+    with pytest.raises(binding.IsingError) as ei:
+        binding.ising_hmc_create(cfg)
+    assert ei.value.status == binding.ISING_ENOTPD
+
+
+def test_dense_asymmetric_rejected(lib):
+    J = np.zeros((5, 5))
+    J[0, 1] = 0.3
+    cfg, keep = binding.make_config(kind="dense", J=J, beta=0.5, C=1.0,
+                                    precision=binding.ISING_PREC_PLAIN_FP64)
+    with pytest.raises(binding.IsingError) as ei:
+        binding.ising_hmc_create(cfg)
+    assert ei.value.status == binding.ISING_EINVAL
+
+
+def test_estimate_bytes(lib):
+    cfg, keep = binding.make_config(dim=2, L=(1024, 1024), n_chains=4096)
+    assert binding.ising_hmc_estimate_bytes(cfg) >= 16 * 1024 * 1024 * 4096

@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (the contract of this library):
+  * proposal psi after one trajectory from a common start:
+      plain FP64 form: ||dpsi||_inf / ||psi||_inf <= 1e-10;  FP32 form: <= 1e-5
+  * dH: plain FP64 form against the fully independent oracle trajectory, and
+    FP32 form against the oracle's FP64 H evaluated on the GPU's own (psi, p)
+    end points: |dH_gpu - dH_oracle| <= 1e-6 absolute
+  * accept decisions identical unless |dH + log u| < 1e-6
+  * observables of the resulting configuration: m, E within 1e-9 (FP64) or
+    1e-6 (FP32); |m| identical up to spin decisions within 1e-6 of their
+    threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+import paper_1912_03278_gb300 as pkg
+from tests.stats_util import gamma_method, within
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = pkg.ISING_PREC_FP32, pkg.ISING_PREC_PLAIN_FP64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    oracle.build()
+
+
+def _oracle_model(kind, dim, L, J, h, beta, C, Jnn=1.0):
+    if kind == "dense":
+        return oracle.Model(kind="dense", J=J, h=h, beta=beta, C=C)
+    return oracle.Model(dim=dim, L=L, Jnn=Jnn, h=h, beta=beta, C=C)
+
+
+def _count_near_ties(model, psi, form, seed, chain, traj):
+    """Sites whose spin decision lies within 1e-6 of its threshold."""
+    _, a, t = oracle.action(model, psi, return_at=True)
+    u = oracle.spin_uniforms(form, 0 if traj == 0xFFFFFFFF else seed, chain, traj, model.N)
+    return int(np.sum(np.abs(u - (1 + t) / 2) < 1e-6))
+
+
+def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,), C=None,
+                          eps=0.1, n_md=5, prec=FP32, integrator=0, flip_every=0, traj=3, seed=11,
+                          psi_scale=0.5, n_traj=1):
+    n_chains = len(betas)
+    betas = np.asarray(betas, dtype=np.float64)
+    N = int(np.prod(L[:dim])) if kind != "dense" else J.shape[0]
+    if C is None:
+        if kind == "dense":
+            C = betas * abs(np.linalg.eigvalsh(J)[0]) + 0.1
+        else:
+            C = betas * 2 * dim + 0.1
+    C = np.broadcast_to(np.asarray(C, dtype=np.float64), (n_chains,)).copy()
+    eps_c = np.broadcast_to(np.asarray(eps, dtype=np.float64), (n_chains,)).copy()
+    psi0 = workloads.start_psi(n_chains, N, scale=psi_scale, seed=17)
+    if prec == FP32:
+        psi0 = psi0.astype(np.float32).astype(np.float64)
+    form = oracle.FORM_FP32 if prec == FP32 else oracle.FORM_FP64
+    sim = pkg.IsingHMC(kind=kind, dim=dim, L=L, J=J, h=h, beta=betas, C=C, eps=eps_c, n_md=n_md,
+                       n_chains=n_chains, precision=prec, integrator=integrator,
+                       flip_every=flip_every)
+    try:
+        sim.set_state(psi0, next_traj=traj)
+        for k in range(n_traj):
+            sim.trajectories(1, seed)
+        rec = sim.records()
+        prop = sim.state(pkg.ISING_STATE_PSI_PROPOSAL)
+        cur = sim.state(pkg.ISING_STATE_PSI)
+        pend = sim.state(pkg.ISING_STATE_P_END)
+        sums = sim.chain_sums()
+        p0 = sim.momenta(seed, traj + n_traj - 1) if n_traj == 1 else None
+    finally:
+        sim.close()
+    for c in range(n_chains):
+        model = _oracle_model(kind, dim, L, J, h, betas[c], C[c])
+        ch = oracle.Chain(model, form=form, seed=seed, chain=c, psi0=psi0[c])
+        ch.traj = traj
+        for k in range(n_traj):
+            r = ch.trajectory(eps_c[c], n_md, integrator=integrator, flip_every=flip_every)
+        scale = max(np.abs(r["psi_prop"]).max(), 1e-30)
+        rel = np.abs(prop[c] - r["psi_prop"]).max() / scale
+        tol_psi = 1e-5 if prec == FP32 else 1e-10
+        assert rel <= tol_psi, ("psi proposal", c, rel)
+        if prec == FP64:
+            assert abs(rec[c, 0] - r["dH"]) <= 1e-6, ("dH", c, rec[c, 0], r["dH"])
+        else:
+            H0 = oracle.kinetic(p0[c]) + oracle.action(model, psi0[c])
+            H1 = oracle.kinetic(pend[c]) + oracle.action(model, prop[c])
+            assert abs(rec[c, 0] - (H1 - H0)) <= 1e-6, ("dH on GPU end points", c, rec[c, 0], H1 - H0)
+            assert abs(rec[c, 0] - r["dH"]) <= max(1e-3, 1e-4 * abs(r["dH"]) * 10)
+        assert abs(rec[c, 1] - r["logu"]) <= 1e-14
+        if abs(r["dH"] + r["logu"]) >= 1e-6:
+            assert bool(rec[c, 2]) == r["accepted"], ("accept", c)
+        # observables of the current configuration (measured trajectory)
+        if bool(rec[c, 2]) == r["accepted"] and not flip_every:
+            o_gpu = dict(m=sums[c, 2], E=sums[c, 4], abs_m=sums[c, 6])
+            if prec == FP64:
+                o_ref = ch.obs
+                tol = 1e-9
+            else:
+                o_ref = oracle.measure(model, cur[c], form, seed if r["accepted"] else 0, c,
+                                       traj if r["accepted"] else 0xFFFFFFFF)
+                tol = 1e-6
+            assert abs(o_gpu["m"] - o_ref["m"]) <= tol, ("m", c)
+            assert abs(o_gpu["E"] - o_ref["E"]) <= tol, ("E", c)
+            ties = _count_near_ties(model, cur[c], form, seed, c,
+                                    traj if r["accepted"] else 0xFFFFFFFF)
+            assert abs(o_gpu["abs_m"] - o_ref["abs_m"]) <= 2.0 * ties / N + 1e-12, ("|m|", c)
+    return rec
+
+
+# ------------------------------------------------------------------ FP32 ----
+@pytest.mark.parametrize("dim,L", [
+    (2, (32, 32)),      # VEC=4, several planes
+    (2, (12, 20)),      # rectangular
+    (2, (10, 7)),       # scalar fallback (row not a multiple of 4)
+    (2, (3, 3)),        # minimum extent
+    (3, (8, 8, 8)),
+    (3, (12, 6, 5)),    # vector path, ragged plane count
+    (3, (5, 6, 7)),     # scalar fallback
+    (1, (16,)),
+    (1, (17,)),
+])
+def test_fp32_one_trajectory(dim, L):
+    one_trajectory_parity(dim=dim, L=L, betas=(0.30, 0.44, 0.21), h=0.05, eps=0.08, n_md=6)
+
+
+def test_fp32_per_site_field_and_long_trajectory():
+    N = 16 * 16
+    h = workloads.dense_fields(N, sigma=0.2, seed=5)
+    one_trajectory_parity(dim=2, L=(16, 16), betas=(0.4, 0.45), h=h, eps=0.05, n_md=20)
+
+
+def test_fp32_single_step_and_large_eps():
+    one_trajectory_parity(dim=2, L=(8, 12), betas=(0.5,), eps=0.3, n_md=1)
+
+
+def test_fp32_omelyan():
+    one_trajectory_parity(dim=2, L=(16, 16), betas=(0.44, 0.3), eps=0.15, n_md=4, integrator=1)
+
+
+def test_fp32_sign_flip_at_zero_field():
+    rec = one_trajectory_parity(dim=2, L=(8, 8), betas=(0.6, 0.5), h=0.0, eps=0.1, n_md=4,
+                                flip_every=1, traj=0)
+    assert np.all(rec[:, 7] == 1.0)  # S(-psi) = S(psi) at h = 0: always accepted
+
+
+def test_fp32_sign_flip_with_field():
+    one_trajectory_parity(dim=2, L=(8, 8), betas=(0.6, 0.5), h=0.02, eps=0.1, n_md=4,
+                          flip_every=1, traj=0)
+
+
+def test_fp32_several_trajectories():
+    one_trajectory_parity(dim=3, L=(6, 6, 6), betas=(0.22,), h=0.05, eps=0.1, n_md=4, n_traj=3,
+                          traj=0)
+
+
+# ------------------------------------------------------------ plain FP64 ----
+@pytest.mark.parametrize("dim,L", [(2, (4, 4)), (3, (4, 5, 3)), (1, (9,)), (2, (16, 12))])
+def test_fp64_one_trajectory(dim, L):
+    one_trajectory_parity(dim=dim, L=L, betas=(0.44, 0.3), h=0.1, eps=0.1, n_md=10, prec=FP64)
+
+
+def test_fp64_dense_with_fields():
+    N = 48
+    J = workloads.dense_couplings(N, seed=1)
+    h = workloads.dense_fields(N, sigma=0.1)
+    one_trajectory_parity(kind="dense", J=J, h=h, betas=(0.5, 0.8), eps=0.1, n_md=8, prec=FP64)
+
+
+def test_fp64_omelyan_and_flip():
+    one_trajectory_parity(dim=2, L=(6, 6), betas=(0.44,), h=0.03, eps=0.2, n_md=3, prec=FP64,
+                          integrator=1, flip_every=1, traj=0)
+
+
+def test_fp64_small_2d_sequence_stays_in_lockstep():
+    """L=4, beta=0.44, eps=0.1, N_md=10, seed 0: 40 trajectories, step by step."""
+    model = oracle.Model(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44 + 0.1)
+    sim = pkg.IsingHMC(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44 + 0.1, eps=0.1, n_md=10,
+                       precision=FP64)
+    ch = oracle.Chain(model, form=oracle.FORM_FP64, seed=0)
+    try:
+        for k in range(40):
+            sim.trajectories(1, 0)
+            rec = sim.records()[0]
+            r = ch.trajectory(0.1, 10)
+            assert abs(rec[0] - r["dH"]) <= 1e-6, k
+            assert bool(rec[2]) == r["accepted"], k
+        np.testing.assert_allclose(sim.state()[0], ch.psi, atol=1e-9)
+    finally:
+        sim.close()
+
+
+# --------------------------------------------------------- invariances ----
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_trajectory_split_is_bitwise_invariant(prec):
+    kw = dict(dim=2, L=(12, 12), beta=np.array([0.4, 0.45]), h=0.02, eps=0.1, n_md=5, n_chains=2,
+              precision=prec, flip_every=2)
+    a = pkg.IsingHMC(**kw)
+    b = pkg.IsingHMC(**kw)
+    try:
+        a.trajectories(5, 99)
+        b.trajectories(3, 99)
+        b.trajectories(2, 99)
+        assert np.array_equal(a.state(), b.state())
+        assert np.array_equal(a.chain_sums(), b.chain_sums())
+    finally:
+        a.close()
+        b.close()
+
+
+def test_checkpoint_resume_is_exact():
+    kw = dict(dim=3, L=(6, 6, 6), beta=0.22, h=0.05, eps=0.1, n_md=5, n_chains=3, precision=FP32)
+    a = pkg.IsingHMC(**kw)
+    b = pkg.IsingHMC(**kw)
+    try:
+        a.trajectories(4, 5)
+        psi, sums, k = a.state(), a.chain_sums(), a.traj_index
+        a.trajectories(3, 5)
+        b.set_state(psi, next_traj=k)
+        pkg.ising_hmc_set_sums(b.h, sums)
+        b.trajectories(3, 5)
+        assert np.array_equal(a.state(), b.state())
+        assert np.array_equal(a.chain_sums(), b.chain_sums())
+    finally:
+        a.close()
+        b.close()
+
+
+def test_chain_result_independent_of_batch_size():
+    """Chain c's trajectory depends only on (seed, c, traj), not on the batch."""
+    betas = np.array([0.3, 0.35, 0.4, 0.45])
+    a = pkg.IsingHMC(dim=2, L=(16, 16), beta=betas, eps=0.1, n_md=5, n_chains=4)
+    b = pkg.IsingHMC(dim=2, L=(16, 16), beta=betas[:2], eps=0.1, n_md=5, n_chains=2)
+    try:
+        a.trajectories(3, 8)
+        b.trajectories(3, 8)
+        assert np.array_equal(a.state()[:2], b.state())
+    finally:
+        a.close()
+        b.close()
+
+
+# --------------------------------------------------------- statistics ----
+def test_fp64_small_2d_against_brute_force():
+    """L=4 periodic, beta=0.44, C=4 beta+0.1, eps=0.1, N_md=10, FP64, 1 chain,
+    20000 trajectories, seed 0: within 3 sigma (Gamma method) of enumeration."""
+    model = oracle.Model(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44 + 0.1)
+    bf = oracle.brute_force(model)
+    sim = pkg.IsingHMC(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44 + 0.1, eps=0.1, n_md=10,
+                       precision=FP64, n_therm=200)
+    try:
+        series = {"E": [], "abs_m": [], "m": []}
+        prev = np.zeros(10)
+        sim.trajectories(200, 0)
+        for k in range(20000 - 200):
+            sim.trajectories(1, 0)
+            if k % 1 == 0:
+                s = sim.chain_sums()[0]
+                d = s - prev
+                prev = s
+                series["m"].append(d[2])
+                series["E"].append(d[4])
+                series["abs_m"].append(d[6])
+        for key in series:
+            mean, err, _ = gamma_method(series[key])
+            assert within(mean, bf[key], err), (key, mean, bf[key], err)
+    finally:
+        sim.close()
+
+
+def test_fp32_small_2d_many_chains_against_brute_force():
+    model = oracle.Model(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44 + 0.1)
+    bf = oracle.brute_force(model)
+    sim = pkg.IsingHMC(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44 + 0.1, eps=0.1, n_md=10,
+                       n_chains=512, n_therm=100)
+    try:
+        sim.trajectories(2100, 1)
+        o = sim.observables()
+        for key in ("E", "abs_m", "m"):
+            assert within(o[key], bf[key], o[key + "_err"]), (key, o[key], bf[key], o[key + "_err"])
+        assert within(o["mean_exp_mdH"], 1.0, o["exp_mdH_err"])
+    finally:
+        sim.close()
+
+
+def test_fp32_2d_onsager_away_from_criticality():
+    from tests.stats_util import onsager_energy
+    beta = 0.30
+    sim = pkg.IsingHMC(dim=2, L=(64, 64), beta=beta, eps=0.12, n_md=8, n_chains=256, n_therm=100)
+    try:
+        sim.trajectories(400, 3)
+        o = sim.observables()
+        assert within(o["E"], onsager_energy(beta), o["E_err"], floor=1e-3), o
+        assert o["acceptance"] > 0.5
+    finally:
+        sim.close()
+
+
+# ------------------------------------------------ full-size sampled parity ----
+def test_full_size_2d_batch_sampled_parity():
+    """The benchmark's launch: 2D L=1024, 16 betas x 256 chains, N_md=20, FP32.
+    Two sampled chains are recomputed by the oracle from the same start."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    L, n_md, eps = 1024, 20, 0.02
+    betas = np.repeat(workloads.beta_sweep(), 256)
+    n_chains = len(betas)
+    if free < 16 * L * L * n_chains * 1.05:
+        pytest.skip("not enough device memory for the full batch")
+    C = workloads.lattice_C(betas, 2)
+    sim = pkg.IsingHMC(dim=2, L=(L, L), beta=betas, C=C, eps=eps, n_md=n_md, n_chains=n_chains)
+    seed, samples = 2024, (0, n_chains - 1)
+    try:
+        sim.trajectories(1, seed)
+        rec = sim.records()
+        got = {c: (sim.chains(pkg.ISING_STATE_PSI_PROPOSAL, c, 1)[0],
+                   sim.chains(pkg.ISING_STATE_P_END, c, 1)[0]) for c in samples}
+        p0 = {c: sim.momenta(seed, 0, c, 1)[0] for c in samples}
+        assert np.all(np.isfinite(rec[:, 0]))
+    finally:
+        sim.close()
+    for c in samples:
+        model = oracle.Model(dim=2, L=(L, L), beta=betas[c], C=C[c])
+        ch = oracle.Chain(model, form=oracle.FORM_FP32, seed=seed, chain=c)
+        r = ch.trajectory(eps, n_md)
+        prop, pend = got[c]
+        rel = np.abs(prop - r["psi_prop"]).max() / np.abs(r["psi_prop"]).max()
+        assert rel <= 1e-5, (c, rel)
+        H0 = oracle.kinetic(p0[c]) + oracle.action(model, np.zeros(L * L))
+        H1 = oracle.kinetic(pend) + oracle.action(model, prop)
+        assert abs(rec[c, 0] - (H1 - H0)) <= 1e-6, (c, rec[c, 0], H1 - H0)
