@@ -384,14 +384,16 @@ void or_trajectory(const or_model *m, or_chain *c, int form, uint64_t seed, uint
     }
     /* 4. optional global sign flip psi -> -psi with its own Metropolis test */
     if (flip_every > 0 && ((tr + 1) % (uint32_t)flip_every) == 0) {
-        for (int64_t i = 0; i < N; ++i) psi[i] = -c->psi[i];
-        double Sf = or_action(m, psi, NULL, NULL);
+        double *neg = (double *)malloc(sizeof(double) * N);
+        for (int64_t i = 0; i < N; ++i) neg[i] = -c->psi[i];
+        double Sf = or_action(m, neg, NULL, NULL);
         double lu = log(flip_uniform(seed, chain, tr));
         if (lu < -(Sf - c->S)) {
-            memcpy(c->psi, psi, sizeof(double) * N);
+            memcpy(c->psi, neg, sizeof(double) * N);
             c->S = Sf;
             changed = 1;
         }
+        free(neg);
     }
     /* 5. measurement; a repeated configuration repeats its measurement */
     if (changed) or_measure(m, c->psi, form, seed, chain, tr, &c->obs);

@@ -425,8 +425,14 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             }
             __syncthreads();
             if (bcast[1]) {
-                float *gs = A.psi[start] + (int64_t)chain * g.N;
-                for (int64_t i = threadIdx.x; i < g.N; i += blockDim.x) gs[i] = -gs[i];
+                // -psi goes to the buffer that is neither current nor the proposal,
+                // so the MD end point stays readable
+                const int f = (start != prop) ? 3 - start - prop : (start + 1) % 3;
+                const float *gs = A.psi[start] + (int64_t)chain * g.N;
+                float *gf = A.psi[f] + (int64_t)chain * g.N;
+                for (int64_t i = threadIdx.x; i < g.N; i += blockDim.x) gf[i] = -gs[i];
+                start = f;
+                if (threadIdx.x == 0) st->start = f;
             }
             __syncthreads();
         }
