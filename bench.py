@@ -197,18 +197,21 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm ----
 def tune_eps(sims, betas_per_chain, rounds, seed):
-    """Robbins-Monro on log eps per beta group toward TARGET_ACC (equilibration only)."""
-    import paper_1912_03278_gb300 as pkg
+    """Step-size tuning during equilibration only (frozen afterwards).  For a
+    second-order integrator <dH> = <dH^2>/2 grows as eps^4, and an acceptance
+    of 80% corresponds to <dH> ~ 0.128; each round rescales eps per beta
+    group by (0.128 / (<dH^2>/2))^(1/4), clamped to [1/2, 2]."""
+    target = 0.128
     ub = np.unique(betas_per_chain)
     for L, sim in sims.items():
         eps = np.full(len(betas_per_chain), EPS0.get(L, 0.02))
         for r in range(rounds):
             sim.trajectories(1, seed + 1000 + r)
-            acc = sim.records()[:, 2]
+            dH = sim.records()[:, 0]
             for b in ub:
                 sel = betas_per_chain == b
-                a = acc[sel].mean()
-                eps[sel] *= math.exp(0.8 * (a - TARGET_ACC))
+                half_msq = 0.5 * float(np.mean(dH[sel] ** 2)) + 1e-12
+                eps[sel] *= float(np.clip((target / half_msq) ** 0.25, 0.5, 2.0))
             sim.set_eps(eps)
         sim._eps = eps.copy()
 

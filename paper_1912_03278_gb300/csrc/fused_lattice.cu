@@ -15,6 +15,7 @@
 // (Sec. 3) itself, so a launch can run many trajectories back to back.
 #include <cuda_runtime.h>
 
+#include "df32.cuh"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -95,11 +96,12 @@ __device__ __forceinline__ void neighbour_sum(const Geometry &g, const float *pm
     }
 }
 
-// Same sum in FP64 (exact for these few FP32 terms), for the action.
+// The same neighbour sum exactly, as a double-float (TwoSum chain), for the
+// FP64-accurate action.
 template <int VEC>
-__device__ __forceinline__ void neighbour_sum_f64(const Geometry &g, const float *pm,
-                                                  const float *pc, const float *pq, int e0,
-                                                  double (&nb)[VEC]) {
+__device__ __forceinline__ void neighbour_sum_df(const Geometry &g, const float *pm,
+                                                 const float *pc, const float *pq, int e0,
+                                                 f2 (&nb)[VEC]) {
     const int x0 = e0 % g.X;
     const int rowbase = e0 - x0;
 #pragma unroll
@@ -107,21 +109,31 @@ __device__ __forceinline__ void neighbour_sum_f64(const Geometry &g, const float
         const int x = x0 + k;
         const int l = rowbase + (x == 0 ? g.X - 1 : x - 1);
         const int r = rowbase + (x == g.X - 1 ? 0 : x + 1);
-        double s = (double)pc[l] + (double)pc[r];
+        f2 s = two_sum(pc[l], pc[r]);
         if (g.dim == 3) {
             const int y = rowbase / g.X;
-            s += (double)pc[(y == 0 ? g.Y - 1 : y - 1) * g.X + x];
-            s += (double)pc[(y == g.Y - 1 ? 0 : y + 1) * g.X + x];
+            s = df_add_f(s, pc[(y == 0 ? g.Y - 1 : y - 1) * g.X + x]);
+            s = df_add_f(s, pc[(y == g.Y - 1 ? 0 : y + 1) * g.X + x]);
         }
-        if (g.dim >= 2) s += (double)pm[e0 + k] + (double)pq[e0 + k];
+        if (g.dim >= 2) {
+            s = df_add_f(s, pm[e0 + k]);
+            s = df_add_f(s, pq[e0 + k]);
+        }
         nb[k] = s;
     }
 }
 
-// Per-thread accumulators of one trajectory (FP64).
+// Per-thread accumulators of one trajectory, double-float (converted to FP64
+// once, for the block reduction).
 struct Acc {
-    double K0, K1, S, sT, sAT, sHT, sS;
+    f2 K0, K1, S, sT, sAT, sHT;
+    int sS;
 };
+
+__device__ __forceinline__ Acc acc_zero() {
+    const f2 z{0.0f, 0.0f};
+    return Acc{z, z, z, z, z, z, 0};
+}
 
 struct PassCfg {
     int src, dst;
@@ -133,9 +145,13 @@ struct PassCfg {
     uint32_t spin_traj;  // trajectory index of the spin draw
 };
 
+__device__ __forceinline__ float *sel3(const FusedArgs &A, int i) {
+    return i == 0 ? A.psi[0] : (i == 1 ? A.psi[1] : A.psi[2]);
+}
+
 template <int VEC, int D>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
-                         float *smem, Acc &acc) {
+                         uint32_t traj, float *smem, Acc &acc) {
     constexpr int R = D + 4;   // psi ring slots
     constexpr int RP = D + 2;  // p ring slots
     const Geometry &g = A.g;
@@ -144,8 +160,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     float *p_ring = psi_ring + R * P;
     float *u_ring = p_ring + RP * P;
     const int64_t cbase = (int64_t)chain * g.N;
-    const float *__restrict__ gsrc = A.psi[pc.src] + cbase;
-    float *__restrict__ gdst = A.psi[pc.dst] + cbase;
+    const float *__restrict__ gsrc = sel3(A, pc.src) + cbase;
+    float *__restrict__ gdst = sel3(A, pc.dst) + cbase;
     float *__restrict__ gp = A.p + cbase;
     const int z0 = 0, z1 = g.nplanes;
     const int nvec = P / VEC;
@@ -183,7 +199,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     int s_next = D + 3;
 
     const float Cf = prm.Cf, bJf = prm.bJf;
-    const double Cd = prm.C, bJd = prm.bJ;
+    const f2 C2 = df_from_double(prm.C), bJ2 = df_from_double(prm.bJ);
+    const f2 hp2 = df_from_double(prm.hp), beta2 = df_from_double(prm.beta);
 
     for (int it = z0 - 1; it <= z1; ++it) {
         cp_wait<D>();
@@ -213,8 +230,10 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     stv<VEC>(uo + e0, u);
                 }
                 if (act) {
-                    double nbd[VEC];
-                    neighbour_sum_f64<VEC>(g, pm, pcen, pq, e0, nbd);
+                    // FP64-accurate action in double-float:
+                    //   S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),  x = a + h'
+                    f2 nbd[VEC];
+                    neighbour_sum_df<VEC>(g, pm, pcen, pq, e0, nbd);
                     const int64_t site0 = (int64_t)zw * P + e0;
                     float su[4];
                     if constexpr (VEC == 4) {
@@ -224,14 +243,20 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     }
 #pragma unroll
                     for (int k = 0; k < VEC; ++k) {
-                        const double hp = A.h64 ? prm.beta * A.h64[site0 + k] : prm.hp;
-                        const double a = pc.sign * (Cd * (double)c.v[k] + bJd * nbd[k]);
-                        const double x = a + hp;
-                        acc.S += 0.5 * (double)(pc.sign * c.v[k]) * a - log2cosh_f64(x);
-                        const float t = tanhf((float)x);
-                        acc.sT += (double)t;
-                        acc.sAT += a * (double)t;
-                        acc.sHT += hp * (double)t;
+                        const float ps = pc.sign * c.v[k];
+                        const f2 hp = A.h64 ? df_mul(beta2, df_from_double(A.h64[site0 + k])) : hp2;
+                        const f2 a = df_add(df_mul_f(C2, ps), df_mul(bJ2, f2{pc.sign * nbd[k].hi,
+                                                                               pc.sign * nbd[k].lo}));
+                        const f2 x = df_add(a, hp);
+                        const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
+                        const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, A.lpe_tab);
+                        f2 term = df_mul_f(a, 0.5f * ps);
+                        term = df_add(term, df_neg(df_add(ax, gl)));
+                        acc.S = df_add(acc.S, term);
+                        const float t = tanhf(x.hi);
+                        acc.sT = df_add_f(acc.sT, t);
+                        acc.sAT = df_add_f(acc.sAT, a.hi * t);
+                        acc.sHT = df_add_f(acc.sHT, hp.hi * t);
                         float uu;
                         if constexpr (VEC == 4) {
                             uu = su[k];
@@ -241,7 +266,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                             const int q = (int)((site0 + k) & 3);
                             uu = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
                         }
-                        acc.sS += (uu < (1.0f + t) * 0.5f) ? 1.0 : -1.0;
+                        acc.sS += (uu < (1.0f + t) * 0.5f) ? 1 : -1;
                     }
                 }
             }
@@ -261,20 +286,20 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 Vec<VEC> pv;
                 if (pc.first) {
                     if constexpr (VEC == 4) {
-                        const float4 w = momenta4_f32((uint32_t)(site0 >> 2), A.traj0,
+                        const float4 w = momenta4_f32((uint32_t)(site0 >> 2), traj,
                                                       (uint32_t)chain, A.seed);
                         pv.v[0] = w.x; pv.v[1] = w.y; pv.v[2] = w.z; pv.v[3] = w.w;
                     } else {
 #pragma unroll
                         for (int k = 0; k < VEC; ++k) {
-                            const float4 w = momenta4_f32((uint32_t)((site0 + k) >> 2), A.traj0,
+                            const float4 w = momenta4_f32((uint32_t)((site0 + k) >> 2), traj,
                                                           (uint32_t)chain, A.seed);
                             const int q = (int)((site0 + k) & 3);
                             pv.v[k] = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) acc.K0 += 0.5 * (double)pv.v[k] * (double)pv.v[k];
+                    for (int k = 0; k < VEC; ++k) acc.K0 = df_add(acc.K0, two_prod(pv.v[k], 0.5f * pv.v[k]));
                 } else {
                     pv = ldv<VEC>(ppz + e0);
                 }
@@ -286,7 +311,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 stv<VEC>(gp + site0, pv);
                 if (pc.last) {
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) acc.K1 += 0.5 * (double)pv.v[k] * (double)pv.v[k];
+                    for (int k = 0; k < VEC; ++k) acc.K1 = df_add(acc.K1, two_prod(pv.v[k], 0.5f * pv.v[k]));
                 } else {
                     const Vec<VEC> ps = ldv<VEC>(psz + e0);
                     Vec<VEC> pn;
@@ -333,11 +358,12 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
     }
 
     if (A.mode == MODE_EVAL) {
-        Acc acc = {0, 0, 0, 0, 0, 0, 0};
+        Acc acc = acc_zero();
         const int start = st->start;
         PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, 1.0f, TRAJ_INIT};
-        run_pass<VEC, D>(A, pc, prm, chain, smem, acc);
-        double v[5] = {acc.S, acc.sT, acc.sAT, acc.sHT, acc.sS};
+        run_pass<VEC, D>(A, pc, prm, chain, TRAJ_INIT, smem, acc);
+        double v[5] = {df_to_double(acc.S), df_to_double(acc.sT), df_to_double(acc.sAT),
+                       df_to_double(acc.sHT), (double)acc.sS};
         block_sum<5>(v, red);
         if (threadIdx.x == 0) {
             st->S = v[0];
@@ -354,9 +380,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
     int start = st->start;
     for (int k = 0; k < A.n_traj; ++k) {
         const uint32_t traj = A.traj0 + (uint32_t)k;
-        FusedArgs Ak = A;
-        Ak.traj0 = traj;
-        Acc acc = {0, 0, 0, 0, 0, 0, 0};
+        Acc acc = acc_zero();
         for (int j = 0; j < S.n_pass; ++j) {
             PassCfg pc;
             pc.src = buf_loc(start, j);
@@ -369,9 +393,11 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             pc.action = pc.last;
             pc.sign = 1.0f;
             pc.spin_traj = traj;
-            run_pass<VEC, D>(Ak, pc, prm, chain, smem, acc);
+            run_pass<VEC, D>(A, pc, prm, chain, traj, smem, acc);
         }
-        double v[7] = {acc.K0, acc.K1, acc.S, acc.sT, acc.sAT, acc.sHT, acc.sS};
+        double v[7] = {df_to_double(acc.K0), df_to_double(acc.K1), df_to_double(acc.S),
+                       df_to_double(acc.sT), df_to_double(acc.sAT), df_to_double(acc.sHT),
+                       (double)acc.sS};
         block_sum<7>(v, red);
         const int prop = buf_loc(start, S.n_pass - 1);
         if (threadIdx.x == 0) {
@@ -404,10 +430,11 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
         __syncthreads();
         // ---- optional global sign flip psi -> -psi (Sec. 3, ergodicity) ----
         if (A.flip_every > 0 && ((traj + 1) % (uint32_t)A.flip_every) == 0) {
-            Acc fa = {0, 0, 0, 0, 0, 0, 0};
+            Acc fa = acc_zero();
             PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, -1.0f, traj};
-            run_pass<VEC, D>(Ak, pc, prm, chain, smem, fa);
-            double w[5] = {fa.S, fa.sT, fa.sAT, fa.sHT, fa.sS};
+            run_pass<VEC, D>(A, pc, prm, chain, traj, smem, fa);
+            double w[5] = {df_to_double(fa.S), df_to_double(fa.sT), df_to_double(fa.sAT),
+                           df_to_double(fa.sHT), (double)fa.sS};
             block_sum<5>(w, red);
             if (threadIdx.x == 0) {
                 const double lu = accept_logu(traj, (uint32_t)chain, A.seed, PURPOSE_FLIP);
@@ -428,8 +455,8 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
                 // -psi goes to the buffer that is neither current nor the proposal,
                 // so the MD end point stays readable
                 const int f = (start != prop) ? 3 - start - prop : (start + 1) % 3;
-                const float *gs = A.psi[start] + (int64_t)chain * g.N;
-                float *gf = A.psi[f] + (int64_t)chain * g.N;
+                const float *gs = sel3(A, start) + (int64_t)chain * g.N;
+                float *gf = sel3(A, f) + (int64_t)chain * g.N;
                 for (int64_t i = threadIdx.x; i < g.N; i += blockDim.x) gf[i] = -gs[i];
                 start = f;
                 if (threadIdx.x == 0) st->start = f;

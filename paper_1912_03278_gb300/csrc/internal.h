@@ -50,6 +50,7 @@ struct FusedArgs {
     float *p;                // momenta, chain-major
     const float *h32;        // per-site h_i (not scaled by beta), or null
     const double *h64;
+    const float4 *lpe_tab;   // Taylor table of log(1 + exp(-y)), see df32.cuh
     const ChainParams *params;
     ChainState *state;
     Geometry g;
@@ -77,6 +78,10 @@ cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int 
                                  int depth, cudaStream_t s);
 int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec);
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
+
+// Host construction of the log(1 + exp(-y)) Taylor table (3 float4 per node).
+void build_log1pexp_table(float *out /* 12 * (LOG1PEXP_K + 1) floats */);
+constexpr int LOG1PEXP_NODES = 36 * 16 + 1;
 
 // Plain FP64 form: one chain per launch, unfused kernels.
 struct PlainArgs {

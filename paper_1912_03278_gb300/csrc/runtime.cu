@@ -36,6 +36,7 @@ struct ising_hmc {
     float *d_h32 = nullptr;
     double *d_h64 = nullptr;
     double *d_J = nullptr;
+    float *d_lpe = nullptr;
     int *d_err = nullptr;
     // launch shape of the fused kernel
     int threads = 0, depth = 0;
@@ -167,13 +168,56 @@ static double lanczos_lambda_min(const double *J, int64_t N, int steps) {
     return 0.5 * (lo + hi);
 }
 
+// Taylor table of g(y) = log(1 + exp(-y)) at y_k = k/16 (layout in df32.cuh).
+// With s = 1/(1 + e^y): g' = -s and ds/dy = -s(1 - s), so g^(n) = P_n(s) with
+// P_1 = -s and P_{n+1}(s) = -s(1 - s) P_n'(s); c_n = P_n(s)/n!.
+void ihmc::build_log1pexp_table(float *out) {
+    double P[8][10];
+    std::memset(P, 0, sizeof P);
+    P[1][1] = -1.0;
+    for (int n = 1; n < 7; ++n) {
+        double D[10] = {0};
+        for (int j = 0; j + 1 < 10; ++j) D[j] = (j + 1) * P[n][j + 1];
+        for (int j = 0; j < 10; ++j) {
+            double v = 0.0;
+            if (j >= 1) v -= D[j - 1];
+            if (j >= 2) v += D[j - 2];
+            P[n + 1][j] = v;
+        }
+    }
+    double fact[8] = {1, 1, 2, 6, 24, 120, 720, 5040};
+    for (int k = 0; k < LOG1PEXP_NODES; ++k) {
+        const double y = (double)k / 16.0;
+        const double sg = 1.0 / (1.0 + std::exp(y));
+        double c[8];
+        c[0] = std::log1p(std::exp(-y));
+        for (int n = 1; n < 8; ++n) {
+            double v = 0.0, pw = 1.0;
+            for (int j = 0; j < 10; ++j) {
+                v += P[n][j] * pw;
+                pw *= sg;
+            }
+            c[n] = v / fact[n];
+        }
+        // exact low-order coefficients: c1 = -s, c2 = s(1-s)/2
+        c[1] = -sg;
+        c[2] = 0.5 * sg * (1.0 - sg);
+        auto hi = [](double x) { return (float)x; };
+        auto lo = [](double x) { return (float)(x - (double)(float)x); };
+        float *q = out + 12 * k;
+        q[0] = hi(c[0]); q[1] = lo(c[0]); q[2] = hi(c[1]); q[3] = lo(c[1]);
+        q[4] = hi(c[2]); q[5] = lo(c[2]); q[6] = (float)c[3]; q[7] = (float)c[4];
+        q[8] = (float)c[5]; q[9] = (float)c[6]; q[10] = (float)c[7]; q[11] = 0.0f;
+    }
+}
+
 static void free_all(ising_hmc *h) {
     for (auto &b : h->psi) {
         if (b) cudaFree(b);
         b = nullptr;
     }
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
-                    h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_err};
+                    h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err};
     for (void *b : bufs)
         if (b) cudaFree(b);
     h->p = nullptr;
@@ -234,6 +278,7 @@ static FusedArgs fused_args(ising_hmc *h) {
     a.p = (float *)h->p;
     a.h32 = h->has_h ? h->d_h32 : nullptr;
     a.h64 = h->has_h ? h->d_h64 : nullptr;
+    a.lpe_tab = reinterpret_cast<const float4 *>(h->d_lpe);
     a.params = h->d_params;
     a.state = h->d_state;
     a.g = h->g;
@@ -432,6 +477,14 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     if ((st = dalloc(h, &h->d_params, sizeof(ChainParams) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_state, sizeof(ChainState) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_err, sizeof(int))) != ISING_OK) return bail(st);
+    if (is_fp32_lattice(h)) {
+        std::vector<float> tab(12 * LOG1PEXP_NODES);
+        build_log1pexp_table(tab.data());
+        if ((st = dalloc(h, &h->d_lpe, tab.size() * sizeof(float))) != ISING_OK) return bail(st);
+        if (cudaMemcpy(h->d_lpe, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "table upload failed"));
+    }
     if (h->has_h) {
         std::vector<float> h32(N);
         for (int64_t i = 0; i < N; ++i) h32[i] = (float)cfg->h[i];

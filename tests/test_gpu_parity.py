@@ -74,12 +74,13 @@ def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=
         for k in range(n_traj - 1):
             sim.trajectories(1, seed)
         start_last = sim.state(pkg.ISING_STATE_PSI)
+        sums_before = sim.chain_sums()
         sim.trajectories(1, seed)
         rec = sim.records()
         prop = sim.state(pkg.ISING_STATE_PSI_PROPOSAL)
         cur = sim.state(pkg.ISING_STATE_PSI)
         pend = sim.state(pkg.ISING_STATE_P_END)
-        sums = sim.chain_sums()
+        sums = sim.chain_sums() - sums_before
         p0 = sim.momenta(seed, traj + n_traj - 1)
     finally:
         sim.close()
@@ -103,20 +104,22 @@ def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=
         assert abs(rec[c, 1] - r["logu"]) <= 1e-14
         if abs(r["dH"] + r["logu"]) >= 1e-6:
             assert bool(rec[c, 2]) == r["accepted"], ("accept", c)
-        # observables of the current configuration (measured trajectory)
-        if bool(rec[c, 2]) == r["accepted"] and not flip_every:
+        # observables of the current configuration (measured trajectory); a
+        # configuration repeated after a rejection keeps its earlier spin draw
+        last = traj + n_traj - 1
+        if bool(rec[c, 2]) == r["accepted"] and not flip_every and (r["accepted"] or n_traj == 1):
             o_gpu = dict(m=sums[c, 2], E=sums[c, 4], abs_m=sums[c, 6])
             if prec == FP64:
                 o_ref = ch.obs
                 tol = 1e-9
             else:
                 o_ref = oracle.measure(model, cur[c], form, seed if r["accepted"] else 0, c,
-                                       traj if r["accepted"] else 0xFFFFFFFF)
+                                       last if r["accepted"] else 0xFFFFFFFF)
                 tol = 1e-6
             assert abs(o_gpu["m"] - o_ref["m"]) <= tol, ("m", c)
             assert abs(o_gpu["E"] - o_ref["E"]) <= tol, ("E", c)
             ties = _count_near_ties(model, cur[c], form, seed, c,
-                                    traj if r["accepted"] else 0xFFFFFFFF)
+                                    last if r["accepted"] else 0xFFFFFFFF)
             assert abs(o_gpu["abs_m"] - o_ref["abs_m"]) <= 2.0 * ties / N + 1e-12, ("|m|", c)
     return rec
 
@@ -342,3 +345,28 @@ def test_full_size_2d_batch_sampled_parity():
         H0 = oracle.kinetic(p0[c]) + oracle.action(model, np.zeros(L * L))
         H1 = oracle.kinetic(pend) + oracle.action(model, prop)
         assert abs(rec[c, 0] - (H1 - H0)) <= 1e-6, (c, rec[c, 0], H1 - H0)
+
+
+def test_fp32_action_large_arguments():
+    """Arguments 2|a + h'| beyond the table's 36 (exp(-y) branch) and near 0."""
+    one_trajectory_parity(dim=2, L=(16, 16), betas=(0.4, 0.3), C=8.0, psi_scale=2.5, h=0.3,
+                          eps=0.01, n_md=3)
+
+
+def test_fp32_action_matches_fp64_on_random_states():
+    """Set arbitrary FP32 states; S of the current configuration equals the
+    oracle's FP64 action within 1e-6 (double-float evaluation)."""
+    L = 64
+    for scale in (0.05, 0.7, 4.0):
+        psi = workloads.start_psi(3, L * L, scale=scale, seed=31).astype(np.float32).astype(np.float64)
+        sim = pkg.IsingHMC(dim=2, L=(L, L), beta=np.array([0.3, 0.44, 0.6]), h=0.07, eps=0.05,
+                           n_md=2, n_chains=3)
+        try:
+            sim.set_state(psi, next_traj=0)
+            sim.trajectories(1, 3)  # S0 in the record is the action of the set state
+            rec = sim.records()
+        finally:
+            sim.close()
+        for c, beta in enumerate((0.3, 0.44, 0.6)):
+            model = oracle.Model(dim=2, L=(L, L), beta=beta, h=0.07)
+            assert abs(rec[c, 4] - oracle.action(model, psi[c])) <= 1e-6, (scale, c)
