@@ -40,7 +40,7 @@ METRIC = "leapfrog site-steps/s chosen vs plain form, same GPU; %roofline; serve
 UNIT = "site-steps/s"
 LS = (256, 1024)
 N_MD = 20
-EPS0 = {256: 0.04, 1024: 0.02, 64: 0.07, 128: 0.05}
+EPS0 = {256: 0.05, 1024: 0.05}
 TARGET_ACC = 0.80
 
 
@@ -196,15 +196,32 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm ----
-def tune_eps(sims, betas_per_chain, rounds, seed):
-    """Step-size tuning during equilibration only (frozen afterwards).  For a
-    second-order integrator <dH> = <dH^2>/2 grows as eps^4, and an acceptance
-    of 80% corresponds to <dH> ~ 0.128; each round rescales eps per beta
-    group by (0.128 / (<dH^2>/2))^(1/4), clamped to [1/2, 2]."""
+def hot_start(pkg, sims, seed):
+    """Start every chain in the wells psi_i = +-1 (random signs), the large-C
+    minima of Sec. 3 in these units, generated on the device."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    for L, sim in sims.items():
+        n = pkg.binding.load().ising_hmc_n_chains(sim.h) * L * L
+        psi = torch.randint(0, 2, (n,), device="cuda", generator=g, dtype=torch.int8)
+        psi = psi.to(torch.float32).mul_(2.0).sub_(1.0)
+        torch.cuda.synchronize()
+        pkg.ising_hmc_set_state_native(sim.h, psi.data_ptr(), 0)
+        del psi
+
+
+def tune_eps(sims, betas_per_chain, rounds, seed, therm=4):
+    """Step-size tuning during equilibration only (frozen afterwards).  After
+    `therm` trajectories, each round rescales eps per beta group by
+    (0.128 / (<dH^2>/2))^(1/4), clamped to [1/2, 2]: for a second-order
+    integrator <dH> = <dH^2>/2 grows as eps^4, and 80% acceptance corresponds
+    to <dH> ~ 0.128."""
     target = 0.128
     ub = np.unique(betas_per_chain)
     for L, sim in sims.items():
-        eps = np.full(len(betas_per_chain), EPS0.get(L, 0.02))
+        eps = np.full(len(betas_per_chain), EPS0.get(L, 0.05))
+        sim.trajectories(therm, seed + 999)
         for r in range(rounds):
             sim.trajectories(1, seed + 1000 + r)
             dH = sim.records()[:, 0]
@@ -236,6 +253,7 @@ def run_ours(args):
                                n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
                                stream=stream.cuda_stream)
     seed = 1234 + 7919 * rank
+    hot_start(pkg, sims, seed)
     tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
         sims[L].reset_sums()

@@ -204,6 +204,18 @@ int64_t ising_hmc_launch_count(const ising_hmc_t *h);
 /* Synchronise the handle's stream; ETIMEOUT if a device wait gave up. */
 ising_status ising_hmc_sync(ising_hmc_t *h);
 
+/* Self-test of device functions the trajectories rely on (no model state;
+ * host buffers; synchronous):
+ *   which = ISING_SELFTEST_TANH: out[i] = tanh(in[i]) for FP32 in/out, the
+ *     force's tanh (Sec. 3 equations of motion), absolute error below 3e-7;
+ *   which = ISING_SELFTEST_LOG1PEXP: out[i] = log(1 + exp(-in[i])) for FP64
+ *     in/out with in[i] >= 0, the double-float evaluation inside the FP32
+ *     form's action log 2cosh x = |x| + log(1 + exp(-2|x|)), absolute error
+ *     below 1e-14.
+ * Errors: EINVAL (unknown which, n < 0, null buffers), ENOMEM, ECUDA. */
+enum { ISING_SELFTEST_TANH = 0, ISING_SELFTEST_LOG1PEXP = 1 };
+ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n);
+
 void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);

@@ -89,6 +89,7 @@ def load(path: str | None = None):
         "ising_hmc_estimate_bytes": (c_int64, [P]),
         "ising_hmc_launch_count": (c_int64, [P]),
         "ising_hmc_sync": (c_int, [P]),
+        "ising_hmc_selftest": (c_int, [c_int, P, P, c_int64]),
         "ising_hmc_destroy": (None, [P]),
         "ising_hmc_last_error": (c_char_p, [P]),
         "ising_hmc_last_create_error": (c_char_p, []),
@@ -283,6 +284,18 @@ def ising_hmc_launch_count(h) -> int:
 
 def ising_hmc_sync(h):
     _check(h, load().ising_hmc_sync(h))
+
+
+ISING_SELFTEST_TANH, ISING_SELFTEST_LOG1PEXP = 0, 1
+
+
+def ising_hmc_selftest(which, x) -> np.ndarray:
+    """Evaluate a device function on host data (see the header)."""
+    dt = np.float32 if which == ISING_SELFTEST_TANH else np.float64
+    xin = np.ascontiguousarray(x, dtype=dt)
+    out = np.zeros_like(xin)
+    _check(None, load().ising_hmc_selftest(which, xin.ctypes.data, out.ctypes.data, xin.size))
+    return out
 
 
 def ising_hmc_destroy(h):

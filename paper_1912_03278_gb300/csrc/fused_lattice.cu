@@ -6,13 +6,20 @@
 //   a = A psi,  u = tanh(a + h') - psi,  F = A u,   p += kick*eps*F,
 //   psi' = psi + drift*eps*p            (the symplectic integrator's schedule)
 // The CTA streams its chain plane by plane (plane = row in 2D, xy-slab in 3D)
-// through shared-memory rings: psi planes arrive by cp.async D planes ahead,
-// u(z+1) is computed from psi(z..z+2), then F(z) from u(z-1..z+1).  Every
-// site's psi and p cross HBM once per force evaluation: 16 B per site-step.
-// The last pass of a trajectory also evaluates the FP64 action
-//   S = sum_i 1/2 psi_i a_i - log 2cosh(a_i + h'_i)   (a in FP64)
-// and the Sec. 4 estimators; the CTA then takes the Metropolis decision
-// (Sec. 3) itself, so a launch can run many trajectories back to back.
+// through shared-memory rings: psi and p planes arrive by cp.async D planes
+// ahead, u(z+1) is computed from psi(z..z+2), then F(z) from u(z-1..z+1).
+// Every site's psi and p cross HBM once per force evaluation: 16 B per
+// site-step.  The last pass of a trajectory also evaluates the action
+//   S = sum_i 1/2 psi_i a_i - log 2cosh(a_i + h'_i)
+// to FP64 accuracy in double-float arithmetic, the kinetic energies and the
+// Sec. 4 estimators; the CTA then takes the Metropolis decision (Sec. 3)
+// itself, so one launch can run many trajectories back to back.
+//
+// Work layout inside a plane: a thread owns up to NVMAX vectors of VEC
+// consecutive sites, fixed for the whole launch, so every neighbour offset is
+// computed once.  x-neighbours come from the adjacent lanes by warp shuffles,
+// except across a row end (periodic wrap) or a warp edge, where they are read
+// from shared memory.
 #include <cuda_runtime.h>
 
 #include "df32.cuh"
@@ -21,6 +28,9 @@
 
 namespace ihmc {
 namespace {
+
+constexpr int NVMAX = 4;
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -34,6 +44,19 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// tanh x = 1 - 2/(1 + e^{2x}) on |x| with the sign restored: e^{2|x|} from
+// the hardware exp2, 1/(1+e) from the hardware reciprocal refined by one
+// Newton step.  Absolute error below 3e-7 for all x (see the self-test).
+__device__ __forceinline__ float tanh_f(float x) {
+    const float ax = fminf(fabsf(x), 20.0f);
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(ax * 2.8853900817779268f));  // 2 log2(e)
+    const float d = e + 1.0f;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    r = fmaf(fmaf(-d, r, 1.0f), r, r);
+    return copysignf(fmaf(-2.0f, r, 1.0f), x);
 }
 
 template <int VEC>
@@ -63,64 +86,101 @@ __device__ __forceinline__ void stv(float *p, const Vec<VEC> &r) {
     }
 }
 
-// Sum of the nearest neighbours of the VEC sites starting at plane offset e0,
-// using the current plane pc (in-plane neighbours) and the planes before and
-// after (pm, pq; out-of-plane neighbours, dim >= 2).  Also returns the centre.
+// One thread's vectors in a plane: plane offset e0 and column x0 of the first
+// site; loads of inactive slots use the last vector (in bounds), stores skip.
+struct Slots {
+    int e0[NVMAX];
+    int x0[NVMAX];
+    bool valid[NVMAX];
+    int nwarp;   // number of k with any active lane in this warp
+};
+
 template <int VEC>
-__device__ __forceinline__ void neighbour_sum(const Geometry &g, const float *pm, const float *pc,
-                                              const float *pq, int e0, Vec<VEC> &c,
-                                              Vec<VEC> &nb) {
-    const int x0 = e0 % g.X;
-    const int rowbase = e0 - x0;
-    c = ldv<VEC>(pc + e0);
-    const float left = pc[rowbase + (x0 == 0 ? g.X - 1 : x0 - 1)];
-    const float right = pc[rowbase + (x0 + VEC == g.X ? 0 : x0 + VEC)];
+__device__ __forceinline__ Slots make_slots(const Geometry &g) {
+    Slots s;
+    const int nvec = g.P / VEC;
+    const int nt = blockDim.x;
+    const int wbase = threadIdx.x & ~31;
+    s.nwarp = 0;
+#pragma unroll
+    for (int k = 0; k < NVMAX; ++k) {
+        const int v = threadIdx.x + k * nt;
+        s.valid[k] = v < nvec;
+        const int vc = v < nvec ? v : nvec - 1;
+        s.e0[k] = vc * VEC;
+        s.x0[k] = (vc * VEC) % g.X;
+        if (wbase + k * nt < nvec) s.nwarp = k + 1;
+    }
+    return s;
+}
+
+// Neighbour sum of the VEC sites at (e0, x0) of plane pc, with planes pm/pq
+// before/after (dim >= 2).  The centre values are returned in c and the
+// individual neighbour values in the arrays (for the exact df sum).
+template <int DIM, int VEC>
+struct Nbr {
+    Vec<VEC> c, nb;
+    float lw, rx;           // x-neighbours of the first and last site
+    Vec<VEC> ym, yp, zm, zp;
+};
+
+template <int DIM, int VEC>
+__device__ __forceinline__ void gather(const Geometry &g, const float *pm, const float *pc,
+                                       const float *pq, int e0, int x0, Nbr<DIM, VEC> &n) {
+    const int X = g.X;
+    n.c = ldv<VEC>(pc + e0);
+    const int lidx = (x0 == 0) ? e0 + X - 1 : e0 - 1;
+    const int ridx = (x0 + VEC == X) ? e0 + VEC - X : e0 + VEC;
+    if constexpr (VEC == 4) {
+        const int lane = threadIdx.x & 31;
+        float lw = __shfl_up_sync(FULL, n.c.v[3], 1);
+        float rx = __shfl_down_sync(FULL, n.c.v[0], 1);
+        if (lane == 0 || x0 == 0) lw = pc[lidx];
+        if (lane == 31 || x0 + VEC == X) rx = pc[ridx];
+        n.lw = lw;
+        n.rx = rx;
+    } else {
+        n.lw = pc[lidx];
+        n.rx = pc[ridx];
+    }
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-        const float l = (k == 0) ? left : c.v[k - 1];
-        const float r = (k == VEC - 1) ? right : c.v[k + 1];
-        nb.v[k] = l + r;
+        const float l = (k == 0) ? n.lw : n.c.v[k - 1];
+        const float r = (k == VEC - 1) ? n.rx : n.c.v[k + 1];
+        n.nb.v[k] = l + r;
     }
-    if (g.dim == 3) {
-        const int y = rowbase / g.X;
-        const int ym = (y == 0 ? g.Y - 1 : y - 1) * g.X + x0;
-        const int yp = (y == g.Y - 1 ? 0 : y + 1) * g.X + x0;
-        const Vec<VEC> a = ldv<VEC>(pc + ym), b = ldv<VEC>(pc + yp);
+    if constexpr (DIM == 3) {
+        const int P = g.P;
+        const int ym = (e0 < X) ? e0 + P - X : e0 - X;
+        const int yp = (e0 + X >= P) ? e0 + X - P : e0 + X;
+        n.ym = ldv<VEC>(pc + ym);
+        n.yp = ldv<VEC>(pc + yp);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) nb.v[k] += a.v[k] + b.v[k];
+        for (int k = 0; k < VEC; ++k) n.nb.v[k] += n.ym.v[k] + n.yp.v[k];
     }
-    if (g.dim >= 2) {
-        const Vec<VEC> a = ldv<VEC>(pm + e0), b = ldv<VEC>(pq + e0);
+    if constexpr (DIM >= 2) {
+        n.zm = ldv<VEC>(pm + e0);
+        n.zp = ldv<VEC>(pq + e0);
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) nb.v[k] += a.v[k] + b.v[k];
+        for (int k = 0; k < VEC; ++k) n.nb.v[k] += n.zm.v[k] + n.zp.v[k];
     }
 }
 
-// The same neighbour sum exactly, as a double-float (TwoSum chain), for the
-// FP64-accurate action.
-template <int VEC>
-__device__ __forceinline__ void neighbour_sum_df(const Geometry &g, const float *pm,
-                                                 const float *pc, const float *pq, int e0,
-                                                 f2 (&nb)[VEC]) {
-    const int x0 = e0 % g.X;
-    const int rowbase = e0 - x0;
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        const int x = x0 + k;
-        const int l = rowbase + (x == 0 ? g.X - 1 : x - 1);
-        const int r = rowbase + (x == g.X - 1 ? 0 : x + 1);
-        f2 s = two_sum(pc[l], pc[r]);
-        if (g.dim == 3) {
-            const int y = rowbase / g.X;
-            s = df_add_f(s, pc[(y == 0 ? g.Y - 1 : y - 1) * g.X + x]);
-            s = df_add_f(s, pc[(y == g.Y - 1 ? 0 : y + 1) * g.X + x]);
-        }
-        if (g.dim >= 2) {
-            s = df_add_f(s, pm[e0 + k]);
-            s = df_add_f(s, pq[e0 + k]);
-        }
-        nb[k] = s;
+// Exact neighbour sum of site k as a double-float (TwoSum chain).
+template <int DIM, int VEC>
+__device__ __forceinline__ f2 exact_nb(const Nbr<DIM, VEC> &n, int k) {
+    const float l = (k == 0) ? n.lw : n.c.v[k - 1];
+    const float r = (k == VEC - 1) ? n.rx : n.c.v[k + 1];
+    f2 s = two_sum(l, r);
+    if constexpr (DIM == 3) {
+        s = df_add_f(s, n.ym.v[k]);
+        s = df_add_f(s, n.yp.v[k]);
     }
+    if constexpr (DIM >= 2) {
+        s = df_add_f(s, n.zm.v[k]);
+        s = df_add_f(s, n.zp.v[k]);
+    }
+    return s;
 }
 
 // Per-thread accumulators of one trajectory, double-float (converted to FP64
@@ -149,9 +209,9 @@ __device__ __forceinline__ float *sel3(const FusedArgs &A, int i) {
     return i == 0 ? A.psi[0] : (i == 1 ? A.psi[1] : A.psi[2]);
 }
 
-template <int VEC, int D>
+template <int DIM, int VEC, int D>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
-                         uint32_t traj, float *smem, Acc &acc) {
+                         uint32_t traj, const Slots &sl, float *smem, Acc &acc) {
     constexpr int R = D + 4;   // psi ring slots
     constexpr int RP = D + 2;  // p ring slots
     const Geometry &g = A.g;
@@ -163,27 +223,28 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     const float *__restrict__ gsrc = sel3(A, pc.src) + cbase;
     float *__restrict__ gdst = sel3(A, pc.dst) + cbase;
     float *__restrict__ gp = A.p + cbase;
-    const int z0 = 0, z1 = g.nplanes;
+    const int nz = g.nplanes;
     const int nvec = P / VEC;
     const int tid = threadIdx.x, nt = blockDim.x;
     const bool load_p = pc.force && !pc.first;
 
+    // copy group s: psi plane s-2 (periodic) and p plane s-4
     auto issue = [&](int s) {
-        const int zpsi = z0 - 2 + s;
-        if (zpsi <= z1 + 1) {
-            const int zw = ((zpsi % g.nplanes) + g.nplanes) % g.nplanes;
+        const int zpsi = s - 2;
+        if (zpsi <= nz + 1) {
+            const int zw = zpsi < 0 ? zpsi + nz : (zpsi >= nz ? zpsi - nz : zpsi);
             const float *src = gsrc + (int64_t)zw * P;
-            float *dst = psi_ring + (s % R) * P;
+            float *dst = psi_ring + (unsigned)s % R * P;
             if constexpr (VEC == 4) {
                 for (int v = tid; v < nvec; v += nt) cp_async16(dst + 4 * v, src + 4 * v);
             } else {
                 for (int v = tid; v < P; v += nt) cp_async4(dst + v, src + v);
             }
         }
-        const int zp = z0 - 4 + s;
-        if (load_p && zp >= z0 && zp < z1) {
+        const int zp = s - 4;
+        if (load_p && zp >= 0 && zp < nz) {
             const float *src = gp + (int64_t)zp * P;
-            float *dst = p_ring + (s % RP) * P;
+            float *dst = p_ring + (unsigned)s % RP * P;
             if constexpr (VEC == 4) {
                 for (int v = tid; v < nvec; v += nt) cp_async16(dst + 4 * v, src + 4 * v);
             } else {
@@ -192,8 +253,9 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         }
         cp_commit();
     };
-    auto psi_slot = [&](int z) -> const float * { return psi_ring + ((z - z0 + 2) % R) * P; };
-    auto u_slot = [&](int z) -> float * { return u_ring + ((z - z0 + 3) % 3) * P; };
+    // ring slot of psi plane z (z >= -2) and u plane z (z >= -1)
+    auto psi_slot = [&](int z) -> const float * { return psi_ring + (unsigned)(z + 2) % R * P; };
+    auto u_slot = [&](int z) -> float * { return u_ring + (unsigned)(z + 3) % 3 * P; };
 
     for (int s = 0; s <= D + 2; ++s) issue(s);
     int s_next = D + 3;
@@ -202,7 +264,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     const f2 C2 = df_from_double(prm.C), bJ2 = df_from_double(prm.bJ);
     const f2 hp2 = df_from_double(prm.hp), beta2 = df_from_double(prm.beta);
 
-    for (int it = z0 - 1; it <= z1; ++it) {
+    for (int it = -1; it <= nz; ++it) {
         cp_wait<D>();
         __syncthreads();
         issue(s_next++);
@@ -210,30 +272,33 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         {
             const float *pm = psi_slot(it - 1), *pcen = psi_slot(it), *pq = psi_slot(it + 1);
             float *uo = u_slot(it);
-            const bool act = pc.action && it >= z0 && it < z1;
-            const int zw = ((it % g.nplanes) + g.nplanes) % g.nplanes;
-            for (int v = tid; v < nvec; v += nt) {
-                const int e0 = v * VEC;
-                Vec<VEC> c, nb;
-                neighbour_sum<VEC>(g, pm, pcen, pq, e0, c, nb);
-                Vec<VEC> u;
+            const bool act = pc.action && it >= 0 && it < nz;
+            const int zw = it < 0 ? it + nz : (it >= nz ? it - nz : it);
+#pragma unroll
+            for (int k = 0; k < NVMAX; ++k) {
+                if (k >= sl.nwarp) break;
+                const int e0 = sl.e0[k];
+                Nbr<DIM, VEC> n;
+                gather<DIM, VEC>(g, pm, pcen, pq, e0, sl.x0[k], n);
                 float hpv[VEC];
 #pragma unroll
-                for (int k = 0; k < VEC; ++k)
-                    hpv[k] = A.h32 ? prm.betaf * A.h32[(int64_t)zw * P + e0 + k] : prm.hpf;
-                if (pc.force) {
+                for (int q = 0; q < VEC; ++q)
+                    hpv[q] = A.h32 ? prm.betaf * A.h32[(int64_t)zw * P + e0 + q] : prm.hpf;
+                Vec<VEC> t;
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) {
-                        const float a = fmaf(Cf, c.v[k], bJf * nb.v[k]);
-                        u.v[k] = tanhf(a + hpv[k]) - c.v[k];
-                    }
+                for (int q = 0; q < VEC; ++q) {
+                    const float a = fmaf(Cf, n.c.v[q], bJf * n.nb.v[q]);
+                    t.v[q] = tanh_f(pc.sign * a + hpv[q]);
+                }
+                if (pc.force && sl.valid[k]) {
+                    Vec<VEC> u;
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) u.v[q] = t.v[q] - n.c.v[q];
                     stv<VEC>(uo + e0, u);
                 }
-                if (act) {
+                if (act && sl.valid[k]) {
                     // FP64-accurate action in double-float:
                     //   S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),  x = a + h'
-                    f2 nbd[VEC];
-                    neighbour_sum_df<VEC>(g, pm, pcen, pq, e0, nbd);
                     const int64_t site0 = (int64_t)zw * P + e0;
                     float su[4];
                     if constexpr (VEC == 4) {
@@ -242,31 +307,32 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                         su[0] = w.x; su[1] = w.y; su[2] = w.z; su[3] = w.w;
                     }
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) {
-                        const float ps = pc.sign * c.v[k];
-                        const f2 hp = A.h64 ? df_mul(beta2, df_from_double(A.h64[site0 + k])) : hp2;
-                        const f2 a = df_add(df_mul_f(C2, ps), df_mul(bJ2, f2{pc.sign * nbd[k].hi,
-                                                                               pc.sign * nbd[k].lo}));
+                    for (int q = 0; q < VEC; ++q) {
+                        const float ps = pc.sign * n.c.v[q];
+                        const f2 nbd = exact_nb<DIM, VEC>(n, q);
+                        const f2 hp = A.h64 ? df_mul(beta2, df_from_double(A.h64[site0 + q])) : hp2;
+                        const f2 a = df_add(df_mul_f(C2, ps),
+                                            df_mul(bJ2, f2{pc.sign * nbd.hi, pc.sign * nbd.lo}));
                         const f2 x = df_add(a, hp);
                         const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
                         const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, A.lpe_tab);
                         f2 term = df_mul_f(a, 0.5f * ps);
                         term = df_add(term, df_neg(df_add(ax, gl)));
                         acc.S = df_add(acc.S, term);
-                        const float t = tanhf(x.hi);
-                        acc.sT = df_add_f(acc.sT, t);
-                        acc.sAT = df_add_f(acc.sAT, a.hi * t);
-                        acc.sHT = df_add_f(acc.sHT, hp.hi * t);
+                        const float tq = t.v[q];
+                        acc.sT = df_add_f(acc.sT, tq);
+                        acc.sAT = df_add_f(acc.sAT, a.hi * tq);
+                        acc.sHT = df_add_f(acc.sHT, hp.hi * tq);
                         float uu;
                         if constexpr (VEC == 4) {
-                            uu = su[k];
+                            uu = su[q];
                         } else {
-                            const float4 w = spin_u4_f32((uint32_t)((site0 + k) >> 2),
+                            const float4 w = spin_u4_f32((uint32_t)((site0 + q) >> 2),
                                                          pc.spin_traj, (uint32_t)chain, A.seed);
-                            const int q = (int)((site0 + k) & 3);
-                            uu = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
+                            const int qq = (int)((site0 + q) & 3);
+                            uu = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
                         }
-                        acc.sS += (uu < (1.0f + t) * 0.5f) ? 1 : -1;
+                        acc.sS += (uu < (1.0f + tq) * 0.5f) ? 1 : -1;
                     }
                 }
             }
@@ -274,50 +340,60 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         __syncthreads();
         // ---- F(z) = A u, kick and drift on plane z = it - 1 ----
         const int z = it - 1;
-        if (pc.force && z >= z0 && z < z1) {
+        if (pc.force && z >= 0 && z < nz) {
             const float *um = u_slot(z - 1), *uc = u_slot(z), *uq = u_slot(z + 1);
             const float *psz = psi_slot(z);
-            const float *ppz = p_ring + ((z - z0 + 4) % RP) * P;
-            for (int v = tid; v < nvec; v += nt) {
-                const int e0 = v * VEC;
-                Vec<VEC> uu, nb;
-                neighbour_sum<VEC>(g, um, uc, uq, e0, uu, nb);
-                const int64_t site0 = (int64_t)z * P + e0;
+            const float *ppz = p_ring + (unsigned)(z + 4) % RP * P;
+            float *gpz = gp + (int64_t)z * P;
+            float *gdz = gdst + (int64_t)z * P;
+#pragma unroll
+            for (int k = 0; k < NVMAX; ++k) {
+                if (k >= sl.nwarp) break;
+                const int e0 = sl.e0[k];
+                Nbr<DIM, VEC> n;
+                gather<DIM, VEC>(g, um, uc, uq, e0, sl.x0[k], n);
                 Vec<VEC> pv;
                 if (pc.first) {
+                    const int64_t site0 = (int64_t)z * P + e0;
                     if constexpr (VEC == 4) {
                         const float4 w = momenta4_f32((uint32_t)(site0 >> 2), traj,
                                                       (uint32_t)chain, A.seed);
                         pv.v[0] = w.x; pv.v[1] = w.y; pv.v[2] = w.z; pv.v[3] = w.w;
                     } else {
 #pragma unroll
-                        for (int k = 0; k < VEC; ++k) {
-                            const float4 w = momenta4_f32((uint32_t)((site0 + k) >> 2), traj,
+                        for (int q = 0; q < VEC; ++q) {
+                            const float4 w = momenta4_f32((uint32_t)((site0 + q) >> 2), traj,
                                                           (uint32_t)chain, A.seed);
-                            const int q = (int)((site0 + k) & 3);
-                            pv.v[k] = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
+                            const int qq = (int)((site0 + q) & 3);
+                            pv.v[q] = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
                         }
                     }
+                    if (sl.valid[k]) {
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) acc.K0 = df_add(acc.K0, two_prod(pv.v[k], 0.5f * pv.v[k]));
+                        for (int q = 0; q < VEC; ++q)
+                            acc.K0 = df_add(acc.K0, two_prod(pv.v[q], 0.5f * pv.v[q]));
+                    }
                 } else {
                     pv = ldv<VEC>(ppz + e0);
                 }
 #pragma unroll
-                for (int k = 0; k < VEC; ++k) {
-                    const float F = fmaf(Cf, uu.v[k], bJf * nb.v[k]);
-                    pv.v[k] = fmaf(pc.kick, F, pv.v[k]);
+                for (int q = 0; q < VEC; ++q) {
+                    const float F = fmaf(Cf, n.c.v[q], bJf * n.nb.v[q]);
+                    pv.v[q] = fmaf(pc.kick, F, pv.v[q]);
                 }
-                stv<VEC>(gp + site0, pv);
-                if (pc.last) {
+                if (sl.valid[k]) {
+                    stv<VEC>(gpz + e0, pv);
+                    if (pc.last) {
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) acc.K1 = df_add(acc.K1, two_prod(pv.v[k], 0.5f * pv.v[k]));
-                } else {
-                    const Vec<VEC> ps = ldv<VEC>(psz + e0);
-                    Vec<VEC> pn;
+                        for (int q = 0; q < VEC; ++q)
+                            acc.K1 = df_add(acc.K1, two_prod(pv.v[q], 0.5f * pv.v[q]));
+                    } else {
+                        const Vec<VEC> ps = ldv<VEC>(psz + e0);
+                        Vec<VEC> pn;
 #pragma unroll
-                    for (int k = 0; k < VEC; ++k) pn.v[k] = fmaf(pc.drift, pv.v[k], ps.v[k]);
-                    stv<VEC>(gdst + site0, pn);
+                        for (int q = 0; q < VEC; ++q) pn.v[q] = fmaf(pc.drift, pv.v[q], ps.v[q]);
+                        stv<VEC>(gdz + e0, pn);
+                    }
                 }
             }
         }
@@ -331,7 +407,16 @@ __device__ __forceinline__ int buf_loc(int start, int j) {
     return (start + ((j & 1) ? 1 : 2)) % 3;
 }
 
-template <int VEC, int D>
+__device__ __forceinline__ void set_obs(ChainState *st, const ChainParams &prm, double sT,
+                                        double sAT, double sHT, double sS, double invN) {
+    const double m = sT * invN;
+    st->obs[0] = m;
+    st->obs[1] = 0.5 * prm.C - 0.5 * sAT * invN - sHT * invN;
+    st->obs[2] = fabs(sS) * invN;
+    st->obs[3] = fabs(m);
+}
+
+template <int DIM, int VEC, int D>
 __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedule S) {
     extern __shared__ float4 smem_f4[];
     float *smem = reinterpret_cast<float *>(smem_f4);
@@ -357,21 +442,19 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
         return;
     }
 
+    const Slots sl = make_slots<VEC>(g);
+
     if (A.mode == MODE_EVAL) {
         Acc acc = acc_zero();
         const int start = st->start;
         PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, 1.0f, TRAJ_INIT};
-        run_pass<VEC, D>(A, pc, prm, chain, TRAJ_INIT, smem, acc);
+        run_pass<DIM, VEC, D>(A, pc, prm, chain, TRAJ_INIT, sl, smem, acc);
         double v[5] = {df_to_double(acc.S), df_to_double(acc.sT), df_to_double(acc.sAT),
                        df_to_double(acc.sHT), (double)acc.sS};
         block_sum<5>(v, red);
         if (threadIdx.x == 0) {
             st->S = v[0];
-            const double m = v[1] * invN;
-            st->obs[0] = m;
-            st->obs[1] = 0.5 * prm.C - 0.5 * v[2] * invN - v[3] * invN;
-            st->obs[2] = fabs(v[4]) * invN;
-            st->obs[3] = fabs(m);
+            set_obs(st, prm, v[1], v[2], v[3], v[4], invN);
             st->prop = start;
         }
         return;
@@ -393,7 +476,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             pc.action = pc.last;
             pc.sign = 1.0f;
             pc.spin_traj = traj;
-            run_pass<VEC, D>(A, pc, prm, chain, traj, smem, acc);
+            run_pass<DIM, VEC, D>(A, pc, prm, chain, traj, sl, smem, acc);
         }
         double v[7] = {df_to_double(acc.K0), df_to_double(acc.K1), df_to_double(acc.S),
                        df_to_double(acc.sT), df_to_double(acc.sAT), df_to_double(acc.sHT),
@@ -417,11 +500,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             if (accd) {
                 st->start = prop;
                 st->S = v[2];
-                const double m = v[3] * invN;
-                st->obs[0] = m;
-                st->obs[1] = 0.5 * prm.C - 0.5 * v[4] * invN - v[5] * invN;
-                st->obs[2] = fabs(v[6]) * invN;
-                st->obs[3] = fabs(m);
+                set_obs(st, prm, v[3], v[4], v[5], v[6], invN);
             }
             bcast[0] = accd ? prop : start;
         }
@@ -432,7 +511,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
         if (A.flip_every > 0 && ((traj + 1) % (uint32_t)A.flip_every) == 0) {
             Acc fa = acc_zero();
             PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, -1.0f, traj};
-            run_pass<VEC, D>(A, pc, prm, chain, traj, smem, fa);
+            run_pass<DIM, VEC, D>(A, pc, prm, chain, traj, sl, smem, fa);
             double w[5] = {df_to_double(fa.S), df_to_double(fa.sT), df_to_double(fa.sAT),
                            df_to_double(fa.sHT), (double)fa.sS};
             block_sum<5>(w, red);
@@ -441,11 +520,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
                 const bool fl = lu < -(w[0] - st->S);
                 if (fl) {
                     st->S = w[0];
-                    const double m = w[1] * invN;
-                    st->obs[0] = m;
-                    st->obs[1] = 0.5 * prm.C - 0.5 * w[2] * invN - w[3] * invN;
-                    st->obs[2] = fabs(w[4]) * invN;
-                    st->obs[3] = fabs(m);
+                    set_obs(st, prm, w[1], w[2], w[3], w[4], invN);
                     st->rec[ISING_REC_FLIPPED] = 1.0;
                 }
                 bcast[1] = fl ? 1 : 0;
@@ -464,43 +539,64 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             __syncthreads();
         }
         // ---- measurement: a repeated configuration repeats its measurement ----
-        if (threadIdx.x == 0) {
-            if ((int64_t)traj >= (int64_t)A.n_therm) {
-                double *sm = st->sums;
-                const double dH = st->rec[ISING_REC_DH];
-                sm[ISING_SUM_NMEAS] += 1.0;
-                sm[ISING_SUM_NACC] += st->rec[ISING_REC_ACCEPTED];
-                sm[ISING_SUM_M] += st->obs[0];
-                sm[ISING_SUM_M2] += st->obs[0] * st->obs[0];
-                sm[ISING_SUM_E] += st->obs[1];
-                sm[ISING_SUM_E2] += st->obs[1] * st->obs[1];
-                sm[ISING_SUM_ABSM] += st->obs[2];
-                sm[ISING_SUM_ABSM2] += st->obs[2] * st->obs[2];
-                sm[ISING_SUM_DH] += dH;
-                sm[ISING_SUM_EXPMDH] += exp(-dH);
-            }
+        if (threadIdx.x == 0 && (int64_t)traj >= (int64_t)A.n_therm) {
+            double *sm = st->sums;
+            const double dH = st->rec[ISING_REC_DH];
+            sm[ISING_SUM_NMEAS] += 1.0;
+            sm[ISING_SUM_NACC] += st->rec[ISING_REC_ACCEPTED];
+            sm[ISING_SUM_M] += st->obs[0];
+            sm[ISING_SUM_M2] += st->obs[0] * st->obs[0];
+            sm[ISING_SUM_E] += st->obs[1];
+            sm[ISING_SUM_E2] += st->obs[1] * st->obs[1];
+            sm[ISING_SUM_ABSM] += st->obs[2];
+            sm[ISING_SUM_ABSM2] += st->obs[2] * st->obs[2];
+            sm[ISING_SUM_DH] += dH;
+            sm[ISING_SUM_EXPMDH] += exp(-dH);
         }
         __syncthreads();
     }
 }
 
-template <int VEC, int D>
-cudaError_t launch_vd(const FusedArgs &a, const Schedule &s, int threads, cudaStream_t st) {
+template <int DIM, int VEC, int D>
+cudaError_t launch_kernel(const FusedArgs &a, const Schedule &s, int threads, cudaStream_t st) {
     const int smem = fused_lattice_smem_bytes(a.g, D, VEC);
-    static bool configured[2] = {false, false};
-    auto kern = fused_lattice_kernel<VEC, D>;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!configured[dev & 1]) {
+    static bool configured = false;
+    auto kern = fused_lattice_kernel<DIM, VEC, D>;
+    if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
         if (e != cudaSuccess) return e;
-        configured[dev & 1] = true;
+        configured = true;
     }
     const int grid = a.n_chains - a.chain0;
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, threads, smem, st>>>(a, s);
     return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t launch_dim(const FusedArgs &a, const Schedule &s, int threads, int depth, int vec,
+                       cudaStream_t st) {
+    if (vec == 4) {
+        if (depth >= 4) return launch_kernel<DIM, 4, 4>(a, s, threads, st);
+        return launch_kernel<DIM, 4, 2>(a, s, threads, st);
+    }
+    if (depth >= 4) return launch_kernel<DIM, 1, 4>(a, s, threads, st);
+    return launch_kernel<DIM, 1, 2>(a, s, threads, st);
+}
+
+// tanh self-test kernel
+__global__ void tanh_selftest_kernel(const float *x, float *y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = tanh_f(x[i]);
+}
+
+__global__ void log1pexp_selftest_kernel(const double *y, double *out, int64_t n,
+                                         const float4 *tab) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = df_to_double(log1pexp_neg(df_from_double(y[i]), tab));
 }
 
 }  // namespace
@@ -512,15 +608,20 @@ int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec) {
     return (int)(floats * 4 + 32 * 8 * 8 + 16);
 }
 
+// Launch shape: VEC = 4 when rows split into float4s; threads = one per vector
+// up to 256, each thread owning at most NVMAX vectors per plane; prefetch
+// depth 4 planes when the rings fit in 200 KB, else 2.  Returns VEC, or -1 if
+// the plane does not fit on chip.
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
     const int vec = (g.X % 4 == 0 && g.P % 4 == 0) ? 4 : 1;
-    int t = (g.P / vec + 31) / 32 * 32;
+    const int nvec = g.P / vec;
+    int t = (nvec + 31) / 32 * 32;
     if (t > 256) t = 256;
     if (t < 32) t = 32;
+    if ((nvec + t - 1) / t > NVMAX) return -1;
     *threads = t;
-    const int limit = 200 * 1024;
     int d = 4;
-    while (d > 1 && fused_lattice_smem_bytes(g, d, vec) > limit) d = (d == 4) ? 2 : 1;
+    if (fused_lattice_smem_bytes(g, d, vec) > 200 * 1024) d = 2;
     if (fused_lattice_smem_bytes(g, d, vec) > 227 * 1024) return -1;
     *depth = d;
     return vec;
@@ -529,14 +630,20 @@ int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
 cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
                                  int depth, cudaStream_t s) {
     const int vec = (a.g.X % 4 == 0 && a.g.P % 4 == 0) ? 4 : 1;
-    if (vec == 4) {
-        if (depth >= 4) return launch_vd<4, 4>(a, sched, threads, s);
-        if (depth >= 2) return launch_vd<4, 2>(a, sched, threads, s);
-        return launch_vd<4, 1>(a, sched, threads, s);
-    }
-    if (depth >= 4) return launch_vd<1, 4>(a, sched, threads, s);
-    if (depth >= 2) return launch_vd<1, 2>(a, sched, threads, s);
-    return launch_vd<1, 1>(a, sched, threads, s);
+    if (a.g.dim == 3) return launch_dim<3>(a, sched, threads, depth, vec, s);
+    if (a.g.dim == 2) return launch_dim<2>(a, sched, threads, depth, vec, s);
+    return launch_dim<1>(a, sched, threads, depth, vec, s);
+}
+
+cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s) {
+    tanh_selftest_kernel<<<148, 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_log1pexp_selftest(const double *y, double *out, int64_t n, const float4 *tab,
+                                     cudaStream_t s) {
+    log1pexp_selftest_kernel<<<148, 256, 0, s>>>(y, out, n, tab);
+    return cudaGetLastError();
 }
 
 }  // namespace ihmc

@@ -79,6 +79,10 @@ cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int 
 int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec);
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
 
+cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s);
+cudaError_t launch_log1pexp_selftest(const double *y, double *out, int64_t n, const float4 *tab,
+                                     cudaStream_t s);
+
 // Host construction of the log(1 + exp(-y)) Taylor table (3 float4 per node).
 void build_log1pexp_table(float *out /* 12 * (LOG1PEXP_K + 1) floats */);
 constexpr int LOG1PEXP_NODES = 36 * 16 + 1;

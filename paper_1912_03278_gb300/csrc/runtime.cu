@@ -815,6 +815,44 @@ int ising_hmc_n_chains(const ising_hmc_t *h) { return h ? h->n_chains : -1; }
 int64_t ising_hmc_device_bytes(const ising_hmc_t *h) { return h ? h->bytes : -1; }
 int64_t ising_hmc_launch_count(const ising_hmc_t *h) { return h ? h->launches : -1; }
 
+ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n) {
+    g_create_err[0] = 0;
+    if (!in || !out || n < 0) return fail(nullptr, ISING_EINVAL, "selftest: bad arguments");
+    if (n == 0) return ISING_OK;
+    const size_t el = which == ISING_SELFTEST_TANH ? sizeof(float) : sizeof(double);
+    if (which != ISING_SELFTEST_TANH && which != ISING_SELFTEST_LOG1PEXP)
+        return fail(nullptr, ISING_EINVAL, "selftest: unknown function %d", which);
+    void *din = nullptr, *dout = nullptr;
+    float *dtab = nullptr;
+    ising_status st = ISING_OK;
+    if (cudaMalloc(&din, n * el) != cudaSuccess || cudaMalloc(&dout, n * el) != cudaSuccess) {
+        st = fail(nullptr, ISING_ENOMEM, "selftest: device allocation failed");
+    } else if (cudaMemcpy(din, in, n * el, cudaMemcpyHostToDevice) != cudaSuccess) {
+        st = fail(nullptr, ISING_ECUDA, "selftest: upload failed");
+    } else {
+        cudaError_t e;
+        if (which == ISING_SELFTEST_TANH) {
+            e = launch_tanh_selftest((const float *)din, (float *)dout, n, 0);
+        } else {
+            std::vector<float> tab(12 * LOG1PEXP_NODES);
+            build_log1pexp_table(tab.data());
+            e = cudaMalloc(&dtab, tab.size() * sizeof(float));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(dtab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = launch_log1pexp_selftest((const double *)din, (double *)dout, n,
+                                             reinterpret_cast<const float4 *>(dtab), 0);
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(out, dout, n * el, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = fail(nullptr, ISING_ECUDA, "selftest: %s", cudaGetErrorString(e));
+    }
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    if (dtab) cudaFree(dtab);
+    return st;
+}
+
 void ising_hmc_destroy(ising_hmc_t *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
