@@ -9,5 +9,5 @@ from .binding import IsingHMC, IsingError, load, make_config  # noqa: F401
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from .builder import build as _build
     return _build(force=force)

@@ -63,7 +63,7 @@ def load(path: str | None = None):
         return _lib
     p = path or LIB_PATH
     if not os.path.exists(p):
-        raise OSError("libising_hmc.so not built (%s); run paper_1912_03278_gb300.build" % p)
+        raise OSError("libising_hmc.so not built (%s); run paper_1912_03278_gb300.builder" % p)
     lib = ctypes.CDLL(p)
     P = c_void_p
     sig = {
