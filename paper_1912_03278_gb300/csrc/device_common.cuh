@@ -51,12 +51,16 @@ __device__ __forceinline__ double u52(uint32_t a, uint32_t b) {
 }
 
 // Box-Muller (1958): r = sqrt(-2 ln u1), z0 = r cos(2 pi u2), z1 = r sin(2 pi u2).
+// FP32 form: the angle 2 pi u2 - pi lies in [-pi, pi), where the hardware
+// sine and cosine are accurate to ~4e-7 absolute; cos(t + pi) = -cos t and
+// sin(t + pi) = -sin t restore the angle 2 pi u2.
 __device__ __forceinline__ void box_muller_f32(float u1, float u2, float &z0, float &z1) {
     const float r = sqrtf(-2.0f * logf(u1));
+    const float th = fmaf(6.2831853071795865f, u2, -3.1415926535897932f);
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(th, &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 __device__ __forceinline__ void box_muller_f64(double u1, double u2, double &z0, double &z1) {
     const double r = sqrt(-2.0 * log(u1));

@@ -17,9 +17,7 @@
 //
 // Work layout inside a plane: a thread owns up to NVMAX vectors of VEC
 // consecutive sites, fixed for the whole launch, so every neighbour offset is
-// computed once.  x-neighbours come from the adjacent lanes by warp shuffles,
-// except across a row end (periodic wrap) or a warp edge, where they are read
-// from shared memory.
+// computed once.
 #include <cuda_runtime.h>
 
 #include "df32.cuh"
@@ -30,7 +28,6 @@ namespace ihmc {
 namespace {
 
 constexpr int NVMAX = 4;
-constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -129,20 +126,12 @@ __device__ __forceinline__ void gather(const Geometry &g, const float *pm, const
                                        const float *pq, int e0, int x0, Nbr<DIM, VEC> &n) {
     const int X = g.X;
     n.c = ldv<VEC>(pc + e0);
+    // x-neighbours of the end sites straight from shared memory (measured
+    // faster than lane shuffles with the wrap fix-ups)
     const int lidx = (x0 == 0) ? e0 + X - 1 : e0 - 1;
     const int ridx = (x0 + VEC == X) ? e0 + VEC - X : e0 + VEC;
-    if constexpr (VEC == 4) {
-        const int lane = threadIdx.x & 31;
-        float lw = __shfl_up_sync(FULL, n.c.v[3], 1);
-        float rx = __shfl_down_sync(FULL, n.c.v[0], 1);
-        if (lane == 0 || x0 == 0) lw = pc[lidx];
-        if (lane == 31 || x0 + VEC == X) rx = pc[ridx];
-        n.lw = lw;
-        n.rx = rx;
-    } else {
-        n.lw = pc[lidx];
-        n.rx = pc[ridx];
-    }
+    n.lw = pc[lidx];
+    n.rx = pc[ridx];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         const float l = (k == 0) ? n.lw : n.c.v[k - 1];
@@ -183,17 +172,43 @@ __device__ __forceinline__ f2 exact_nb(const Nbr<DIM, VEC> &n, int k) {
     return s;
 }
 
-// Per-thread accumulators of one trajectory, double-float (converted to FP64
-// once, for the block reduction).
+// Per-thread accumulators of one trajectory.  Energies: the high words are
+// summed as double-floats, the low words of the addends in a separate FP32
+// sum (their magnitude is ~2^-24 of the terms).  Estimators: Kahan FP32 sums.
 struct Acc {
-    f2 K0, K1, S, sT, sAT, sHT;
+    f2 K0, K1, S;
+    float K0lo, K1lo, Slo;
+    float sT, cT, sAT, cAT, sHT, cHT;
     int sS;
 };
 
 __device__ __forceinline__ Acc acc_zero() {
-    const f2 z{0.0f, 0.0f};
-    return Acc{z, z, z, z, z, z, 0};
+    Acc a;
+    a.K0 = a.K1 = a.S = f2{0.0f, 0.0f};
+    a.K0lo = a.K1lo = a.Slo = 0.0f;
+    a.sT = a.cT = a.sAT = a.cAT = a.sHT = a.cHT = 0.0f;
+    a.sS = 0;
+    return a;
 }
+
+__device__ __forceinline__ void acc_add(f2 &hi, float &lo, f2 v) {
+    hi = df_add_f(hi, v.hi);
+    lo = __fadd_rn(lo, v.lo);
+}
+
+// Kahan (1965) compensated summation.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+__device__ __forceinline__ double acc_val(f2 hi, float lo) {
+    return df_to_double(hi) + (double)lo;
+}
+
+__device__ __forceinline__ double kahan_val(float s, float c) { return (double)s - (double)c; }
 
 struct PassCfg {
     int src, dst;
@@ -263,6 +278,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     const float Cf = prm.Cf, bJf = prm.bJf;
     const f2 C2 = df_from_double(prm.C), bJ2 = df_from_double(prm.bJ);
     const f2 hp2 = df_from_double(prm.hp), beta2 = df_from_double(prm.beta);
+    const bool hzero = prm.hp == 0.0;
 
     for (int it = -1; it <= nz; ++it) {
         cp_wait<D>();
@@ -283,7 +299,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 float hpv[VEC];
 #pragma unroll
                 for (int q = 0; q < VEC; ++q)
-                    hpv[q] = A.h32 ? prm.betaf * A.h32[(int64_t)zw * P + e0 + q] : prm.hpf;
+                    hpv[q] = A.hdf ? prm.betaf * A.hdf[(int64_t)zw * P + e0 + q].x : prm.hpf;
                 Vec<VEC> t;
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
@@ -310,19 +326,28 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     for (int q = 0; q < VEC; ++q) {
                         const float ps = pc.sign * n.c.v[q];
                         const f2 nbd = exact_nb<DIM, VEC>(n, q);
-                        const f2 hp = A.h64 ? df_mul(beta2, df_from_double(A.h64[site0 + q])) : hp2;
                         const f2 a = df_add(df_mul_f(C2, ps),
                                             df_mul(bJ2, f2{pc.sign * nbd.hi, pc.sign * nbd.lo}));
-                        const f2 x = df_add(a, hp);
+                        f2 x = a;
+                        float hq = 0.0f;
+                        if (A.hdf) {
+                            const float2 hh = A.hdf[site0 + q];
+                            const f2 hp = df_mul(beta2, f2{hh.x, hh.y});
+                            x = df_add(a, hp);
+                            hq = hp.hi;
+                        } else if (!hzero) {
+                            x = df_add(a, hp2);
+                            hq = hp2.hi;
+                        }
                         const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
                         const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, A.lpe_tab);
-                        f2 term = df_mul_f(a, 0.5f * ps);
-                        term = df_add(term, df_neg(df_add(ax, gl)));
-                        acc.S = df_add(acc.S, term);
+                        acc_add(acc.S, acc.Slo, df_mul_f(a, 0.5f * ps));
+                        acc_add(acc.S, acc.Slo, df_neg(ax));
+                        acc_add(acc.S, acc.Slo, df_neg(gl));
                         const float tq = t.v[q];
-                        acc.sT = df_add_f(acc.sT, tq);
-                        acc.sAT = df_add_f(acc.sAT, a.hi * tq);
-                        acc.sHT = df_add_f(acc.sHT, hp.hi * tq);
+                        kahan_add(acc.sT, acc.cT, tq);
+                        kahan_add(acc.sAT, acc.cAT, a.hi * tq);
+                        kahan_add(acc.sHT, acc.cHT, hq * tq);
                         float uu;
                         if constexpr (VEC == 4) {
                             uu = su[q];
@@ -371,7 +396,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     if (sl.valid[k]) {
 #pragma unroll
                         for (int q = 0; q < VEC; ++q)
-                            acc.K0 = df_add(acc.K0, two_prod(pv.v[q], 0.5f * pv.v[q]));
+                            acc_add(acc.K0, acc.K0lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
                     }
                 } else {
                     pv = ldv<VEC>(ppz + e0);
@@ -386,7 +411,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     if (pc.last) {
 #pragma unroll
                         for (int q = 0; q < VEC; ++q)
-                            acc.K1 = df_add(acc.K1, two_prod(pv.v[q], 0.5f * pv.v[q]));
+                            acc_add(acc.K1, acc.K1lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
                     } else {
                         const Vec<VEC> ps = ldv<VEC>(psz + e0);
                         Vec<VEC> pn;
@@ -449,8 +474,8 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
         const int start = st->start;
         PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, 1.0f, TRAJ_INIT};
         run_pass<DIM, VEC, D>(A, pc, prm, chain, TRAJ_INIT, sl, smem, acc);
-        double v[5] = {df_to_double(acc.S), df_to_double(acc.sT), df_to_double(acc.sAT),
-                       df_to_double(acc.sHT), (double)acc.sS};
+        double v[5] = {acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
+                       kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
         block_sum<5>(v, red);
         if (threadIdx.x == 0) {
             st->S = v[0];
@@ -478,9 +503,9 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             pc.spin_traj = traj;
             run_pass<DIM, VEC, D>(A, pc, prm, chain, traj, sl, smem, acc);
         }
-        double v[7] = {df_to_double(acc.K0), df_to_double(acc.K1), df_to_double(acc.S),
-                       df_to_double(acc.sT), df_to_double(acc.sAT), df_to_double(acc.sHT),
-                       (double)acc.sS};
+        double v[7] = {acc_val(acc.K0, acc.K0lo), acc_val(acc.K1, acc.K1lo),
+                       acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
+                       kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
         block_sum<7>(v, red);
         const int prop = buf_loc(start, S.n_pass - 1);
         if (threadIdx.x == 0) {
@@ -512,8 +537,8 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             Acc fa = acc_zero();
             PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, -1.0f, traj};
             run_pass<DIM, VEC, D>(A, pc, prm, chain, traj, sl, smem, fa);
-            double w[5] = {df_to_double(fa.S), df_to_double(fa.sT), df_to_double(fa.sAT),
-                           df_to_double(fa.sHT), (double)fa.sS};
+            double w[5] = {acc_val(fa.S, fa.Slo), kahan_val(fa.sT, fa.cT),
+                           kahan_val(fa.sAT, fa.cAT), kahan_val(fa.sHT, fa.cHT), (double)fa.sS};
             block_sum<5>(w, red);
             if (threadIdx.x == 0) {
                 const double lu = accept_logu(traj, (uint32_t)chain, A.seed, PURPOSE_FLIP);

@@ -48,8 +48,7 @@ struct Geometry {
 struct FusedArgs {
     float *psi[3];           // three state buffers, chain-major
     float *p;                // momenta, chain-major
-    const float *h32;        // per-site h_i (not scaled by beta), or null
-    const double *h64;
+    const float2 *hdf;       // per-site h_i (not scaled by beta) as hi/lo floats, or null
     const float4 *lpe_tab;   // Taylor table of log(1 + exp(-y)), see df32.cuh
     const ChainParams *params;
     ChainState *state;

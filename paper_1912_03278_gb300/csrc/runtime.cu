@@ -235,7 +235,7 @@ static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_
         b += 4 * C * N * (int64_t)sizeof(float);
     }
     b += C * (int64_t)(sizeof(ChainParams) + sizeof(ChainState) + 2 * sizeof(int));
-    if (has_h) b += N * (int64_t)(sizeof(float) + sizeof(double));
+    if (has_h) b += N * (int64_t)(2 * sizeof(float) + sizeof(double));
     if (kind == ISING_KIND_DENSE) b += N * N * (int64_t)sizeof(double);
     return b;
 }
@@ -276,8 +276,7 @@ static FusedArgs fused_args(ising_hmc *h) {
     FusedArgs a{};
     for (int i = 0; i < 3; ++i) a.psi[i] = (float *)h->psi[i];
     a.p = (float *)h->p;
-    a.h32 = h->has_h ? h->d_h32 : nullptr;
-    a.h64 = h->has_h ? h->d_h64 : nullptr;
+    a.hdf = h->has_h ? reinterpret_cast<const float2 *>(h->d_h32) : nullptr;
     a.lpe_tab = reinterpret_cast<const float4 *>(h->d_lpe);
     a.params = h->d_params;
     a.state = h->d_state;
@@ -486,9 +485,13 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             return bail(fail(h, ISING_ECUDA, "table upload failed"));
     }
     if (h->has_h) {
-        std::vector<float> h32(N);
-        for (int64_t i = 0; i < N; ++i) h32[i] = (float)cfg->h[i];
-        if ((st = dalloc(h, &h->d_h32, N * sizeof(float))) != ISING_OK) return bail(st);
+        // FP32 form: h_i as a double-float pair (hi, lo)
+        std::vector<float> h32(2 * N);
+        for (int64_t i = 0; i < N; ++i) {
+            h32[2 * i] = (float)cfg->h[i];
+            h32[2 * i + 1] = (float)(cfg->h[i] - (double)h32[2 * i]);
+        }
+        if ((st = dalloc(h, &h->d_h32, 2 * N * sizeof(float))) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->d_h64, N * sizeof(double))) != ISING_OK) return bail(st);
         if (cudaMemcpy(h->d_h32, h32.data(), N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->d_h64, cfg->h, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -34,6 +34,10 @@ def test_log1pexp_double_float_accuracy():
     g = np.random.default_rng(1)
     y = np.concatenate([np.linspace(0, 40, 400_001), g.uniform(0, 60, 200_000),
                         np.array([0.0, 1 / 32, 35.999, 36.0, 36.001, 700.0])])
+    # inputs representable as a double-float (hi + lo of two FP32 numbers),
+    # which is how the action hands them to the function
+    hi = y.astype(np.float32).astype(np.float64)
+    y = hi + (y - hi).astype(np.float32).astype(np.float64)
     out = binding.ising_hmc_selftest(binding.ISING_SELFTEST_LOG1PEXP, y)
     ref = np.log1p(np.exp(-y))
     assert np.abs(out - ref).max() < 1e-14, np.abs(out - ref).max()
