@@ -211,7 +211,7 @@ ising_status ising_hmc_sync(ising_hmc_t *h);
  *   which = ISING_SELFTEST_LOG1PEXP: out[i] = log(1 + exp(-in[i])) for FP64
  *     in/out with in[i] >= 0, the double-float evaluation inside the FP32
  *     form's action log 2cosh x = |x| + log(1 + exp(-2|x|)), absolute error
- *     below 1e-14.
+ *     below 1e-13.
  * Errors: EINVAL (unknown which, n < 0, null buffers), ENOMEM, ECUDA. */
 enum { ISING_SELFTEST_TANH = 0, ISING_SELFTEST_LOG1PEXP = 1 };
 ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n);
