@@ -73,32 +73,41 @@ __device__ __forceinline__ f2 df_from_double(double x) {
 
 __device__ __forceinline__ double df_to_double(f2 a) { return (double)a.hi + (double)a.lo; }
 
-// Table of g(y) = log(1 + exp(-y)) on y_k = k/16, k = 0 .. LOG1PEXP_K, as
-// Taylor coefficients c_n = g^(n)(y_k)/n!, n = 0..7: c0, c1, c2 as double-
-// floats and c3..c7 as floats, packed into three float4 per node:
-//   {c0.hi, c0.lo, c1.hi, c1.lo}, {c2.hi, c2.lo, c3, c4}, {c5, c6, c7, 0}.
-// For y >= 36, g(y) < 2.4e-16 and is taken as exp(-y).
-constexpr int LOG1PEXP_PER_UNIT = 16;
+// Table of g(y) = log(1 + exp(-y)) on y_k = k/32, k = 0 .. LOG1PEXP_K: one
+// float4 per node {g(y_k).hi, g(y_k).lo, s.hi, s.lo} with s = 1/(1 + e^{y_k}).
+// With w = s(1-s) and v = 1-2s the derivatives are polynomials in s
+// (g' = -s, ds/dy = -w):
+//   g1 = -s, g2 = w, g3 = -w v, g4 = w(1-6w), g5 = -w v(1-12w),
+//   g6 = w(1-30w+120w^2),
+// and g(y_k + d) = sum_n g_n d^n / n!, |d| <= 1/64; the next term is below
+// 2e-17.  For y >= 36, g(y) < 2.4e-16 and is taken as exp(-y).
+constexpr int LOG1PEXP_PER_UNIT = 32;
 constexpr int LOG1PEXP_K = 36 * LOG1PEXP_PER_UNIT;
 
-// g(y) for y >= 0 given as a double-float; absolute error below 1e-13 (the
-// FP32 rounding of c3 times d^3 dominates).
-__device__ __forceinline__ f2 log1pexp_neg(f2 y, const float4 *__restrict__ tab) {
+// g(y) for y >= 0 given as a double-float; absolute error below 1e-14.
+// tab may live in shared or global memory.
+__device__ __forceinline__ f2 log1pexp_neg(f2 y, const float4 *tab) {
     if (y.hi >= 36.0f) return f2{__expf(-y.hi), 0.0f};
     const int k = __float2int_rn(y.hi * (float)LOG1PEXP_PER_UNIT);
-    // y.hi - k/16 is exact (Sterbenz), the low word carries the rest
-    const f2 d = fast_two_sum(__fsub_rn(y.hi, (float)k * (1.0f / LOG1PEXP_PER_UNIT)), y.lo);
-    const float4 q0 = __ldg(tab + 3 * k);
-    const float4 q1 = __ldg(tab + 3 * k + 1);
-    const float4 q2 = __ldg(tab + 3 * k + 2);
-    const float dh = d.hi;
-    float r = fmaf(dh, q2.z, q2.y);   // c6 + d c7
-    r = fmaf(dh, r, q2.x);            // c5 + d (...)
-    r = fmaf(dh, r, q1.w);            // c4 + ...
-    r = fmaf(dh, r, q1.z);            // c3 + ...
-    f2 t = df_add_f(f2{q1.x, q1.y}, __fmul_rn(dh, r));  // c2 + d r
-    t = df_add(f2{q0.z, q0.w}, df_mul(d, t));            // c1 + d t
-    return df_add(f2{q0.x, q0.y}, df_mul(d, t));          // c0 + d t
+    // y.hi - k/32 is exact (Sterbenz), the low word carries the rest
+    const f2 d = two_sum(__fsub_rn(y.hi, (float)k * (1.0f / LOG1PEXP_PER_UNIT)), y.lo);
+    const float4 q = tab[k];
+    const f2 g0{q.x, q.y}, s{q.z, q.w};
+    // first and second order in double-float
+    const f2 t1 = df_mul(df_neg(s), d);                             // g1 d
+    const f2 w = df_mul(s, df_add_f(df_neg(s), 1.0f));             // s (1 - s)
+    const f2 t2 = df_mul(w, df_mul(d, d));                          // g2 d^2 (halved below)
+    // third to sixth order in FP32 (their sum is below 7e-8)
+    const float wf = w.hi, vf = fmaf(-2.0f, s.hi, 1.0f), dh = d.hi;
+    const float c3 = -wf * vf * (1.0f / 6.0f);
+    const float c4 = wf * fmaf(-6.0f, wf, 1.0f) * (1.0f / 24.0f);
+    const float c5 = -wf * vf * fmaf(-12.0f, wf, 1.0f) * (1.0f / 120.0f);
+    const float c6 = wf * fmaf(wf, fmaf(120.0f, wf, -30.0f), 1.0f) * (1.0f / 720.0f);
+    const float r = fmaf(dh, fmaf(dh, fmaf(dh, c6, c5), c4), c3);
+    const float t3 = dh * dh * dh * r;
+    f2 gs = df_add(g0, t1);
+    gs = df_add(gs, f2{0.5f * t2.hi, 0.5f * t2.lo});
+    return df_add_f(gs, t3);
 }
 
 }  // namespace ihmc

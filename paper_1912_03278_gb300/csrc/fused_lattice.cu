@@ -213,11 +213,7 @@ __device__ __forceinline__ double kahan_val(float s, float c) { return (double)s
 struct PassCfg {
     int src, dst;
     float kick, drift;   // already multiplied by eps
-    bool first, last;    // first pass draws momenta; last pass has no drift
-    bool force;          // compute F and update p (and psi unless last)
-    bool action;         // accumulate action/observables of the src planes
-    float sign;          // +1, or -1 to evaluate at -psi (sign-flip proposal)
-    uint32_t spin_traj;  // trajectory index of the spin draw
+    bool first, last;    // first pass sums K0; last pass has no drift and sums K1
 };
 
 __device__ __forceinline__ float *sel3(const FusedArgs &A, int i) {
@@ -226,7 +222,7 @@ __device__ __forceinline__ float *sel3(const FusedArgs &A, int i) {
 
 template <int DIM, int VEC, int D>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
-                         uint32_t traj, const Slots &sl, float *smem, Acc &acc) {
+                         const Slots &sl, float *smem, Acc &acc) {
     constexpr int R = D + 4;   // psi ring slots
     constexpr int RP = D + 2;  // p ring slots
     const Geometry &g = A.g;
@@ -241,7 +237,6 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     const int nz = g.nplanes;
     const int nvec = P / VEC;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const bool load_p = pc.force && !pc.first;
 
     // copy group s: psi plane s-2 (periodic) and p plane s-4
     auto issue = [&](int s) {
@@ -257,7 +252,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
             }
         }
         const int zp = s - 4;
-        if (load_p && zp >= 0 && zp < nz) {
+        if (zp >= 0 && zp < nz) {
             const float *src = gp + (int64_t)zp * P;
             float *dst = p_ring + (unsigned)s % RP * P;
             if constexpr (VEC == 4) {
@@ -276,9 +271,6 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     int s_next = D + 3;
 
     const float Cf = prm.Cf, bJf = prm.bJf;
-    const f2 C2 = df_from_double(prm.C), bJ2 = df_from_double(prm.bJ);
-    const f2 hp2 = df_from_double(prm.hp), beta2 = df_from_double(prm.beta);
-    const bool hzero = prm.hp == 0.0;
 
     for (int it = -1; it <= nz; ++it) {
         cp_wait<D>();
@@ -288,7 +280,6 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         {
             const float *pm = psi_slot(it - 1), *pcen = psi_slot(it), *pq = psi_slot(it + 1);
             float *uo = u_slot(it);
-            const bool act = pc.action && it >= 0 && it < nz;
             const int zw = it < 0 ? it + nz : (it >= nz ? it - nz : it);
 #pragma unroll
             for (int k = 0; k < NVMAX; ++k) {
@@ -304,68 +295,20 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
                     const float a = fmaf(Cf, n.c.v[q], bJf * n.nb.v[q]);
-                    t.v[q] = tanh_f(pc.sign * a + hpv[q]);
+                    t.v[q] = tanh_f(a + hpv[q]);
                 }
-                if (pc.force && sl.valid[k]) {
+                if (sl.valid[k]) {
                     Vec<VEC> u;
 #pragma unroll
                     for (int q = 0; q < VEC; ++q) u.v[q] = t.v[q] - n.c.v[q];
                     stv<VEC>(uo + e0, u);
-                }
-                if (act && sl.valid[k]) {
-                    // FP64-accurate action in double-float:
-                    //   S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),  x = a + h'
-                    const int64_t site0 = (int64_t)zw * P + e0;
-                    float su[4];
-                    if constexpr (VEC == 4) {
-                        const float4 w = spin_u4_f32((uint32_t)(site0 >> 2), pc.spin_traj,
-                                                     (uint32_t)chain, A.seed);
-                        su[0] = w.x; su[1] = w.y; su[2] = w.z; su[3] = w.w;
-                    }
-#pragma unroll
-                    for (int q = 0; q < VEC; ++q) {
-                        const float ps = pc.sign * n.c.v[q];
-                        const f2 nbd = exact_nb<DIM, VEC>(n, q);
-                        const f2 a = df_add(df_mul_f(C2, ps),
-                                            df_mul(bJ2, f2{pc.sign * nbd.hi, pc.sign * nbd.lo}));
-                        f2 x = a;
-                        float hq = 0.0f;
-                        if (A.hdf) {
-                            const float2 hh = A.hdf[site0 + q];
-                            const f2 hp = df_mul(beta2, f2{hh.x, hh.y});
-                            x = df_add(a, hp);
-                            hq = hp.hi;
-                        } else if (!hzero) {
-                            x = df_add(a, hp2);
-                            hq = hp2.hi;
-                        }
-                        const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
-                        const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, A.lpe_tab);
-                        acc_add(acc.S, acc.Slo, df_mul_f(a, 0.5f * ps));
-                        acc_add(acc.S, acc.Slo, df_neg(ax));
-                        acc_add(acc.S, acc.Slo, df_neg(gl));
-                        const float tq = t.v[q];
-                        kahan_add(acc.sT, acc.cT, tq);
-                        kahan_add(acc.sAT, acc.cAT, a.hi * tq);
-                        kahan_add(acc.sHT, acc.cHT, hq * tq);
-                        float uu;
-                        if constexpr (VEC == 4) {
-                            uu = su[q];
-                        } else {
-                            const float4 w = spin_u4_f32((uint32_t)((site0 + q) >> 2),
-                                                         pc.spin_traj, (uint32_t)chain, A.seed);
-                            const int qq = (int)((site0 + q) & 3);
-                            uu = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
-                        }
-                        acc.sS += (uu < (1.0f + tq) * 0.5f) ? 1 : -1;
-                    }
                 }
             }
         }
         __syncthreads();
         // ---- F(z) = A u, kick and drift on plane z = it - 1 ----
         const int z = it - 1;
-        if (pc.force && z >= 0 && z < nz) {
+        if (z >= 0 && z < nz) {
             const float *um = u_slot(z - 1), *uc = u_slot(z), *uq = u_slot(z + 1);
             const float *psz = psi_slot(z);
             const float *ppz = p_ring + (unsigned)(z + 4) % RP * P;
@@ -377,29 +320,11 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 const int e0 = sl.e0[k];
                 Nbr<DIM, VEC> n;
                 gather<DIM, VEC>(g, um, uc, uq, e0, sl.x0[k], n);
-                Vec<VEC> pv;
-                if (pc.first) {
-                    const int64_t site0 = (int64_t)z * P + e0;
-                    if constexpr (VEC == 4) {
-                        const float4 w = momenta4_f32((uint32_t)(site0 >> 2), traj,
-                                                      (uint32_t)chain, A.seed);
-                        pv.v[0] = w.x; pv.v[1] = w.y; pv.v[2] = w.z; pv.v[3] = w.w;
-                    } else {
+                Vec<VEC> pv = ldv<VEC>(ppz + e0);
+                if (pc.first && sl.valid[k]) {
 #pragma unroll
-                        for (int q = 0; q < VEC; ++q) {
-                            const float4 w = momenta4_f32((uint32_t)((site0 + q) >> 2), traj,
-                                                          (uint32_t)chain, A.seed);
-                            const int qq = (int)((site0 + q) & 3);
-                            pv.v[q] = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
-                        }
-                    }
-                    if (sl.valid[k]) {
-#pragma unroll
-                        for (int q = 0; q < VEC; ++q)
-                            acc_add(acc.K0, acc.K0lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
-                    }
-                } else {
-                    pv = ldv<VEC>(ppz + e0);
+                    for (int q = 0; q < VEC; ++q)
+                        acc_add(acc.K0, acc.K0lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
                 }
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
@@ -427,6 +352,113 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     __syncthreads();
 }
 
+// Momentum refresh (Sec. 3): p ~ N(0,1) for every site of the chain, written
+// to global memory.  No barriers: every thread streams its own vectors.
+template <int VEC>
+__device__ void momenta_sweep(const FusedArgs &A, int chain, uint32_t traj, const Slots &sl) {
+    const Geometry &g = A.g;
+    float *gp = A.p + (int64_t)chain * g.N;
+    for (int z = 0; z < g.nplanes; ++z) {
+#pragma unroll
+        for (int k = 0; k < NVMAX; ++k) {
+            if (k >= sl.nwarp) break;
+            if (!sl.valid[k]) continue;
+            const int64_t site0 = (int64_t)z * g.P + sl.e0[k];
+            Vec<VEC> pv;
+            if constexpr (VEC == 4) {
+                const float4 w = momenta4_f32((uint32_t)(site0 >> 2), traj, (uint32_t)chain, A.seed);
+                pv.v[0] = w.x; pv.v[1] = w.y; pv.v[2] = w.z; pv.v[3] = w.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const float4 w = momenta4_f32((uint32_t)((site0 + q) >> 2), traj,
+                                                  (uint32_t)chain, A.seed);
+                    const int qq = (int)((site0 + q) & 3);
+                    pv.v[q] = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
+                }
+            }
+            stv<VEC>(gp + site0, pv);
+        }
+    }
+}
+
+// Action S(sign*psi) (Sec. 2, Eq. phi_psi_substitution in the form
+// S = 1/2 psi.A psi - sum_i log 2cosh((A psi)_i + h'_i)) to FP64 accuracy in
+// double-float arithmetic, and the Sec. 4 estimators with one conditional
+// spin draw, over the chain stored in buffer `buf`:
+//   S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),  x = a + h'.
+// No barriers: every thread streams its own vectors, neighbours come from
+// global memory (L1/L2).
+template <int DIM, int VEC>
+__device__ void action_sweep(const FusedArgs &A, const ChainParams &prm, int chain, int buf,
+                             float sign, uint32_t spin_traj, uint64_t seed, const Slots &sl,
+                             const float4 *tab, Acc &acc) {
+    const Geometry &g = A.g;
+    const int P = g.P, nz = g.nplanes;
+    const float *psi = sel3(A, buf) + (int64_t)chain * g.N;
+    const float Cf = prm.Cf, bJf = prm.bJf;
+    const f2 C2 = df_from_double(prm.C), bJ2 = df_from_double(prm.bJ);
+    const f2 hp2 = df_from_double(prm.hp), beta2 = df_from_double(prm.beta);
+    const bool hzero = prm.hp == 0.0;
+    for (int z = 0; z < nz; ++z) {
+        const float *pc = psi + (int64_t)z * P;
+        const float *pm = psi + (int64_t)(z == 0 ? nz - 1 : z - 1) * P;
+        const float *pq = psi + (int64_t)(z == nz - 1 ? 0 : z + 1) * P;
+#pragma unroll
+        for (int k = 0; k < NVMAX; ++k) {
+            if (k >= sl.nwarp) break;
+            if (!sl.valid[k]) continue;
+            const int e0 = sl.e0[k];
+            Nbr<DIM, VEC> n;
+            gather<DIM, VEC>(g, pm, pc, pq, e0, sl.x0[k], n);
+            const int64_t site0 = (int64_t)z * P + e0;
+            float su[4];
+            if constexpr (VEC == 4) {
+                const float4 w = spin_u4_f32((uint32_t)(site0 >> 2), spin_traj, (uint32_t)chain, seed);
+                su[0] = w.x; su[1] = w.y; su[2] = w.z; su[3] = w.w;
+            }
+            f2 sv{0.0f, 0.0f};
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const float ps = sign * n.c.v[q];
+                const f2 nbd = exact_nb<DIM, VEC>(n, q);
+                const f2 a = df_add(df_mul_f(C2, ps), df_mul(bJ2, f2{sign * nbd.hi, sign * nbd.lo}));
+                f2 x = a;
+                float hq = 0.0f;
+                if (A.hdf) {
+                    const float2 hh = A.hdf[site0 + q];
+                    const f2 hp = df_mul(beta2, f2{hh.x, hh.y});
+                    x = df_add(a, hp);
+                    hq = hp.hi;
+                } else if (!hzero) {
+                    x = df_add(a, hp2);
+                    hq = hp2.hi;
+                }
+                const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
+                const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, tab);
+                // S_i for this site, summed over the vector first (short chains)
+                const f2 si = df_add(df_mul_f(a, 0.5f * ps), df_neg(df_add(ax, gl)));
+                sv = df_add(sv, si);
+                const float tq = tanh_f(fmaf(Cf, ps, sign * bJf * n.nb.v[q]) + hq);
+                kahan_add(acc.sT, acc.cT, tq);
+                kahan_add(acc.sAT, acc.cAT, a.hi * tq);
+                kahan_add(acc.sHT, acc.cHT, hq * tq);
+                float uu;
+                if constexpr (VEC == 4) {
+                    uu = su[q];
+                } else {
+                    const float4 w = spin_u4_f32((uint32_t)((site0 + q) >> 2), spin_traj,
+                                                 (uint32_t)chain, seed);
+                    const int qq = (int)((site0 + q) & 3);
+                    uu = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
+                }
+                acc.sS += (uu < (1.0f + tq) * 0.5f) ? 1 : -1;
+            }
+            acc_add(acc.S, acc.Slo, sv);
+        }
+    }
+}
+
 __device__ __forceinline__ int buf_loc(int start, int j) {
     if (j == 0) return start;
     return (start + ((j & 1) ? 1 : 2)) % 3;
@@ -447,8 +479,9 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
     float *smem = reinterpret_cast<float *>(smem_f4);
     constexpr int R = D + 4, RP = D + 2;
     const Geometry &g = A.g;
-    const size_t ring_floats = (size_t)(R + RP + 3) * g.P;
-    double *red = reinterpret_cast<double *>(smem + ((ring_floats + 3) & ~(size_t)3));
+    const size_t ring_floats = ((size_t)(R + RP + 3) * g.P + 3) & ~(size_t)3;
+    float4 *tab = reinterpret_cast<float4 *>(smem + ring_floats);
+    double *red = reinterpret_cast<double *>(tab + LOG1PEXP_NODES);
     int *bcast = reinterpret_cast<int *>(red + 32 * 8);
 
     const int chain = A.chain0 + blockIdx.x;
@@ -456,24 +489,19 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
     ChainState *st = A.state + chain;
     const ChainParams prm = A.params[chain];
     const double invN = 1.0 / (double)g.N;
+    const Slots sl = make_slots<VEC>(g);
 
     if (A.mode == MODE_MOMENTA) {
-        float *gp = A.p + (int64_t)chain * g.N;
-        for (int64_t i = threadIdx.x; i < g.N; i += blockDim.x) {
-            const float4 w = momenta4_f32((uint32_t)(i >> 2), A.traj0, (uint32_t)chain, A.seed);
-            const int q = (int)(i & 3);
-            gp[i] = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
-        }
+        momenta_sweep<VEC>(A, chain, A.traj0, sl);
         return;
     }
-
-    const Slots sl = make_slots<VEC>(g);
+    for (int i = threadIdx.x; i < LOG1PEXP_NODES; i += blockDim.x) tab[i] = A.lpe_tab[i];
+    __syncthreads();
 
     if (A.mode == MODE_EVAL) {
         Acc acc = acc_zero();
         const int start = st->start;
-        PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, 1.0f, TRAJ_INIT};
-        run_pass<DIM, VEC, D>(A, pc, prm, chain, TRAJ_INIT, sl, smem, acc);
+        action_sweep<DIM, VEC>(A, prm, chain, start, 1.0f, TRAJ_INIT, 0, sl, tab, acc);
         double v[5] = {acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
                        kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
         block_sum<5>(v, red);
@@ -489,6 +517,9 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
     for (int k = 0; k < A.n_traj; ++k) {
         const uint32_t traj = A.traj0 + (uint32_t)k;
         Acc acc = acc_zero();
+        // momentum refresh, then the integrator's force passes
+        momenta_sweep<VEC>(A, chain, traj, sl);
+        __syncthreads();
         for (int j = 0; j < S.n_pass; ++j) {
             PassCfg pc;
             pc.src = buf_loc(start, j);
@@ -497,17 +528,14 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             pc.drift = (float)(S.drift[j] * prm.eps);
             pc.first = (j == 0);
             pc.last = (j == S.n_pass - 1);
-            pc.force = true;
-            pc.action = pc.last;
-            pc.sign = 1.0f;
-            pc.spin_traj = traj;
-            run_pass<DIM, VEC, D>(A, pc, prm, chain, traj, sl, smem, acc);
+            run_pass<DIM, VEC, D>(A, pc, prm, chain, sl, smem, acc);
         }
+        const int prop = buf_loc(start, S.n_pass - 1);
+        action_sweep<DIM, VEC>(A, prm, chain, prop, 1.0f, traj, A.seed, sl, tab, acc);
         double v[7] = {acc_val(acc.K0, acc.K0lo), acc_val(acc.K1, acc.K1lo),
                        acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
                        kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
         block_sum<7>(v, red);
-        const int prop = buf_loc(start, S.n_pass - 1);
         if (threadIdx.x == 0) {
             const double S0 = st->S;
             const double dH = (v[1] + v[2]) - (v[0] + S0);
@@ -535,8 +563,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
         // ---- optional global sign flip psi -> -psi (Sec. 3, ergodicity) ----
         if (A.flip_every > 0 && ((traj + 1) % (uint32_t)A.flip_every) == 0) {
             Acc fa = acc_zero();
-            PassCfg pc{start, start, 0.f, 0.f, false, false, false, true, -1.0f, traj};
-            run_pass<DIM, VEC, D>(A, pc, prm, chain, traj, sl, smem, fa);
+            action_sweep<DIM, VEC>(A, prm, chain, start, -1.0f, traj, A.seed, sl, tab, fa);
             double w[5] = {acc_val(fa.S, fa.Slo), kahan_val(fa.sT, fa.cT),
                            kahan_val(fa.sAT, fa.cAT), kahan_val(fa.sHT, fa.cHT), (double)fa.sS};
             block_sum<5>(w, red);
@@ -604,10 +631,12 @@ cudaError_t launch_dim(const FusedArgs &a, const Schedule &s, int threads, int d
                        cudaStream_t st) {
     if (vec == 4) {
         if (depth >= 4) return launch_kernel<DIM, 4, 4>(a, s, threads, st);
-        return launch_kernel<DIM, 4, 2>(a, s, threads, st);
+        if (depth >= 2) return launch_kernel<DIM, 4, 2>(a, s, threads, st);
+        return launch_kernel<DIM, 4, 1>(a, s, threads, st);
     }
     if (depth >= 4) return launch_kernel<DIM, 1, 4>(a, s, threads, st);
-    return launch_kernel<DIM, 1, 2>(a, s, threads, st);
+    if (depth >= 2) return launch_kernel<DIM, 1, 2>(a, s, threads, st);
+    return launch_kernel<DIM, 1, 1>(a, s, threads, st);
 }
 
 // tanh self-test kernel
@@ -630,12 +659,13 @@ int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec) {
     (void)vec;
     const size_t ring = (size_t)(depth + 4 + depth + 2 + 3) * g.P;
     const size_t floats = ((ring + 3) & ~(size_t)3);
-    return (int)(floats * 4 + 32 * 8 * 8 + 16);
+    return (int)(floats * 4 + LOG1PEXP_NODES * 16 + 32 * 8 * 8 + 16);
 }
 
 // Launch shape: VEC = 4 when rows split into float4s; threads = one per vector
 // up to 256, each thread owning at most NVMAX vectors per plane; prefetch
-// depth 4 planes when the rings fit in 200 KB, else 2.  Returns VEC, or -1 if
+// depth 4 planes when the rings fit in 200 KB, else 2 (or 1 for the largest
+// planes).  Returns VEC, or -1 if
 // the plane does not fit on chip.
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
     const int vec = (g.X % 4 == 0 && g.P % 4 == 0) ? 4 : 1;
@@ -647,6 +677,7 @@ int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
     *threads = t;
     int d = 4;
     if (fused_lattice_smem_bytes(g, d, vec) > 200 * 1024) d = 2;
+    if (fused_lattice_smem_bytes(g, d, vec) > 220 * 1024) d = 1;
     if (fused_lattice_smem_bytes(g, d, vec) > 227 * 1024) return -1;
     *depth = d;
     return vec;

@@ -82,9 +82,9 @@ cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream
 cudaError_t launch_log1pexp_selftest(const double *y, double *out, int64_t n, const float4 *tab,
                                      cudaStream_t s);
 
-// Host construction of the log(1 + exp(-y)) Taylor table (3 float4 per node).
-void build_log1pexp_table(float *out /* 12 * (LOG1PEXP_K + 1) floats */);
-constexpr int LOG1PEXP_NODES = 36 * 16 + 1;
+// Host construction of the log(1 + exp(-y)) table (one float4 per node).
+void build_log1pexp_table(float *out /* 4 * LOG1PEXP_NODES floats */);
+constexpr int LOG1PEXP_NODES = 36 * 32 + 1;
 
 // Plain FP64 form: one chain per launch, unfused kernels.
 struct PlainArgs {

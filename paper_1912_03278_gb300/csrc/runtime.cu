@@ -168,46 +168,18 @@ static double lanczos_lambda_min(const double *J, int64_t N, int steps) {
     return 0.5 * (lo + hi);
 }
 
-// Taylor table of g(y) = log(1 + exp(-y)) at y_k = k/16 (layout in df32.cuh).
-// With s = 1/(1 + e^y): g' = -s and ds/dy = -s(1 - s), so g^(n) = P_n(s) with
-// P_1 = -s and P_{n+1}(s) = -s(1 - s) P_n'(s); c_n = P_n(s)/n!.
+// Table of g(y) = log(1 + exp(-y)) at y_k = k/32 with s = 1/(1 + e^{y_k})
+// (layout in df32.cuh), each value split into a double-float pair.
 void ihmc::build_log1pexp_table(float *out) {
-    double P[8][10];
-    std::memset(P, 0, sizeof P);
-    P[1][1] = -1.0;
-    for (int n = 1; n < 7; ++n) {
-        double D[10] = {0};
-        for (int j = 0; j + 1 < 10; ++j) D[j] = (j + 1) * P[n][j + 1];
-        for (int j = 0; j < 10; ++j) {
-            double v = 0.0;
-            if (j >= 1) v -= D[j - 1];
-            if (j >= 2) v += D[j - 2];
-            P[n + 1][j] = v;
-        }
-    }
-    double fact[8] = {1, 1, 2, 6, 24, 120, 720, 5040};
     for (int k = 0; k < LOG1PEXP_NODES; ++k) {
-        const double y = (double)k / 16.0;
+        const double y = (double)k / 32.0;
+        const double g0 = std::log1p(std::exp(-y));
         const double sg = 1.0 / (1.0 + std::exp(y));
-        double c[8];
-        c[0] = std::log1p(std::exp(-y));
-        for (int n = 1; n < 8; ++n) {
-            double v = 0.0, pw = 1.0;
-            for (int j = 0; j < 10; ++j) {
-                v += P[n][j] * pw;
-                pw *= sg;
-            }
-            c[n] = v / fact[n];
-        }
-        // exact low-order coefficients: c1 = -s, c2 = s(1-s)/2
-        c[1] = -sg;
-        c[2] = 0.5 * sg * (1.0 - sg);
-        auto hi = [](double x) { return (float)x; };
-        auto lo = [](double x) { return (float)(x - (double)(float)x); };
-        float *q = out + 12 * k;
-        q[0] = hi(c[0]); q[1] = lo(c[0]); q[2] = hi(c[1]); q[3] = lo(c[1]);
-        q[4] = hi(c[2]); q[5] = lo(c[2]); q[6] = (float)c[3]; q[7] = (float)c[4];
-        q[8] = (float)c[5]; q[9] = (float)c[6]; q[10] = (float)c[7]; q[11] = 0.0f;
+        float *q = out + 4 * k;
+        q[0] = (float)g0;
+        q[1] = (float)(g0 - (double)q[0]);
+        q[2] = (float)sg;
+        q[3] = (float)(sg - (double)q[2]);
     }
 }
 
@@ -477,7 +449,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     if ((st = dalloc(h, &h->d_state, sizeof(ChainState) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_err, sizeof(int))) != ISING_OK) return bail(st);
     if (is_fp32_lattice(h)) {
-        std::vector<float> tab(12 * LOG1PEXP_NODES);
+        std::vector<float> tab(4 * LOG1PEXP_NODES);
         build_log1pexp_table(tab.data());
         if ((st = dalloc(h, &h->d_lpe, tab.size() * sizeof(float))) != ISING_OK) return bail(st);
         if (cudaMemcpy(h->d_lpe, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
@@ -493,7 +465,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         }
         if ((st = dalloc(h, &h->d_h32, 2 * N * sizeof(float))) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->d_h64, N * sizeof(double))) != ISING_OK) return bail(st);
-        if (cudaMemcpy(h->d_h32, h32.data(), N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        if (cudaMemcpy(h->d_h32, h32.data(), 2 * N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h->d_h64, cfg->h, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "field upload failed"));
     }
@@ -837,7 +809,7 @@ ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n)
         if (which == ISING_SELFTEST_TANH) {
             e = launch_tanh_selftest((const float *)din, (float *)dout, n, 0);
         } else {
-            std::vector<float> tab(12 * LOG1PEXP_NODES);
+            std::vector<float> tab(4 * LOG1PEXP_NODES);
             build_log1pexp_table(tab.data());
             e = cudaMalloc(&dtab, tab.size() * sizeof(float));
             if (e == cudaSuccess)
