@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chains-per-beta", type=int, default=256)
     ap.add_argument("--L", type=str, default="256,1024")
-    ap.add_argument("--tune-rounds", type=int, default=6)
+    ap.add_argument("--tune-rounds", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -212,12 +212,14 @@ def hot_start(pkg, sims, seed):
 
 
 def tune_eps(sims, betas_per_chain, rounds, seed, therm=4):
-    """Step-size tuning during equilibration only (frozen afterwards).  After
-    `therm` trajectories, each round rescales eps per beta group by
-    (0.128 / (<dH^2>/2))^(1/4), clamped to [1/2, 2]: for a second-order
-    integrator <dH> = <dH^2>/2 grows as eps^4, and 80% acceptance corresponds
-    to <dH> ~ 0.128."""
-    target = 0.128
+    """Step-size tuning during equilibration only (frozen afterwards).  For a
+    second-order integrator the mean energy violation grows as eps^4 and the
+    acceptance is erfc(sqrt(<dH>)/2); each round estimates the acceptance per
+    beta group from the smooth mean of min(1, exp(-dH)), converts it to an
+    effective <dH>, and rescales eps by (0.128 / <dH>)^(1/4) (0.128 gives 80%),
+    clamped to [1/2, 2]."""
+    from scipy.special import erfcinv
+    target = 4.0 * erfcinv(TARGET_ACC) ** 2
     ub = np.unique(betas_per_chain)
     for L, sim in sims.items():
         eps = np.full(len(betas_per_chain), EPS0.get(L, 0.05))
@@ -225,10 +227,12 @@ def tune_eps(sims, betas_per_chain, rounds, seed, therm=4):
         for r in range(rounds):
             sim.trajectories(1, seed + 1000 + r)
             dH = sim.records()[:, 0]
+            pacc = np.minimum(1.0, np.exp(-np.clip(dH, -50, 50)))
             for b in ub:
                 sel = betas_per_chain == b
-                half_msq = 0.5 * float(np.mean(dH[sel] ** 2)) + 1e-12
-                eps[sel] *= float(np.clip((target / half_msq) ** 0.25, 0.5, 2.0))
+                a = float(np.clip(pacc[sel].mean(), 1e-3, 1 - 1e-6))
+                eff = 4.0 * erfcinv(a) ** 2
+                eps[sel] *= float(np.clip((target / eff) ** 0.25, 0.5, 2.0))
             sim.set_eps(eps)
         sim._eps = eps.copy()
 
