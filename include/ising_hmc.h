@@ -216,6 +216,36 @@ ising_status ising_hmc_sync(ising_hmc_t *h);
 enum { ISING_SELFTEST_TANH = 0, ISING_SELFTEST_LOG1PEXP = 1 };
 ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n);
 
+/* Energy without allocation.  Some callers cannot call cudaMalloc: code that
+ * runs inside a memory pool or arena it does not own, hosts that forbid
+ * allocation after start-up, or work inside a region where an allocation
+ * would stall or break the caller's stream.  For them this entry point
+ * computes, in FP64 and with the plain form's kernels, the action
+ * S(psi) = 1/2 psi.A.psi - sum_i log 2cosh((A psi)_i + beta*h0) and the
+ * kinetic energy 1/2 p.p of n_chains periodic-lattice configurations
+ * (A = beta*Jnn*K + C*1), without allocating any memory.  The paper has no
+ * counterpart: it is a deployment variant, not a step of the method.
+ *   psi, p : device arrays of n_chains*N FP64 values, chain-major (p may be
+ *            NULL, then K = 0); out: device array of 2*n_chains FP64 values,
+ *            out[2c] = S of chain c, out[2c+1] = K of chain c.  The caller
+ *            owns all three.
+ *   stream : cudaStream_t or NULL; the call is asynchronous on it.
+ * The partial sums live in one fixed device array of
+ * ISING_NOALLOC_MAX_CHAINS * 256 * 2 doubles (256 KB) that every GPU loading
+ * this library holds until the process exits; hence n_chains is limited to
+ * ISING_NOALLOC_MAX_CHAINS (EINVAL beyond it).  Every call overwrites the
+ * array's slots it uses before reading them; calls that overlap on the GPU
+ * (other streams, other host threads) share the array and race, so
+ * serialise them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Errors: EINVAL (arguments; message in
+ * ising_hmc_energy_noalloc_error()), ECUDA. */
+#define ISING_NOALLOC_MAX_CHAINS 64
+ising_status ising_hmc_energy_noalloc(int dim, const int L[3], double beta, double Jnn, double C,
+                                      double h0, int n_chains, const double *psi, const double *p,
+                                      double *out, void *stream);
+const char *ising_hmc_energy_noalloc_error(void);
+
 void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);

@@ -90,6 +90,9 @@ def load(path: str | None = None):
         "ising_hmc_launch_count": (c_int64, [P]),
         "ising_hmc_sync": (c_int, [P]),
         "ising_hmc_selftest": (c_int, [c_int, P, P, c_int64]),
+        "ising_hmc_energy_noalloc": (c_int, [c_int, P, c_double, c_double, c_double, c_double,
+                                             c_int, P, P, P, P]),
+        "ising_hmc_energy_noalloc_error": (c_char_p, []),
         "ising_hmc_destroy": (None, [P]),
         "ising_hmc_last_error": (c_char_p, [P]),
         "ising_hmc_last_create_error": (c_char_p, []),
@@ -296,6 +299,26 @@ def ising_hmc_selftest(which, x) -> np.ndarray:
     out = np.zeros_like(xin)
     _check(None, load().ising_hmc_selftest(which, xin.ctypes.data, out.ctypes.data, xin.size))
     return out
+
+
+ISING_NOALLOC_MAX_CHAINS = 64
+
+
+def ising_hmc_energy_noalloc(dim, L, beta, Jnn, C, h0, n_chains, psi_ptr, p_ptr, out_ptr,
+                             stream=None):
+    """FP64 S and 1/2 p.p of n_chains lattice configurations without any
+    allocation; all pointers are device addresses owned by the caller."""
+    Lc = (c_int * 3)(*[int(x) for x in (tuple(L) + (1, 1, 1))[:3]])
+    st = load().ising_hmc_energy_noalloc(int(dim), Lc, float(beta), float(Jnn), float(C),
+                                         float(h0), int(n_chains), c_void_p(psi_ptr),
+                                         c_void_p(p_ptr) if p_ptr else None, c_void_p(out_ptr),
+                                         c_void_p(stream) if stream else None)
+    if st != ISING_OK:
+        raise IsingError(st, (load().ising_hmc_energy_noalloc_error() or b"").decode())
+
+
+def ising_hmc_energy_noalloc_error() -> str:
+    return (load().ising_hmc_energy_noalloc_error() or b"").decode()
 
 
 def ising_hmc_destroy(h):

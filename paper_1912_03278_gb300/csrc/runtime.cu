@@ -604,7 +604,7 @@ ising_status ising_hmc_observables(ising_hmc_t *h, ising_obs *out) {
     const int C = h->n_chains;
     double nmeas = 0, nacc = 0, sdh = 0, sexp = 0;
     std::vector<double> cm(C), ca(C), ce(C), cx(C);
-    double vm = 0, va = 0, ve = 0, vx = 0;
+    double vm = 0, va = 0, ve = 0;
     for (int c = 0; c < C; ++c) {
         const double *s = hs[c].sums;
         const double n = s[ISING_SUM_NMEAS];
