@@ -204,6 +204,70 @@ int64_t ising_hmc_launch_count(const ising_hmc_t *h);
 /* Synchronise the handle's stream; ETIMEOUT if a device wait gave up. */
 ising_status ising_hmc_sync(ising_hmc_t *h);
 
+/* Launch shape of the fused FP32 lattice kernel: threads per CTA (one CTA per
+ * chain; 32..256, a multiple of 32, at most 4 float4 vectors of a plane per
+ * thread) and the prefetch depth in planes (1, 2 or 4; the shared-memory
+ * rings must fit).  EINVAL for other forms or invalid shapes. */
+ising_status ising_hmc_set_launch(ising_hmc_t *h, int threads, int depth);
+ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth);
+
+/* Autotuner: times `reps` trajectories for every valid launch shape on a
+ * temporary handle with the same lattice and the first chains' parameters
+ * (the handle's own chains are not advanced), keeps the fastest shape, and
+ * returns its time per trajectory in *best_ms (may be NULL).  Allocates the
+ * temporary handle; synchronises. */
+ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms);
+
+/* Groups: FP32 lattice handles of any mix of lattice sizes advanced together
+ * by one CUDA-graph launch per call (one kernel node per member, the nodes
+ * independent so they run concurrently on the device).  The graph is built
+ * once and its nodes' parameters (trajectory index, count, seed) are updated
+ * per call; it is rebuilt if a member's launch shape changes.  A group does
+ * not own its members; destroy the group before them.  Work already queued on
+ * a member's stream runs before the group's, and later member work after it. */
+typedef struct ising_group ising_group_t;
+ising_status ising_group_create(ising_hmc_t *const *members, int n, ising_group_t **out);
+/* n trajectories of every chain of every member (same semantics as
+ * ising_hmc_trajectories per member).  Asynchronous. */
+ising_status ising_group_trajectories(ising_group_t *g, int64_t n, uint64_t seed);
+/* Same with one seed per member (seeds[i] for the i-th member). */
+ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const uint64_t *seeds);
+ising_status ising_group_sync(ising_group_t *g);
+int64_t ising_group_launch_count(const ising_group_t *g);   /* graph launches so far */
+void *ising_group_stream(const ising_group_t *g);           /* cudaStream_t of the launches */
+const char *ising_group_last_error(const ising_group_t *g);
+void ising_group_destroy(ising_group_t *g);
+
+/* Serving: a continuous-batching request loop.  A server owns a worker thread
+ * on the current device.  Requests (a configuration as for ising_hmc_create,
+ * a number of trajectories and a seed) are queued from any host thread and
+ * admitted in arrival order while their device memory
+ * (ising_hmc_estimate_bytes) fits the budget; their state stays resident
+ * until they finish.  Each quantum advances every active request by the same
+ * number of trajectories (at most quantum_traj): all FP32 lattice requests in
+ * one CUDA-graph launch, others on their own streams.  Finished requests keep
+ * their observables and latency and free their memory for waiting ones.  A
+ * request's result does not depend on the other requests in the batch.
+ * Requests larger than the whole budget are rejected (state 3, ENOMEM). */
+typedef struct ising_server ising_server_t;
+ising_status ising_server_create(int64_t budget_bytes, int quantum_traj, ising_server_t **out);
+ising_status ising_server_submit(ising_server_t *s, const ising_hmc_config *cfg, int64_t n_traj,
+                                 uint64_t seed, int64_t *request_id);
+/* state: 0 queued, 1 running, 2 done (obs, latency and queue time valid),
+ * 3 rejected (the return value is the reason).  latency = done - submit,
+ * queue = admit - submit, in seconds. */
+ising_status ising_server_poll(ising_server_t *s, int64_t request_id, int *state, ising_obs *obs,
+                               double *latency_s, double *queue_s);
+ising_status ising_server_wait(ising_server_t *s, int64_t request_id, double timeout_s);
+ising_status ising_server_drain(ising_server_t *s, double timeout_s);
+/* out[ISING_SERVER_NSTATS]: admitted, completed, rejected, queued, active,
+ * device bytes in use, site-steps done, shared graph launches, quanta,
+ * seconds since creation. */
+#define ISING_SERVER_NSTATS 10
+ising_status ising_server_stats(ising_server_t *s, double *out);
+const char *ising_server_last_error(const ising_server_t *s);
+void ising_server_destroy(ising_server_t *s);
+
 /* Self-test of device functions the trajectories rely on (no model state;
  * host buffers; synchronous):
  *   which = ISING_SELFTEST_TANH: out[i] = tanh(in[i]) for FP32 in/out, the

@@ -90,6 +90,25 @@ def load(path: str | None = None):
         "ising_hmc_launch_count": (c_int64, [P]),
         "ising_hmc_sync": (c_int, [P]),
         "ising_hmc_selftest": (c_int, [c_int, P, P, c_int64]),
+        "ising_hmc_set_launch": (c_int, [P, c_int, c_int]),
+        "ising_hmc_get_launch": (c_int, [P, P, P]),
+        "ising_hmc_autotune": (c_int, [P, c_int, P]),
+        "ising_group_create": (c_int, [P, c_int, P]),
+        "ising_group_trajectories": (c_int, [P, c_int64, c_uint64]),
+        "ising_group_trajectories_seeds": (c_int, [P, c_int64, P]),
+        "ising_server_create": (c_int, [c_int64, c_int, P]),
+        "ising_server_submit": (c_int, [P, P, c_int64, c_uint64, P]),
+        "ising_server_poll": (c_int, [P, c_int64, P, P, P, P]),
+        "ising_server_wait": (c_int, [P, c_int64, c_double]),
+        "ising_server_drain": (c_int, [P, c_double]),
+        "ising_server_stats": (c_int, [P, P]),
+        "ising_server_last_error": (c_char_p, [P]),
+        "ising_server_destroy": (None, [P]),
+        "ising_group_sync": (c_int, [P]),
+        "ising_group_launch_count": (c_int64, [P]),
+        "ising_group_stream": (c_void_p, [P]),
+        "ising_group_last_error": (c_char_p, [P]),
+        "ising_group_destroy": (None, [P]),
         "ising_hmc_energy_noalloc": (c_int, [c_int, P, c_double, c_double, c_double, c_double,
                                              c_int, P, P, P, P]),
         "ising_hmc_energy_noalloc_error": (c_char_p, []),
@@ -301,6 +320,192 @@ def ising_hmc_selftest(which, x) -> np.ndarray:
     return out
 
 
+def ising_hmc_set_launch(h, threads, depth):
+    _check(h, load().ising_hmc_set_launch(h, int(threads), int(depth)))
+
+
+def ising_hmc_get_launch(h):
+    t, d = ctypes.c_int(), ctypes.c_int()
+    _check(h, load().ising_hmc_get_launch(h, ctypes.byref(t), ctypes.byref(d)))
+    return t.value, d.value
+
+
+def ising_hmc_autotune(h, reps=2) -> float:
+    ms = c_double()
+    _check(h, load().ising_hmc_autotune(h, int(reps), ctypes.byref(ms)))
+    return ms.value
+
+
+def _gcheck(g, st):
+    if st != ISING_OK:
+        msg = load().ising_group_last_error(g)
+        raise IsingError(st, (msg or b"").decode())
+
+
+def ising_group_create(handles) -> int:
+    arr = (c_void_p * len(handles))(*handles)
+    out = c_void_p()
+    _gcheck(None, load().ising_group_create(arr, len(handles), ctypes.byref(out)))
+    return out.value
+
+
+def ising_group_trajectories(g, n, seed):
+    _gcheck(g, load().ising_group_trajectories(g, int(n), int(seed)))
+
+
+def ising_group_trajectories_seeds(g, n, seeds):
+    arr = np.ascontiguousarray(seeds, dtype=np.uint64)
+    _gcheck(g, load().ising_group_trajectories_seeds(g, int(n), arr.ctypes.data))
+
+
+def ising_group_sync(g):
+    _gcheck(g, load().ising_group_sync(g))
+
+
+def ising_group_launch_count(g) -> int:
+    return load().ising_group_launch_count(g)
+
+
+def ising_group_stream(g) -> int:
+    return load().ising_group_stream(g)
+
+
+def ising_group_last_error(g) -> str:
+    return (load().ising_group_last_error(g) or b"").decode()
+
+
+def ising_group_destroy(g):
+    if g:
+        load().ising_group_destroy(g)
+
+
+class IsingGroup:
+    """Several IsingHMC objects advanced by one CUDA-graph launch per call."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        self.g = ising_group_create([s.h for s in self.sims])
+
+    def trajectories(self, n, seed):
+        ising_group_trajectories(self.g, n, seed)
+
+    def sync(self):
+        ising_group_sync(self.g)
+
+    @property
+    def launches(self):
+        return ising_group_launch_count(self.g)
+
+    def close(self):
+        if self.g:
+            ising_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scheck(s, st):
+    if st != ISING_OK:
+        msg = load().ising_server_last_error(s)
+        raise IsingError(st, (msg or b"").decode())
+
+
+ISING_SERVER_NSTATS = 10
+SERVER_STAT_NAMES = ["admitted", "completed", "rejected", "queued", "active", "bytes_in_use",
+                     "site_steps", "group_launches", "quanta", "seconds"]
+
+
+def ising_server_create(budget_bytes, quantum_traj) -> int:
+    out = c_void_p()
+    _scheck(None, load().ising_server_create(int(budget_bytes), int(quantum_traj),
+                                             ctypes.byref(out)))
+    return out.value
+
+
+def ising_server_submit(s, cfg, n_traj, seed) -> int:
+    rid = c_int64()
+    _scheck(s, load().ising_server_submit(s, ctypes.byref(cfg), int(n_traj), int(seed),
+                                          ctypes.byref(rid)))
+    return rid.value
+
+
+def ising_server_poll(s, rid):
+    state = c_int()
+    o = ising_obs()
+    lat, q = c_double(), c_double()
+    st = load().ising_server_poll(s, int(rid), ctypes.byref(state), ctypes.byref(o),
+                                  ctypes.byref(lat), ctypes.byref(q))
+    res = dict(state=state.value, status=st)
+    if state.value >= 2:
+        res.update(latency=lat.value, queue=q.value,
+                   obs={k: getattr(o, k) for k, _ in ising_obs._fields_})
+    return res
+
+
+def ising_server_wait(s, rid, timeout_s):
+    _scheck(s, load().ising_server_wait(s, int(rid), float(timeout_s)))
+
+
+def ising_server_drain(s, timeout_s):
+    _scheck(s, load().ising_server_drain(s, float(timeout_s)))
+
+
+def ising_server_stats(s) -> dict:
+    out = np.zeros(ISING_SERVER_NSTATS)
+    _scheck(s, load().ising_server_stats(s, out.ctypes.data))
+    return dict(zip(SERVER_STAT_NAMES, out.tolist()))
+
+
+def ising_server_last_error(s) -> str:
+    return (load().ising_server_last_error(s) or b"").decode()
+
+
+def ising_server_destroy(s):
+    if s:
+        load().ising_server_destroy(s)
+
+
+class IsingServer:
+    """Continuous-batching request loop (see the header)."""
+
+    def __init__(self, budget_bytes, quantum_traj=4):
+        self.s = ising_server_create(budget_bytes, quantum_traj)
+
+    def submit(self, n_traj, seed, **kw):
+        cfg, keep = make_config(**kw)
+        rid = ising_server_submit(self.s, cfg, n_traj, seed)
+        del keep
+        return rid
+
+    def poll(self, rid):
+        return ising_server_poll(self.s, rid)
+
+    def wait(self, rid, timeout_s=60.0):
+        ising_server_wait(self.s, rid, timeout_s)
+        return self.poll(rid)
+
+    def drain(self, timeout_s=600.0):
+        ising_server_drain(self.s, timeout_s)
+
+    def stats(self):
+        return ising_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            ising_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 ISING_NOALLOC_MAX_CHAINS = 64
 
 
@@ -385,6 +590,16 @@ class IsingHMC:
 
     def reset_sums(self):
         ising_hmc_reset_sums(self.h)
+
+    def autotune(self, reps=2):
+        return ising_hmc_autotune(self.h, reps)
+
+    def set_launch(self, threads, depth):
+        ising_hmc_set_launch(self.h, threads, depth)
+
+    @property
+    def launch(self):
+        return ising_hmc_get_launch(self.h)
 
     def sync(self):
         ising_hmc_sync(self.h)

@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
 }
 
 template <int DIM, int VEC, int D>
-cudaError_t launch_kernel(const FusedArgs &a, const Schedule &s, int threads, cudaStream_t st) {
+cudaError_t kernel_node(const FusedArgs &a, int threads, cudaKernelNodeParams *np, void **args) {
     const int smem = fused_lattice_smem_bytes(a.g, D, VEC);
     static bool configured = false;
     auto kern = fused_lattice_kernel<DIM, VEC, D>;
@@ -620,23 +620,26 @@ cudaError_t launch_kernel(const FusedArgs &a, const Schedule &s, int threads, cu
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int grid = a.n_chains - a.chain0;
-    if (grid <= 0) return cudaSuccess;
-    kern<<<grid, threads, smem, st>>>(a, s);
-    return cudaGetLastError();
+    np->func = reinterpret_cast<void *>(kern);
+    np->gridDim = dim3((unsigned)(a.n_chains - a.chain0), 1, 1);
+    np->blockDim = dim3((unsigned)threads, 1, 1);
+    np->sharedMemBytes = (unsigned)smem;
+    np->kernelParams = args;
+    np->extra = nullptr;
+    return cudaSuccess;
 }
 
 template <int DIM>
-cudaError_t launch_dim(const FusedArgs &a, const Schedule &s, int threads, int depth, int vec,
-                       cudaStream_t st) {
+cudaError_t node_dim(const FusedArgs &a, int threads, int depth, int vec, cudaKernelNodeParams *np,
+                     void **args) {
     if (vec == 4) {
-        if (depth >= 4) return launch_kernel<DIM, 4, 4>(a, s, threads, st);
-        if (depth >= 2) return launch_kernel<DIM, 4, 2>(a, s, threads, st);
-        return launch_kernel<DIM, 4, 1>(a, s, threads, st);
+        if (depth >= 4) return kernel_node<DIM, 4, 4>(a, threads, np, args);
+        if (depth >= 2) return kernel_node<DIM, 4, 2>(a, threads, np, args);
+        return kernel_node<DIM, 4, 1>(a, threads, np, args);
     }
-    if (depth >= 4) return launch_kernel<DIM, 1, 4>(a, s, threads, st);
-    if (depth >= 2) return launch_kernel<DIM, 1, 2>(a, s, threads, st);
-    return launch_kernel<DIM, 1, 1>(a, s, threads, st);
+    if (depth >= 4) return kernel_node<DIM, 1, 4>(a, threads, np, args);
+    if (depth >= 2) return kernel_node<DIM, 1, 2>(a, threads, np, args);
+    return kernel_node<DIM, 1, 1>(a, threads, np, args);
 }
 
 // tanh self-test kernel
@@ -683,12 +686,31 @@ int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
     return vec;
 }
 
+cudaError_t fused_lattice_node(const FusedArgs &a, int threads, int depth,
+                               cudaKernelNodeParams *np, void **args) {
+    const int vec = (a.g.X % 4 == 0 && a.g.P % 4 == 0) ? 4 : 1;
+    if (a.g.dim == 3) return node_dim<3>(a, threads, depth, vec, np, args);
+    if (a.g.dim == 2) return node_dim<2>(a, threads, depth, vec, np, args);
+    return node_dim<1>(a, threads, depth, vec, np, args);
+}
+
+int fused_lattice_valid_launch(const Geometry &g, int threads, int depth) {
+    const int vec = (g.X % 4 == 0 && g.P % 4 == 0) ? 4 : 1;
+    const int nvec = g.P / vec;
+    if (threads < 32 || threads > 256 || threads % 32) return 0;
+    if ((nvec + threads - 1) / threads > NVMAX) return 0;
+    if (depth != 1 && depth != 2 && depth != 4) return 0;
+    return fused_lattice_smem_bytes(g, depth, vec) <= 227 * 1024;
+}
+
 cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
                                  int depth, cudaStream_t s) {
-    const int vec = (a.g.X % 4 == 0 && a.g.P % 4 == 0) ? 4 : 1;
-    if (a.g.dim == 3) return launch_dim<3>(a, sched, threads, depth, vec, s);
-    if (a.g.dim == 2) return launch_dim<2>(a, sched, threads, depth, vec, s);
-    return launch_dim<1>(a, sched, threads, depth, vec, s);
+    cudaKernelNodeParams np;
+    void *args[2] = {const_cast<FusedArgs *>(&a), const_cast<Schedule *>(&sched)};
+    cudaError_t e = fused_lattice_node(a, threads, depth, &np, args);
+    if (e != cudaSuccess) return e;
+    if (np.gridDim.x == 0) return cudaSuccess;
+    return cudaLaunchKernel(np.func, np.gridDim, np.blockDim, np.kernelParams, np.sharedMemBytes, s);
 }
 
 cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s) {

@@ -76,6 +76,12 @@ enum { KERR_TIMEOUT = 1, KERR_BOUNDS = 2 };
 cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
                                  int depth, cudaStream_t s);
 int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec);
+// Kernel-node parameters of the same launch (for CUDA graphs); args[0..1]
+// must point at the FusedArgs and Schedule values to pass.
+cudaError_t fused_lattice_node(const FusedArgs &a, int threads, int depth,
+                               cudaKernelNodeParams *np, void **args);
+// 1 if (threads, depth) is a valid launch shape for this geometry.
+int fused_lattice_valid_launch(const Geometry &g, int threads, int depth);
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
 
 cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s);

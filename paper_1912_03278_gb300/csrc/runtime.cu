@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -826,6 +827,287 @@ ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n)
     if (dout) cudaFree(dout);
     if (dtab) cudaFree(dtab);
     return st;
+}
+
+ising_status ising_hmc_set_launch(ising_hmc_t *h, int threads, int depth) {
+    if (!h) return ISING_EINVAL;
+    if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "launch shape applies to the FP32 lattice form");
+    if (!fused_lattice_valid_launch(h->g, threads, depth))
+        return fail(h, ISING_EINVAL, "invalid launch shape threads=%d depth=%d", threads, depth);
+    h->threads = threads;
+    h->depth = depth;
+    return ISING_OK;
+}
+
+ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth) {
+    if (!h || !threads || !depth) return ISING_EINVAL;
+    *threads = h->threads;
+    *depth = h->depth;
+    return ISING_OK;
+}
+
+// Autotuner: time one trajectory of every valid (threads, depth) on a
+// temporary copy of the handle's geometry and parameters (so the handle's own
+// chains do not move) and keep the fastest.
+ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
+    if (!h) return ISING_EINVAL;
+    if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "autotune applies to the FP32 lattice form");
+    if (reps < 1) reps = 1;
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    // temporary handle: same lattice and first chains' parameters, at most 2 waves of CTAs
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nt = std::min(h->n_chains, std::max(1, 2 * nsm));
+    ising_hmc_config cfg{};
+    cfg.kind = ISING_KIND_LATTICE;
+    cfg.dim = h->dim;
+    for (int d = 0; d < 3; ++d) cfg.L[d] = h->L[d];
+    std::vector<double> beta(nt), C(nt), eps(nt), h0(nt);
+    for (int c = 0; c < nt; ++c) {
+        beta[c] = h->params[c].beta;
+        C[c] = h->params[c].C;
+        eps[c] = h->params[c].eps;
+        h0[c] = h->params[c].hp / h->params[c].beta;
+    }
+    cfg.Jnn = h->params[0].bJ / h->params[0].beta;
+    cfg.beta = beta[0];
+    cfg.C = C[0];
+    cfg.eps = eps[0];
+    cfg.beta_chain = beta.data();
+    cfg.C_chain = C.data();
+    cfg.eps_chain = eps.data();
+    cfg.h0_chain = h0.data();
+    cfg.n_md = h->n_md;
+    cfg.n_chains = nt;
+    cfg.precision = ISING_PREC_FP32;
+    cfg.integrator = h->integrator;
+    cfg.stream = h->stream;
+    ising_hmc *t = nullptr;
+    st = ising_hmc_create(&cfg, &t);
+    if (st != ISING_OK) return fail(h, st, "autotune: %s", ising_hmc_last_create_error());
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int bt = h->threads, bd = h->depth;
+    const int cand_t[] = {32, 64, 96, 128, 160, 192, 224, 256};
+    const int cand_d[] = {1, 2, 4};
+    for (int th : cand_t) {
+        for (int dp : cand_d) {
+            if (!fused_lattice_valid_launch(h->g, th, dp)) continue;
+            t->threads = th;
+            t->depth = dp;
+            if (ising_hmc_trajectories(t, 1, 99) != ISING_OK) continue;  // warm-up
+            cudaEventRecord(e0, t->stream);
+            ising_hmc_trajectories(t, reps, 99);
+            cudaEventRecord(e1, t->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms / reps < best) {
+                best = ms / reps;
+                bt = th;
+                bd = dp;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ising_hmc_destroy(t);
+    h->threads = bt;
+    h->depth = bd;
+    if (best_ms) *best_ms = best;
+    return ISING_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Groups: several FP32 lattice handles (any mix of lattice sizes) advanced by
+// one CUDA-graph launch with one kernel node per member, nodes independent so
+// they run concurrently.
+// ---------------------------------------------------------------------------
+struct ising_group {
+    std::vector<ising_hmc *> m;
+    std::vector<FusedArgs> args;
+    std::vector<std::array<void *, 2>> argv;
+    std::vector<cudaGraphNode_t> nodes;
+    std::vector<int> shape;  // threads, depth per member at instantiation
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    int64_t launches = 0;
+    char err[512] = {0};
+};
+
+static ising_status gfail(ising_group *g, ising_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g ? g->err : g_create_err, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+static void group_free_graph(ising_group *g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->exec = nullptr;
+    g->graph = nullptr;
+    g->nodes.clear();
+}
+
+static ising_status group_build_graph(ising_group *g) {
+    group_free_graph(g);
+    const size_t n = g->m.size();
+    g->args.resize(n);
+    g->argv.resize(n);
+    g->nodes.resize(n);
+    g->shape.assign(2 * n, 0);
+    if (cudaGraphCreate(&g->graph, 0) != cudaSuccess) return gfail(g, ISING_ECUDA, "graph create failed");
+    for (size_t i = 0; i < n; ++i) {
+        ising_hmc *h = g->m[i];
+        g->args[i] = fused_args(h);
+        g->args[i].mode = MODE_TRAJ;
+        g->args[i].n_traj = 1;
+        g->argv[i] = {&g->args[i], &h->sched};
+        cudaKernelNodeParams np;
+        cudaError_t e = fused_lattice_node(g->args[i], h->threads, h->depth, &np, g->argv[i].data());
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g->nodes[i], g->graph, nullptr, 0, &np);
+        if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph node: %s", cudaGetErrorString(e));
+        g->shape[2 * i] = h->threads;
+        g->shape[2 * i + 1] = h->depth;
+    }
+    cudaError_t e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return ISING_OK;
+}
+
+ising_status ising_group_create(ising_hmc_t *const *members, int n, ising_group_t **out) {
+    g_create_err[0] = 0;
+    if (!members || n < 1 || !out) return gfail(nullptr, ISING_EINVAL, "group: need members");
+    *out = nullptr;
+    ising_group *g = new (std::nothrow) ising_group();
+    if (!g) return gfail(nullptr, ISING_ENOMEM, "group: host allocation failed");
+    for (int i = 0; i < n; ++i) {
+        if (!members[i] || !is_fp32_lattice(members[i])) {
+            delete g;
+            return gfail(nullptr, ISING_EINVAL, "group member %d is not an FP32 lattice handle", i);
+        }
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) {
+                delete g;
+                return gfail(nullptr, ISING_EINVAL, "group member %d repeated", i);
+            }
+        g->m.push_back(members[i]);
+    }
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming) != cudaSuccess) {
+        delete g;
+        return gfail(nullptr, ISING_ECUDA, "group: stream/event creation failed");
+    }
+    ising_status st = group_build_graph(g);
+    if (st != ISING_OK) {
+        std::snprintf(g_create_err, sizeof g_create_err, "%s", g->err);
+        group_free_graph(g);
+        cudaEventDestroy(g->ev);
+        cudaStreamDestroy(g->stream);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return ISING_OK;
+}
+
+ising_status ising_group_trajectories(ising_group_t *g, int64_t n, uint64_t seed) {
+    if (!g) return ISING_EINVAL;
+    std::vector<uint64_t> seeds(g->m.size(), seed);
+    return ising_group_trajectories_seeds(g, n, seeds.data());
+}
+
+ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const uint64_t *seeds) {
+    if (!g || !seeds) return ISING_EINVAL;
+    if (n < 0) return gfail(g, ISING_EINVAL, "n must be >= 0");
+    if (n == 0) return ISING_OK;
+    // rebuild if a member's launch shape changed (autotune, set_launch)
+    for (size_t i = 0; i < g->m.size(); ++i)
+        if (g->shape[2 * i] != g->m[i]->threads || g->shape[2 * i + 1] != g->m[i]->depth) {
+            ising_status st = group_build_graph(g);
+            if (st != ISING_OK) return st;
+            break;
+        }
+    // trajectories per graph launch: bounded work per kernel, like the single-handle path
+    int64_t per = 4096;
+    for (ising_hmc *h : g->m) {
+        const double work = (double)h->N * h->n_chains * h->sched.n_pass;
+        per = std::min<int64_t>(per, (int64_t)std::max(1.0, std::floor(4.0e9 / std::max(work, 1.0))));
+        if (h->traj + n > (int64_t)0xfffffffe) return gfail(g, ISING_EINVAL, "trajectory counter overflow");
+    }
+    // order after work already queued on the members' streams
+    for (ising_hmc *h : g->m) {
+        if (cudaEventRecord(g->ev, h->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(g->stream, g->ev, 0) != cudaSuccess)
+            return gfail(g, ISING_ECUDA, "group: stream ordering failed");
+    }
+    int64_t done = 0;
+    while (done < n) {
+        const int64_t k = std::min(per, n - done);
+        for (size_t i = 0; i < g->m.size(); ++i) {
+            ising_hmc *h = g->m[i];
+            g->args[i] = fused_args(h);
+            g->args[i].mode = MODE_TRAJ;
+            g->args[i].seed = seeds[i];
+            g->args[i].traj0 = (uint32_t)(h->traj + done);
+            g->args[i].n_traj = (int)k;
+            cudaKernelNodeParams np;
+            cudaError_t e = fused_lattice_node(g->args[i], h->threads, h->depth, &np, g->argv[i].data());
+            if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(g->exec, g->nodes[i], &np);
+            if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph update: %s", cudaGetErrorString(e));
+        }
+        cudaError_t e = cudaGraphLaunch(g->exec, g->stream);
+        if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        g->launches += 1;
+        done += k;
+    }
+    for (ising_hmc *h : g->m) {
+        h->traj += n;
+        h->launches += (n + per - 1) / per;
+    }
+    // members' later work waits for the group's
+    if (cudaEventRecord(g->ev, g->stream) != cudaSuccess) return gfail(g, ISING_ECUDA, "group: event");
+    for (ising_hmc *h : g->m)
+        if (cudaStreamWaitEvent(h->stream, g->ev, 0) != cudaSuccess)
+            return gfail(g, ISING_ECUDA, "group: stream ordering failed");
+    return ISING_OK;
+}
+
+ising_status ising_group_sync(ising_group_t *g) {
+    if (!g) return ISING_EINVAL;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess)
+        return gfail(g, ISING_ECUDA, "group sync: %s", cudaGetErrorString(cudaGetLastError()));
+    for (ising_hmc *h : g->m) {
+        ising_status st = ising_hmc_sync(h);
+        if (st != ISING_OK) return gfail(g, st, "member: %s", h->err);
+    }
+    return ISING_OK;
+}
+
+int64_t ising_group_launch_count(const ising_group_t *g) { return g ? g->launches : -1; }
+
+void *ising_group_stream(const ising_group_t *g) { return g ? (void *)g->stream : nullptr; }
+
+const char *ising_group_last_error(const ising_group_t *g) { return g ? g->err : g_create_err; }
+
+void ising_group_destroy(ising_group_t *g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    group_free_graph(g);
+    if (g->ev) cudaEventDestroy(g->ev);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
 }
 
 void ising_hmc_destroy(ising_hmc_t *h) {

@@ -1,0 +1,83 @@
+"""Mixed lattice sizes in one CUDA-graph launch, and the launch-shape autotuner."""
+import numpy as np
+import pytest
+
+import paper_1912_03278_gb300 as pkg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+
+
+def _members():
+    return [
+        dict(dim=2, L=(16, 16), beta=np.array([0.4, 0.44, 0.48]), h=0.0, eps=0.1, n_md=6,
+             n_chains=3),
+        dict(dim=3, L=(8, 8, 8), beta=0.2217, h=0.05, eps=0.1, n_md=5, n_chains=4,
+             flip_every=3),
+        dict(dim=2, L=(12, 20), beta=0.3, h=0.02, eps=0.12, n_md=4, n_chains=2),
+        dict(dim=3, L=(6, 5, 7), beta=0.2, h=0.0, eps=0.1, n_md=4, n_chains=2),
+    ]
+
+
+def test_group_matches_members_run_alone():
+    alone = [pkg.IsingHMC(**kw) for kw in _members()]
+    mixed = [pkg.IsingHMC(**kw) for kw in _members()]
+    grp = pkg.IsingGroup(mixed)
+    try:
+        for s in alone:
+            s.trajectories(7, 123)
+        grp.trajectories(4, 123)
+        grp.trajectories(3, 123)
+        grp.sync()
+        for a, b in zip(alone, mixed):
+            assert np.array_equal(a.state(), b.state())
+            assert np.array_equal(a.chain_sums(), b.chain_sums())
+            assert a.traj_index == b.traj_index == 7
+        assert grp.launches <= 2
+    finally:
+        grp.close()
+        for s in alone + mixed:
+            s.close()
+
+
+def test_group_then_member_calls_stay_ordered():
+    sims = [pkg.IsingHMC(**kw) for kw in _members()[:2]]
+    ref = [pkg.IsingHMC(**kw) for kw in _members()[:2]]
+    grp = pkg.IsingGroup(sims)
+    try:
+        grp.trajectories(2, 5)
+        sims[0].trajectories(2, 5)
+        grp.trajectories(1, 5)
+        ref[0].trajectories(5, 5)
+        ref[1].trajectories(3, 5)
+        assert np.array_equal(sims[0].state(), ref[0].state())
+        assert np.array_equal(sims[1].state(), ref[1].state())
+    finally:
+        grp.close()
+        for s in sims + ref:
+            s.close()
+
+
+def test_autotune_picks_valid_shape_and_keeps_chain():
+    sim = pkg.IsingHMC(dim=3, L=(16, 16, 16), beta=0.2217, h=0.05, eps=0.1, n_md=4, n_chains=8)
+    try:
+        before = sim.state()
+        ms = sim.autotune(reps=1)
+        assert ms > 0
+        t, d = sim.launch
+        assert 32 <= t <= 256 and d in (1, 2, 4)
+        assert np.array_equal(before, sim.state())   # the handle's chains did not move
+        assert sim.traj_index == 0
+        sim.trajectories(2, 9)
+        assert np.all(np.isfinite(sim.state()))
+        with pytest.raises(pkg.IsingError):
+            sim.set_launch(48, 2)
+    finally:
+        sim.close()
