@@ -94,7 +94,7 @@ def test_admission_by_memory_budget():
 def test_oversized_request_rejected():
     srv = pkg.IsingServer(1 << 20, 2)
     try:
-        rid = srv.submit(**REQ[0])
+        rid = srv.submit(**dict(REQ[0], L=(512, 512)))   # 16 MB of state, budget 1 MB
         srv.drain(30.0)
         r = srv.poll(rid)
         assert r["state"] == 3 and r["status"] == binding.ISING_ENOMEM
