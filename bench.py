@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -221,13 +224,16 @@ def tune_eps(sims, betas_per_chain, rounds, seed, therm=4):
     from scipy.special import erfcinv
     target = 4.0 * erfcinv(TARGET_ACC) ** 2
     ub = np.unique(betas_per_chain)
+    trace = {}
     for L, sim in sims.items():
         eps = np.full(len(betas_per_chain), EPS0.get(L, 0.05))
         sim.trajectories(therm, seed + 999)
+        trace[str(L)] = []
         for r in range(rounds):
             sim.trajectories(1, seed + 1000 + r)
             dH = sim.records()[:, 0]
             pacc = np.minimum(1.0, np.exp(-np.clip(dH, -50, 50)))
+            trace[str(L)].append(round(float(pacc.mean()), 3))
             for b in ub:
                 sel = betas_per_chain == b
                 a = float(np.clip(pacc[sel].mean(), 1e-3, 1 - 1e-6))
@@ -235,6 +241,8 @@ def tune_eps(sims, betas_per_chain, rounds, seed, therm=4):
                 eps[sel] *= float(np.clip((target / eff) ** 0.25, 0.5, 2.0))
             sim.set_eps(eps)
         sim._eps = eps.copy()
+        trace[str(L)].append([round(float(eps.min()), 4), round(float(eps.max()), 4)])
+    return trace
 
 
 def run_ours(args):
@@ -258,7 +266,7 @@ def run_ours(args):
                                stream=stream.cuda_stream)
     seed = 1234 + 7919 * rank
     hot_start(pkg, sims, seed)
-    tune_eps(sims, betas, args.tune_rounds, seed)
+    tune_trace = tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
         sims[L].reset_sums()
 
@@ -326,6 +334,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (state %.1f GB)"
                              % (16 * sum(L * L for L in Ls) * n_chains / 1e9)},
             "acceptance": {str(L): obs[L]["acceptance"] for L in Ls},
+            "tuning": tune_trace,
             "roofline": roofline,
             "gpu_launches": int(launches)}
 
@@ -336,6 +345,14 @@ def run_ours(args):
             line["speedup_vs_plain"] = value / ws / line["plain_form"]["value"]
         if not args.no_e2e:
             line["e2e"] = e2e_rate(pkg, sims, Ls, n_chains, seed, stream)
+    for s in sims.values():
+        s.close()
+    sims = {}
+    if rank == 0:
+        if not args.no_mixed:
+            line["mixed_3d"] = mixed_3d_rate(pkg)
+        if not args.no_serve:
+            line["serve"] = serve_run(pkg, args.serve_seconds)
         if not args.no_cpu:
             import oracle
             oracle.build()
@@ -345,8 +362,6 @@ def run_ours(args):
                                     "sample": "%d chains of L=%d (one per core), 1 trajectory, "
                                               "N_md=%d, %.1f s" % (cores, big, N_MD, dt)}
         print(json.dumps(line), flush=True)
-    for s in sims.values():
-        s.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
@@ -378,6 +393,116 @@ def plain_rate(pkg, L, betas, C, tuned, stream):
                 "acceptance_sample": acc}
     finally:
         sim.close()
+
+
+def mixed_3d_rate(pkg, steps=4, seed=31):
+    """3D simple-cubic lattices L in {16,24,32,48,64}, 64 chains each, J=1,
+    h=0.05, beta=0.2217, C=6 beta+0.1, N_md=floor(ln N), eps=1/(N_md sqrt(beta))
+    (unit trajectory length in the paper's units): one autotuned CUDA-graph
+    launch per step for all five sizes."""
+    import torch
+    beta = 0.2217
+    sims = []
+    for L in (16, 24, 32, 48, 64):
+        n_md = workloads.n_md_default(L ** 3)
+        sims.append(pkg.IsingHMC(dim=3, L=(L, L, L), beta=beta, h=0.05, C=6 * beta + 0.1,
+                                 eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md, n_chains=64))
+    tuned = {}
+    for s in sims:
+        ms = s.autotune(reps=1)
+        tuned[s.kw["L"][0]] = dict(zip(("threads", "depth"), s.launch), ms=ms)
+    grp = pkg.IsingGroup(sims)
+    try:
+        grp.trajectories(2, seed)
+        grp.sync()
+        l0 = grp.launches
+        t0 = time.perf_counter()
+        grp.trajectories(steps, seed)
+        grp.sync()
+        dt = time.perf_counter() - t0
+        work = sum(s.kw["L"][0] ** 3 * 64 * s.kw["n_md"] for s in sims) * steps
+        acc = [s.observables()["acceptance"] for s in sims]
+        return {"value": work / dt, "unit": UNIT, "graph_launches": grp.launches - l0,
+                "steps": steps, "sites": sum(s.kw["L"][0] ** 3 * 64 for s in sims),
+                "tuned_launch": tuned, "acceptance": acc}
+    finally:
+        grp.close()
+        for s in sims:
+            s.close()
+
+
+def serve_requests(rng, n, scale):
+    """Requests drawn as in the serving workload: 2D L in [32,1024] or 3D L in
+    [16,64], beta in [0.15,0.6], h in [0,0.2], 100-5000 trajectories (times
+    `scale`, at least 1), 1-256 chains; N_md = floor(ln N), eps = 1/(N_md
+    sqrt(beta)), C = 2d beta + 0.1.  Dense requests are not drawn."""
+    out = []
+    for _ in range(n):
+        dim = 2 if rng.random() < 0.5 else 3
+        L = int(rng.integers(32, 1025)) if dim == 2 else int(rng.integers(16, 65))
+        if dim == 3 and L % 4:
+            L += 4 - L % 4   # keep the vector path; the scalar path serves any L
+        N = L ** dim
+        beta = float(rng.uniform(0.15, 0.6))
+        n_md = workloads.n_md_default(N)
+        chains = int(rng.integers(1, 257))
+        traj = max(1, int(round(int(rng.integers(100, 5001)) * scale)))
+        out.append(dict(n_traj=traj, seed=int(rng.integers(1, 2 ** 31)), dim=dim,
+                        L=(L,) * dim, beta=beta, h=float(rng.uniform(0, 0.2)),
+                        C=2 * dim * beta + 0.1, eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md,
+                        n_chains=chains))
+    return out
+
+
+def serve_run(pkg, seconds, rate=200.0, rho=0.8, seed=2, budget_gb=120.0):
+    """Serving: measure the server's capacity on a saturating batch, then
+    Poisson arrivals at `rate` requests/s for `seconds`, with trajectory counts
+    scaled so the offered load is `rho` of that capacity; p50/p99 latency."""
+    rng = np.random.default_rng(seed)
+    work = lambda r: (np.prod(r["L"]) * r["n_chains"] * r["n_traj"] * r["n_md"])
+    # mean work of an unscaled request, from a large sample
+    mean_w = float(np.mean([work(r) for r in serve_requests(np.random.default_rng(7), 4000, 1.0)]))
+    srv = pkg.IsingServer(int(budget_gb * 1e9), 4)
+    try:
+        cal = serve_requests(rng, 64, 0.02)
+        t0 = time.perf_counter()
+        for r in cal:
+            srv.submit(**r)
+        srv.drain(600.0)
+        cap = sum(work(r) for r in cal) / (time.perf_counter() - t0)
+    finally:
+        srv.close()
+    scale = rho * cap / (rate * mean_w)
+    n = int(rng.poisson(rate * seconds))
+    arrivals = np.sort(rng.uniform(0, seconds, n))
+    reqs = serve_requests(rng, n, scale)
+    srv = pkg.IsingServer(int(budget_gb * 1e9), 4)
+    try:
+        ids = []
+        t0 = time.perf_counter()
+        for ta, r in zip(arrivals, reqs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(**r))
+        t_sub = time.perf_counter() - t0
+        peak_queue = srv.stats()["queued"]
+        srv.drain(600.0)
+        t_all = time.perf_counter() - t0
+        res = [srv.poll(i) for i in ids]
+        st = srv.stats()
+    finally:
+        srv.close()
+    lat = np.array([r["latency"] for r in res if r["state"] == 2])
+    done_work = sum(work(r) for r, x in zip(reqs, res) if x["state"] == 2)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "requests": n, "completed": int(st["completed"]),
+            "rejected": int(st["rejected"]), "rho": rho, "arrival_rate": rate,
+            "arrival_seconds": seconds, "submit_seconds": t_sub, "total_seconds": t_all,
+            "site_steps_per_s": done_work / t_all, "capacity_site_steps_per_s": cap,
+            "trajectory_scale": scale, "queued_at_end_of_arrivals": int(peak_queue),
+            "shared_graph_launches": int(st["group_launches"]), "quanta": int(st["quanta"]),
+            "dense_requests": "not drawn (no dense tensor-core path yet)"}
 
 
 def e2e_rate(pkg, sims, Ls, n_chains, seed, stream, steps=3):
