@@ -199,22 +199,30 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm ----
-def hot_start(pkg, sims, seed):
-    """Start every chain in the wells psi_i = +-1 (random signs), the large-C
-    minima of Sec. 3 in these units, generated on the device."""
+def hot_start(pkg, sims, seed, C):
+    """Start every chain from random spins s = +-1 dressed with the HS field's
+    conditional fluctuation: given s, phi = A psi ~ N(A s, A) (Sec. 2,
+    Eq. did_HS_trafo), i.e. psi = s + A^{-1/2} xi, taken as s + xi/sqrt(C).
+    Local fluctuations are then already typical, so step-size tuning sees
+    representative energy violations.  Generated on the device."""
     import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     for L, sim in sims.items():
-        n = pkg.binding.load().ising_hmc_n_chains(sim.h) * L * L
+        n_chains = pkg.binding.load().ising_hmc_n_chains(sim.h)
+        n = n_chains * L * L
         psi = torch.randint(0, 2, (n,), device="cuda", generator=g, dtype=torch.int8)
         psi = psi.to(torch.float32).mul_(2.0).sub_(1.0)
+        scale = torch.tensor(1.0 / np.sqrt(C), dtype=torch.float32, device="cuda")
+        noise = torch.randn(n_chains, L * L, device="cuda", generator=g, dtype=torch.float32)
+        psi.view(n_chains, L * L).add_(noise.mul_(scale[:, None]))
+        del noise
         torch.cuda.synchronize()
         pkg.ising_hmc_set_state_native(sim.h, psi.data_ptr(), 0)
         del psi
 
 
-def tune_eps(sims, betas_per_chain, rounds, seed, therm=4):
+def tune_eps(sims, betas_per_chain, rounds, seed, therm=6):
     """Step-size tuning during equilibration only (frozen afterwards).  For a
     second-order integrator the mean energy violation grows as eps^4 and the
     acceptance is erfc(sqrt(<dH>)/2); each round estimates the acceptance per
@@ -265,7 +273,7 @@ def run_ours(args):
                                n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
                                stream=stream.cuda_stream)
     seed = 1234 + 7919 * rank
-    hot_start(pkg, sims, seed)
+    hot_start(pkg, sims, seed, C)
     tune_trace = tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
         sims[L].reset_sums()
