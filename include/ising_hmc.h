@@ -310,6 +310,14 @@ ising_status ising_hmc_energy_noalloc(int dim, const int L[3], double beta, doub
                                       double *out, void *stream);
 const char *ising_hmc_energy_noalloc_error(void);
 
+/* Self-test of the BF16 tensor-core GEMM behind the dense force:
+ * D[n*M + m] = sum_k A[m*K + k] * B[n*K + k] for host BF16 bit patterns A
+ * (M x K) and B (N x K), FP32 host output D; M and N multiples of 128, K a
+ * multiple of 64.  Synchronous.  Errors: EINVAL, ECUDA, ETIMEOUT (a pipeline
+ * wait gave up). */
+ising_status ising_hmc_selftest_gemm(int M, int N, int K, const uint16_t *A, const uint16_t *B,
+                                     float *D);
+
 void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);

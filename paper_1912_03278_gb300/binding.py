@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "ising_hmc_launch_count": (c_int64, [P]),
         "ising_hmc_sync": (c_int, [P]),
         "ising_hmc_selftest": (c_int, [c_int, P, P, c_int64]),
+        "ising_hmc_selftest_gemm": (c_int, [c_int, c_int, c_int, P, P, P]),
         "ising_hmc_set_launch": (c_int, [P, c_int, c_int]),
         "ising_hmc_get_launch": (c_int, [P, P, P]),
         "ising_hmc_autotune": (c_int, [P, c_int, P]),
@@ -524,6 +525,18 @@ def ising_hmc_energy_noalloc(dim, L, beta, Jnn, C, h0, n_chains, psi_ptr, p_ptr,
 
 def ising_hmc_energy_noalloc_error() -> str:
     return (load().ising_hmc_energy_noalloc_error() or b"").decode()
+
+
+def ising_hmc_selftest_gemm(A_bf16_bits, B_bf16_bits) -> np.ndarray:
+    """D (N x M, n-major) = B A^T from BF16 bit patterns (uint16 arrays M x K, N x K)."""
+    A = np.ascontiguousarray(A_bf16_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bf16_bits, dtype=np.uint16)
+    M, K = A.shape
+    N = B.shape[0]
+    D = np.zeros((N, M), dtype=np.float32)
+    _check(None, load().ising_hmc_selftest_gemm(M, N, K, A.ctypes.data, B.ctypes.data,
+                                                D.ctypes.data))
+    return D
 
 
 def ising_hmc_destroy(h):

@@ -62,12 +62,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             if verbose and msg:
                 print(msg)
     if force or jobs or _stale(LIB, objs):
-        cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcuda"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            # libcuda is only needed for driver entry points; link without it if absent
-            cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs]
-            subprocess.check_call(cmd)
+        # the CUDA runtime is linked statically; driver entry points are looked up
+        # at run time, so the library loads on machines without a GPU driver
+        subprocess.check_call([cc, *ARCH, "-shared", "-o", LIB, *objs])
     return LIB
 
 

@@ -1,0 +1,431 @@
+// dense.cu -- dense all-to-all couplings on the tensor cores.
+//
+// For a block of chains Psi (chains x sites, chain-major) the force of Sec. 3,
+// F = A (tanh(A psi + h') - psi) with A = beta*J + C*1, is two BF16 tcgen05
+// GEMMs per force evaluation, G = J Psi^T, with fused FP32 epilogues:
+//   pass 1:  a = beta G + C psi,  u = tanh(a + h') - psi      -> U (FP32, BF16)
+//   pass 2:  F = beta (J U^T) + C u,  p += kick F,  psi += drift p  (FP32, BF16)
+// beta and C stay in the FP32 epilogue, so one BF16 copy of J serves every
+// chain's beta.  The action of the end point needs a = A psi to FP64
+// accuracy: a double-float GEMM on the FP32 pipe (exact products through FMA,
+// compensated sums) followed by a per-chain kernel that evaluates S, the Sec. 4
+// estimators, dH and the Metropolis test (Sec. 3).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "df32.cuh"
+#include "device_common.cuh"
+#include "internal.h"
+#include "tc_gemm.cuh"
+
+namespace ihmc {
+namespace {
+
+// ---------------------------------------------------------------- GEMM tests
+struct StoreEpi {
+    float *out;
+    int M;
+    __device__ void operator()(int m, int n0, const float (&v)[32]) const {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) out[(int64_t)(n0 + j) * M + m] = v[j];
+    }
+};
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    gemm_store_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                      float *out, int M, int K, int *err) {
+    StoreEpi epi{out, M};
+    tc::gemm_tile(&ta, &tb, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K / tc::BK, epi, err);
+}
+
+// ------------------------------------------------------- force epilogues
+__device__ __forceinline__ float hprime_f(const DenseArgs &d, const ChainParams &pr, int m) {
+    return d.hdf ? pr.betaf * d.hdf[m].x : pr.hpf;
+}
+
+// u = tanh(beta G + C psi + h') - psi for the 32 chains n0.. of site m.
+struct Epi1 {
+    const DenseArgs *d;
+    __device__ void operator()(int m, int n0, const float (&v)[32]) const {
+        const DenseArgs &D = *d;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int n = n0 + j;
+            const int64_t idx = (int64_t)n * D.N + m;
+            float u = 0.0f;
+            if (n < D.n_chains) {
+                const ChainParams &pr = D.params[n];
+                const float ps = D.psi[idx];
+                const float a = fmaf(pr.betaf, v[j], pr.Cf * ps);
+                u = tanh_f(a + hprime_f(D, pr, m)) - ps;
+            }
+            D.u32[idx] = u;
+            D.u16[idx] = __float2bfloat16_rn(u);
+        }
+    }
+};
+
+// F = beta (J U) + C u; p += kick F; psi += drift p.
+struct Epi2 {
+    const DenseArgs *d;
+    float kick, drift;   // schedule coefficients (times each chain's eps)
+    bool do_drift;
+    __device__ void operator()(int m, int n0, const float (&v)[32]) const {
+        const DenseArgs &D = *d;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int n = n0 + j;
+            if (n >= D.n_chains) continue;
+            const int64_t idx = (int64_t)n * D.N + m;
+            const ChainParams &pr = D.params[n];
+            const float F = fmaf(pr.betaf, v[j], pr.Cf * D.u32[idx]);
+            const float p = fmaf(kick * pr.epsf, F, D.p[idx]);
+            D.p[idx] = p;
+            if (do_drift) {
+                const float ps = fmaf(drift * pr.epsf, p, D.psi[idx]);
+                D.psi[idx] = ps;
+                D.psi16[idx] = __float2bfloat16_rn(ps);
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    force1_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tpsi,
+                  const __grid_constant__ DenseArgs d) {
+    Epi1 epi{&d};
+    tc::gemm_tile(&tj, &tpsi, blockIdx.x * tc::BM, blockIdx.y * tc::BN, d.N / tc::BK, epi, d.err);
+}
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    force2_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tu,
+                  const __grid_constant__ DenseArgs d, float kick, float drift, int do_drift) {
+    Epi2 epi{&d, kick, drift, do_drift != 0};
+    tc::gemm_tile(&tj, &tu, blockIdx.x * tc::BM, blockIdx.y * tc::BN, d.N / tc::BK, epi, d.err);
+}
+
+// ------------------------------------------------------------- state helpers
+__global__ void k_copy_state(const float *__restrict__ src, float *__restrict__ dst,
+                             __nv_bfloat16 *__restrict__ dst16, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = src[i];
+        dst[i] = v;
+        if (dst16) dst16[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// p ~ N(0,1), FP32 form: sites 4q..4q+3 of chain n from one Philox call.
+__global__ void k_dense_momenta(float *__restrict__ p, int N, int n_chains, int b_pad,
+                                uint64_t seed, uint32_t traj) {
+    const int64_t nq = (int64_t)b_pad * (N / 4);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i / (N / 4));
+        const int q = (int)(i % (N / 4));
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < n_chains) z = momenta4_f32((uint32_t)q, traj, (uint32_t)n, seed);
+        reinterpret_cast<float4 *>(p)[i] = z;
+    }
+}
+
+// ------------------------------------------- FP64-accurate G = J Psi^T on FP32
+// Double-float GEMM: J = Jhi + Jlo (two FP32), psi exact in FP32; every product
+// Jhi*psi is split exactly by an FMA, Jlo*psi is added to the error word, and
+// the running sum is kept as a TwoSum pair.  Tile 64 sites x 64 chains, 256
+// threads with 4 x 4 outputs each, K slabs of 16 in shared memory.
+constexpr int DG_T = 64, DG_K = 16;
+
+__global__ void __launch_bounds__(256) k_df_gemm(const float *__restrict__ Jhi,
+                                                 const float *__restrict__ Jlo,
+                                                 const float *__restrict__ psi, float *__restrict__ Ghi,
+                                                 float *__restrict__ Glo, int N) {
+    __shared__ float sJh[DG_K][DG_T + 4], sJl[DG_K][DG_T + 4], sP[DG_K][DG_T + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.x * DG_T, n0 = blockIdx.y * DG_T;
+    float s[4][4], c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[i][j] = c[i][j] = 0.0f;
+    for (int k0 = 0; k0 < N; k0 += DG_K) {
+        // 64 rows x 16 k of each operand: 1024 values, 4 per thread
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = threadIdx.x + r * 256;
+            const int row = e >> 4, kk = e & 15;
+            sJh[kk][row] = Jhi[(int64_t)(m0 + row) * N + k0 + kk];
+            sJl[kk][row] = Jlo[(int64_t)(m0 + row) * N + k0 + kk];
+            sP[kk][row] = psi[(int64_t)(n0 + row) * N + k0 + kk];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < DG_K; ++kk) {
+            float ah[4], al[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ah[i] = sJh[kk][ty * 4 + i];
+                al[i] = sJl[kk][ty * 4 + i];
+                b[i] = sP[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = __fmul_rn(ah[i], b[j]);
+                    float e = __fmaf_rn(ah[i], b[j], -p);
+                    e = __fmaf_rn(al[i], b[j], e);
+                    const f2 t = two_sum(s[i][j], p);
+                    s[i][j] = t.hi;
+                    c[i][j] = __fadd_rn(c[i][j], __fadd_rn(t.lo, e));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const f2 r = fast_two_sum(s[i][j], c[i][j]);
+            const int64_t idx = (int64_t)(n0 + tx * 4 + j) * N + (m0 + ty * 4 + i);
+            Ghi[idx] = r.hi;
+            Glo[idx] = r.lo;
+        }
+}
+
+// ----------------------------------------- per-chain action, dH, Metropolis
+// mode 0: end of a trajectory (psi_w = proposal, p = end momenta, K0 from the
+// regenerated momenta, Metropolis test, copy to psi_cur on accept);
+// mode 1: evaluate S and the estimators of psi_cur (G computed from psi_cur).
+__global__ void __launch_bounds__(256) k_dense_finalize(DenseArgs d, int mode, uint32_t traj,
+                                                        uint64_t seed, int measure) {
+    __shared__ float4 tab[LOG1PEXP_NODES];
+    __shared__ double red[32 * 8];
+    __shared__ int bcast;
+    const int n = blockIdx.x;
+    if (n >= d.n_chains) return;
+    for (int i = threadIdx.x; i < LOG1PEXP_NODES; i += blockDim.x) tab[i] = d.lpe_tab[i];
+    __syncthreads();
+    const ChainParams pr = d.params[n];
+    ChainState *st = d.state + n;
+    const float *psi = (mode == 0 ? d.psi : d.psi_cur) + (int64_t)n * d.N;
+    const f2 beta2 = df_from_double(pr.beta), C2 = df_from_double(pr.C), hp2 = df_from_double(pr.hp);
+    f2 S{0.f, 0.f}, K0{0.f, 0.f}, K1{0.f, 0.f};
+    float Slo = 0.f, K0lo = 0.f, K1lo = 0.f;
+    float sT = 0.f, cT = 0.f, sAT = 0.f, cAT = 0.f, sHT = 0.f, cHT = 0.f;
+    int sS = 0;
+    const uint32_t spin_traj = mode == 0 ? traj : TRAJ_INIT;
+    const uint64_t spin_seed = mode == 0 ? seed : 0;
+    for (int q = threadIdx.x; q < d.N / 4; q += blockDim.x) {
+        const float4 su = spin_u4_f32((uint32_t)q, spin_traj, (uint32_t)n, spin_seed);
+        const float suv[4] = {su.x, su.y, su.z, su.w};
+        float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mode == 0) p0 = momenta4_f32((uint32_t)q, traj, (uint32_t)n, seed);
+        const float p0v[4] = {p0.x, p0.y, p0.z, p0.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int m = 4 * q + k;
+            const int64_t idx = (int64_t)n * d.N + m;
+            const float ps = psi[m];
+            const f2 G{d.Ghi[idx], d.Glo[idx]};
+            const f2 a = df_add(df_mul(beta2, G), df_mul_f(C2, ps));
+            f2 x = a;
+            float hq = pr.hpf;
+            if (d.hdf) {
+                const f2 hp = df_mul(beta2, f2{d.hdf[m].x, d.hdf[m].y});
+                x = df_add(a, hp);
+                hq = hp.hi;
+            } else if (pr.hp != 0.0) {
+                x = df_add(a, hp2);
+            }
+            const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
+            const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, tab);
+            acc_add(S, Slo, df_mul_f(a, 0.5f * ps));
+            acc_add(S, Slo, df_neg(ax));
+            acc_add(S, Slo, df_neg(gl));
+            const float t = tanh_f(x.hi);
+            kahan_add(sT, cT, t);
+            kahan_add(sAT, cAT, a.hi * t);
+            kahan_add(sHT, cHT, hq * t);
+            sS += (suv[k] < (1.0f + t) * 0.5f) ? 1 : -1;
+            if (mode == 0) {
+                const float p1 = d.p[idx];
+                acc_add(K1, K1lo, two_prod(p1, 0.5f * p1));
+                acc_add(K0, K0lo, two_prod(p0v[k], 0.5f * p0v[k]));
+            }
+        }
+    }
+    double v[8] = {acc_val(K0, K0lo), acc_val(K1, K1lo), acc_val(S, Slo), kahan_val(sT, cT),
+                   kahan_val(sAT, cAT), kahan_val(sHT, cHT), (double)sS, 0.0};
+    block_sum<8>(v, red);
+    const double invN = 1.0 / (double)d.N;
+    if (threadIdx.x == 0) {
+        auto set_obs = [&]() {
+            const double m = v[3] * invN;
+            st->obs[0] = m;
+            st->obs[1] = 0.5 * pr.C - 0.5 * v[4] * invN - v[5] * invN;
+            st->obs[2] = fabs(v[6]) * invN;
+            st->obs[3] = fabs(m);
+        };
+        if (mode == 1) {
+            st->S = v[2];
+            set_obs();
+            bcast = 0;
+        } else {
+            const double S0 = st->S;
+            const double dH = (v[1] + v[2]) - (v[0] + S0);
+            const double logu = accept_logu(traj, (uint32_t)n, seed, PURPOSE_ACC);
+            const bool acc = logu < -dH;
+            st->rec[ISING_REC_DH] = dH;
+            st->rec[ISING_REC_LOGU] = logu;
+            st->rec[ISING_REC_ACCEPTED] = acc ? 1.0 : 0.0;
+            st->rec[ISING_REC_K0] = v[0];
+            st->rec[ISING_REC_S0] = S0;
+            st->rec[ISING_REC_K1] = v[1];
+            st->rec[ISING_REC_S1] = v[2];
+            st->rec[ISING_REC_FLIPPED] = 0.0;
+            if (acc) {
+                st->S = v[2];
+                set_obs();
+            }
+            if (measure) {
+                double *sm = st->sums;
+                sm[ISING_SUM_NMEAS] += 1.0;
+                sm[ISING_SUM_NACC] += acc ? 1.0 : 0.0;
+                sm[ISING_SUM_M] += st->obs[0];
+                sm[ISING_SUM_M2] += st->obs[0] * st->obs[0];
+                sm[ISING_SUM_E] += st->obs[1];
+                sm[ISING_SUM_E2] += st->obs[1] * st->obs[1];
+                sm[ISING_SUM_ABSM] += st->obs[2];
+                sm[ISING_SUM_ABSM2] += st->obs[2] * st->obs[2];
+                sm[ISING_SUM_DH] += dH;
+                sm[ISING_SUM_EXPMDH] += exp(-dH);
+            }
+            bcast = acc ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    if (bcast) {
+        float *dst = d.psi_cur + (int64_t)n * d.N;
+        for (int m = threadIdx.x; m < d.N; m += blockDim.x) dst[m] = psi[m];
+    }
+}
+
+template <class K>
+cudaError_t smem_attr(K kern, int bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace
+
+// Tensor map of a row-major BF16 matrix (rows x cols, cols contiguous) read in
+// boxes of box_rows x 64 with 128-byte swizzling.
+cudaError_t make_tmap_bf16(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
+                           int box_rows) {
+    // the driver entry point is looked up through the runtime, so the library
+    // does not link the driver library itself
+    using encode_fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static encode_fn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<encode_fn>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int N, int K, int *err,
+                              cudaStream_t s) {
+    CUtensorMap ta, tb;
+    cudaError_t e = make_tmap_bf16(&ta, A, M, K, tc::BM);
+    if (e == cudaSuccess) e = make_tmap_bf16(&tb, B, N, K, tc::BN);
+    if (e != cudaSuccess) return e;
+    static bool configured = false;
+    if (!configured) {
+        e = smem_attr(gemm_store_kernel, tc::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    gemm_store_kernel<<<dim3(M / tc::BM, N / tc::BN), tc::THREADS, tc::SMEM_BYTES, s>>>(ta, tb, D, M,
+                                                                                      K, err);
+    return cudaGetLastError();
+}
+
+cudaError_t dense_setup(DenseArgs &d) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = smem_attr(force1_kernel, tc::SMEM_BYTES);
+        if (e == cudaSuccess) e = smem_attr(force2_kernel, tc::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaError_t e = make_tmap_bf16(&d.tm_J, d.J16, d.N, d.N, tc::BM);
+    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_psi, d.psi16, d.b_pad, d.N, tc::BN);
+    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_u, d.u16, d.b_pad, d.N, tc::BN);
+    return e;
+}
+
+static int grid_elems(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
+                             int measure, cudaStream_t s, int64_t *launches) {
+    const int64_t nel = (int64_t)d.b_pad * d.N;
+    const dim3 gg(d.N / tc::BM, d.b_pad / tc::BN);
+    int64_t n = 0;
+    k_copy_state<<<grid_elems(nel), 256, 0, s>>>(d.psi_cur, d.psi, d.psi16, nel); ++n;
+    k_dense_momenta<<<grid_elems(nel / 4), 256, 0, s>>>(d.p, d.N, d.n_chains, d.b_pad, seed, traj); ++n;
+    for (int j = 0; j < sched.n_pass; ++j) {
+        force1_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_psi, d); ++n;
+        const bool drift = j + 1 < sched.n_pass;
+        force2_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(
+            d.tm_J, d.tm_u, d, (float)sched.kick[j], (float)sched.drift[j], drift ? 1 : 0); ++n;
+    }
+    k_df_gemm<<<dim3(d.N / DG_T, d.b_pad / DG_T), 256, 0, s>>>(d.Jhi, d.Jlo, d.psi, d.Ghi, d.Glo, d.N); ++n;
+    k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 0, traj, seed, measure); ++n;
+    *launches += n;
+    return cudaGetLastError();
+}
+
+cudaError_t dense_eval(DenseArgs &d, cudaStream_t s, int64_t *launches) {
+    k_df_gemm<<<dim3(d.N / DG_T, d.b_pad / DG_T), 256, 0, s>>>(d.Jhi, d.Jlo, d.psi_cur, d.Ghi, d.Glo,
+                                                              d.N);
+    k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 1, 0, 0, 0);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream_t s,
+                          int64_t *launches) {
+    const int64_t nel = (int64_t)d.b_pad * d.N;
+    k_dense_momenta<<<grid_elems(nel / 4), 256, 0, s>>>(d.p, d.N, d.n_chains, d.b_pad, seed, traj);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+// One force evaluation of the dense path alone (two GEMMs with epilogues), for
+// timing the tensor-core kernels.
+cudaError_t dense_force_once(DenseArgs &d, cudaStream_t s) {
+    const dim3 gg(d.N / tc::BM, d.b_pad / tc::BN);
+    force1_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_psi, d);
+    force2_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_u, d, 0.0f, 0.0f, 0);
+    return cudaGetLastError();
+}
+
+}  // namespace ihmc

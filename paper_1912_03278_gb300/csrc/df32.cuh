@@ -73,6 +73,23 @@ __device__ __forceinline__ f2 df_from_double(double x) {
 
 __device__ __forceinline__ double df_to_double(f2 a) { return (double)a.hi + (double)a.lo; }
 
+// Accumulators: a double-float high part plus an FP32 sum of the addends' low
+// words (their magnitude is ~2^-24 of the terms).
+__device__ __forceinline__ void acc_add(f2 &hi, float &lo, f2 v) {
+    hi = df_add_f(hi, v.hi);
+    lo = __fadd_rn(lo, v.lo);
+}
+__device__ __forceinline__ double acc_val(f2 hi, float lo) { return df_to_double(hi) + (double)lo; }
+
+// Kahan (1965) compensated summation in FP32.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+__device__ __forceinline__ double kahan_val(float s, float c) { return (double)s - (double)c; }
+
 // Table of g(y) = log(1 + exp(-y)) on y_k = k/32, k = 0 .. LOG1PEXP_K: one
 // float4 per node {g(y_k).hi, g(y_k).lo, s.hi, s.lo} with s = 1/(1 + e^{y_k}).
 // With w = s(1-s) and v = 1-2s the derivatives are polynomials in s

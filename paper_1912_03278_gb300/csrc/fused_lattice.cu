@@ -43,19 +43,6 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// tanh x = 1 - 2/(1 + e^{2x}) on |x| with the sign restored: e^{2|x|} from
-// the hardware exp2, 1/(1+e) from the hardware reciprocal refined by one
-// Newton step.  Absolute error below 3e-7 for all x (see the self-test).
-__device__ __forceinline__ float tanh_f(float x) {
-    const float ax = fminf(fabsf(x), 20.0f);
-    float e, r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(ax * 2.8853900817779268f));  // 2 log2(e)
-    const float d = e + 1.0f;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-    r = fmaf(fmaf(-d, r, 1.0f), r, r);
-    return copysignf(fmaf(-2.0f, r, 1.0f), x);
-}
-
 template <int VEC>
 struct Vec {
     float v[VEC];
@@ -190,25 +177,6 @@ __device__ __forceinline__ Acc acc_zero() {
     a.sS = 0;
     return a;
 }
-
-__device__ __forceinline__ void acc_add(f2 &hi, float &lo, f2 v) {
-    hi = df_add_f(hi, v.hi);
-    lo = __fadd_rn(lo, v.lo);
-}
-
-// Kahan (1965) compensated summation.
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-__device__ __forceinline__ double acc_val(f2 hi, float lo) {
-    return df_to_double(hi) + (double)lo;
-}
-
-__device__ __forceinline__ double kahan_val(float s, float c) { return (double)s - (double)c; }
 
 struct PassCfg {
     int src, dst;

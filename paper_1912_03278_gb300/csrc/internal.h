@@ -1,5 +1,7 @@
 // internal.h -- structures shared by the host runtime and the kernels.
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -85,12 +87,46 @@ int fused_lattice_valid_launch(const Geometry &g, int threads, int depth);
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
 
 cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s);
+// BF16 tensor-core GEMM D[n*M + m] = sum_k A[m][k] B[n][k]; M, N multiples of
+// 128, K a multiple of 64; *err gets bit 0 if a bounded wait ran out.
+cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int N, int K, int *err,
+                              cudaStream_t s);
 cudaError_t launch_log1pexp_selftest(const double *y, double *out, int64_t n, const float4 *tab,
                                      cudaStream_t s);
 
 // Host construction of the log(1 + exp(-y)) table (one float4 per node).
 void build_log1pexp_table(float *out /* 4 * LOG1PEXP_NODES floats */);
 constexpr int LOG1PEXP_NODES = 36 * 32 + 1;
+
+// Dense couplings on the tensor cores (BF16 force, FP32 state, FP64-accurate
+// action).  Arrays are chain-major with b_pad >= n_chains rows (a multiple of
+// 128; padded chains stay zero) and N sites (a multiple of 128).
+struct DenseArgs {
+    const __nv_bfloat16 *J16;   // N x N BF16 couplings
+    const float *Jhi, *Jlo;     // N x N couplings as a double-float pair
+    float *psi_cur;             // current configurations
+    float *psi;                 // working (proposal) configurations
+    __nv_bfloat16 *psi16;       // BF16 copy of psi (GEMM operand)
+    float *p;                   // momenta
+    float *u32;                 // u = tanh(A psi + h') - psi
+    __nv_bfloat16 *u16;         // BF16 copy of u (GEMM operand)
+    float *Ghi, *Glo;           // J psi as a double-float pair (action)
+    const float2 *hdf;          // per-site h_i as hi/lo floats, or null
+    const float4 *lpe_tab;      // log(1 + exp(-y)) table (global)
+    const ChainParams *params;
+    ChainState *state;
+    int N, n_chains, b_pad;
+    int *err;
+    CUtensorMap tm_J, tm_psi, tm_u;
+};
+
+cudaError_t dense_setup(DenseArgs &d);
+cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
+                             int measure, cudaStream_t s, int64_t *launches);
+cudaError_t dense_eval(DenseArgs &d, cudaStream_t s, int64_t *launches);
+cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream_t s,
+                          int64_t *launches);
+cudaError_t dense_force_once(DenseArgs &d, cudaStream_t s);
 
 // Plain FP64 form: one chain per launch, unfused kernels.
 struct PlainArgs {

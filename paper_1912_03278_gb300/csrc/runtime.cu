@@ -41,6 +41,12 @@ struct ising_hmc {
     int *d_err = nullptr;
     // launch shape of the fused kernel
     int threads = 0, depth = 0;
+    // dense couplings on the tensor cores
+    bool dense_tc = false;
+    int b_pad = 0;
+    DenseArgs dense{};
+    void *dJ16 = nullptr, *dJhi = nullptr, *dJlo = nullptr, *dpsi16 = nullptr, *du32 = nullptr,
+         *du16 = nullptr, *dGhi = nullptr, *dGlo = nullptr;
     // counters
     int64_t traj = 0;
     int64_t launches = 0;
@@ -66,6 +72,10 @@ static ising_status fail(ising_hmc *h, ising_status st, const char *fmt, ...) {
             return fail((h), ISING_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
                         __FILE__, __LINE__);                                            \
     } while (0)
+
+static bool is_dense_tc(const ising_hmc *h) {
+    return h->kind == ISING_KIND_DENSE && h->prec == ISING_PREC_BF16;
+}
 
 static bool is_fp32_lattice(const ising_hmc *h) {
     return h->kind == ISING_KIND_LATTICE && h->prec == ISING_PREC_FP32;
@@ -190,7 +200,8 @@ static void free_all(ising_hmc *h) {
         b = nullptr;
     }
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
-                    h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err};
+                    h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err, h->dJ16,
+                    h->dJhi, h->dJlo, h->dpsi16, h->du32, h->du16, h->dGhi, h->dGlo};
     for (void *b : bufs)
         if (b) cudaFree(b);
     h->p = nullptr;
@@ -201,6 +212,14 @@ static void free_all(ising_hmc *h) {
 static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_h) {
     const int64_t C = n_chains;
     int64_t b = 0;
+    if (kind == ISING_KIND_DENSE && prec == ISING_PREC_BF16) {
+        const int64_t Bp = (C + 127) / 128 * 128;
+        b += Bp * N * (3 * 4 + 2 + 4 + 2 + 8);          // psi x2, p, psi16, u32, u16, G hi/lo
+        b += N * N * (2 + 4 + 4);                        // J in BF16 and as two FP32
+        b += C * (int64_t)(sizeof(ChainParams) + sizeof(ChainState) + 2 * sizeof(int));
+        if (has_h) b += N * (int64_t)(2 * sizeof(float) + sizeof(double));
+        return b + 4 * LOG1PEXP_NODES * 4;
+    }
     if (prec == ISING_PREC_PLAIN_FP64) {
         b += 6 * C * N * (int64_t)sizeof(double);
         b += C * 7 * (int64_t)plain_partial_blocks(N) * (int64_t)sizeof(double);
@@ -264,6 +283,10 @@ static FusedArgs fused_args(ising_hmc *h) {
 
 // Recompute S and the observables of the current configurations.
 static ising_status eval_current(ising_hmc *h) {
+    if (is_dense_tc(h)) {
+        CUDA_OR_FAIL(h, dense_eval(h->dense, h->stream, &h->launches));
+        return ISING_OK;
+    }
     if (is_fp32_lattice(h)) {
         FusedArgs a = fused_args(h);
         a.mode = MODE_EVAL;
@@ -362,9 +385,17 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         h->g.dim = 0;
         h->g.X = (int)h->N; h->g.Y = 1; h->g.Z = 1; h->g.P = (int)h->N; h->g.nplanes = 1;
         h->g.N = h->N;
-        if (h->prec != ISING_PREC_PLAIN_FP64)
+        if (h->prec == ISING_PREC_BF16) {
+            if (h->N % 128)
+                return bail(fail(h, ISING_EINVAL, "BF16 dense form needs n_sites a multiple of 128"));
+            if (h->flip_every)
+                return bail(fail(h, ISING_EINVAL, "sign flip not available in the BF16 dense form"));
+            h->dense_tc = true;
+            h->b_pad = (h->n_chains + 127) / 128 * 128;
+        } else if (h->prec != ISING_PREC_PLAIN_FP64) {
             return bail(fail(h, ISING_EINVAL, "precision %d not available for dense couplings in this build",
                              h->prec));
+        }
     } else {
         return bail(fail(h, ISING_EINVAL, "unknown kind %d", cfg->kind));
     }
@@ -430,7 +461,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         h->own_stream = true;
     }
     const size_t elem = state_elem(h);
-    const size_t sbytes = (size_t)h->n_chains * N * elem;
+    const size_t sbytes = (size_t)(h->dense_tc ? h->b_pad : h->n_chains) * N * elem;
     ising_status st;
     const int nbuf = is_fp32_lattice(h) ? 3 : 2;
     for (int i = 0; i < nbuf; ++i)
@@ -449,7 +480,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     if ((st = dalloc(h, &h->d_params, sizeof(ChainParams) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_state, sizeof(ChainState) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_err, sizeof(int))) != ISING_OK) return bail(st);
-    if (is_fp32_lattice(h)) {
+    if (is_fp32_lattice(h) || is_dense_tc(h)) {
         std::vector<float> tab(4 * LOG1PEXP_NODES);
         build_log1pexp_table(tab.data());
         if ((st = dalloc(h, &h->d_lpe, tab.size() * sizeof(float))) != ISING_OK) return bail(st);
@@ -470,7 +501,55 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             cudaMemcpy(h->d_h64, cfg->h, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "field upload failed"));
     }
-    if (h->kind == ISING_KIND_DENSE) {
+    if (is_dense_tc(h)) {
+        const size_t bn = (size_t)h->b_pad * N;
+        if ((st = dalloc(h, &h->dpsi16, bn * 2)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->du32, bn * 4)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->du16, bn * 2)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->dGhi, bn * 4)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->dGlo, bn * 4)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->dJ16, (size_t)N * N * 2)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->dJhi, (size_t)N * N * 4)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->dJlo, (size_t)N * N * 4)) != ISING_OK) return bail(st);
+        std::vector<uint16_t> j16((size_t)N * N);
+        std::vector<float> jhi((size_t)N * N), jlo((size_t)N * N);
+        for (size_t i = 0; i < (size_t)N * N; ++i) {
+            const float f = (float)cfg->J[i];
+            jhi[i] = f;
+            jlo[i] = (float)(cfg->J[i] - (double)f);
+            uint32_t b;
+            std::memcpy(&b, &f, 4);
+            j16[i] = (uint16_t)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);   // round to nearest even
+        }
+        if (cudaMemcpy(h->dJ16, j16.data(), j16.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->dJhi, jhi.data(), jhi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h->dJlo, jlo.data(), jlo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(h->dpsi16, 0, bn * 2) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
+            cudaMemset(h->du16, 0, bn * 2) != cudaSuccess || cudaMemset(h->psi[1], 0, bn * 4) != cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "dense upload failed"));
+        DenseArgs &d = h->dense;
+        d.J16 = (const __nv_bfloat16 *)h->dJ16;
+        d.Jhi = (const float *)h->dJhi;
+        d.Jlo = (const float *)h->dJlo;
+        d.psi_cur = (float *)h->psi[0];
+        d.psi = (float *)h->psi[1];
+        d.psi16 = (__nv_bfloat16 *)h->dpsi16;
+        d.p = (float *)h->p;
+        d.u32 = (float *)h->du32;
+        d.u16 = (__nv_bfloat16 *)h->du16;
+        d.Ghi = (float *)h->dGhi;
+        d.Glo = (float *)h->dGlo;
+        d.hdf = h->has_h ? (const float2 *)h->d_h32 : nullptr;
+        d.lpe_tab = (const float4 *)h->d_lpe;
+        d.params = h->d_params;
+        d.state = h->d_state;
+        d.N = (int)N;
+        d.n_chains = h->n_chains;
+        d.b_pad = h->b_pad;
+        d.err = h->d_err;
+        if (dense_setup(d) != cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "tensor map setup failed"));
+    } else if (h->kind == ISING_KIND_DENSE) {
         if ((st = dalloc(h, &h->d_J, (size_t)N * N * sizeof(double))) != ISING_OK) return bail(st);
         if (cudaMemcpy(h->d_J, cfg->J, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice) !=
             cudaSuccess)
@@ -501,6 +580,16 @@ ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
     if (n < 0) return fail(h, ISING_EINVAL, "n must be >= 0");
     if (n == 0) return ISING_OK;
     if (h->traj + n > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "trajectory counter overflow");
+    if (is_dense_tc(h)) {
+        for (int64_t t = 0; t < n; ++t) {
+            const uint32_t tr = (uint32_t)(h->traj + t);
+            CUDA_OR_FAIL(h, dense_trajectory(h->dense, h->sched, seed, tr,
+                                             (int64_t)tr >= (int64_t)h->n_therm, h->stream,
+                                             &h->launches));
+        }
+        h->traj += n;
+        return ISING_OK;
+    }
     if (is_fp32_lattice(h)) {
         // trajectories per launch: keep each launch to a bounded amount of work
         const double work = (double)h->N * h->n_chains * h->sched.n_pass;
@@ -675,7 +764,7 @@ ising_status ising_hmc_get_chains(ising_hmc_t *h, int which, int chain0, int cou
             const int b = which == ISING_STATE_PSI ? hs[c].start : hs[c].prop;
             src = (const char *)h->psi[b] + (size_t)c * N * sizeof(float);
         } else {
-            src = (const char *)h->psi[which == ISING_STATE_PSI ? 0 : 1] + (size_t)c * N * sizeof(double);
+            src = (const char *)h->psi[which == ISING_STATE_PSI ? 0 : 1] + (size_t)c * N * state_elem(h);
         }
         if (state_elem(h) == sizeof(double)) {
             CUDA_OR_FAIL(h, cudaMemcpy(out + (size_t)k * N, src, N * sizeof(double), cudaMemcpyDeviceToHost));
@@ -738,7 +827,9 @@ ising_status ising_hmc_momenta(ising_hmc_t *h, uint64_t seed, int64_t traj, int 
     if (traj < 0 || traj > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "bad trajectory index");
     if (chain0 < 0 || count < 0 || chain0 + count > h->n_chains)
         return fail(h, ISING_EINVAL, "chain range out of bounds");
-    if (is_fp32_lattice(h)) {
+    if (is_dense_tc(h)) {
+        CUDA_OR_FAIL(h, dense_momenta(h->dense, seed, (uint32_t)traj, h->stream, &h->launches));
+    } else if (is_fp32_lattice(h)) {
         FusedArgs a = fused_args(h);
         a.mode = MODE_MOMENTA;
         a.seed = seed;
@@ -1108,6 +1199,35 @@ void ising_group_destroy(ising_group_t *g) {
     if (g->ev) cudaEventDestroy(g->ev);
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
+}
+
+ising_status ising_hmc_selftest_gemm(int M, int N, int K, const uint16_t *A, const uint16_t *B,
+                                     float *D) {
+    g_create_err[0] = 0;
+    if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64)
+        return fail(nullptr, ISING_EINVAL, "selftest_gemm: M, N multiples of 128, K of 64");
+    void *dA = nullptr, *dB = nullptr, *dD = nullptr;
+    int *derr = nullptr;
+    ising_status st = ISING_OK;
+    cudaError_t e = cudaMalloc(&dA, (size_t)M * K * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, (size_t)N * K * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dD, (size_t)M * N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(dA, A, (size_t)M * K * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, B, (size_t)N * K * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_gemm_store(dA, dB, (float *)dD, M, N, K, derr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(D, dD, (size_t)M * N * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = fail(nullptr, ISING_ECUDA, "selftest_gemm: %s", cudaGetErrorString(e));
+    else if (herr) st = fail(nullptr, ISING_ETIMEOUT, "selftest_gemm: a pipeline wait ran out");
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dD);
+    cudaFree(derr);
+    return st;
 }
 
 void ising_hmc_destroy(ising_hmc_t *h) {

@@ -1,0 +1,111 @@
+"""Dense couplings on the tensor cores: the BF16 tcgen05 GEMM behind the force."""
+import numpy as np
+import pytest
+
+import paper_1912_03278_gb300 as pkg
+from paper_1912_03278_gb300 import binding
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+
+
+def to_bf16_bits(x):
+    """Round FP32 to BF16 (nearest even) and return the 16-bit patterns."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = (b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) >> np.uint32(16)
+    return r.astype(np.uint16)
+
+
+def from_bf16_bits(b):
+    return (b.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (512, 256, 4096),
+                                   (1024, 1024, 1024)])
+def test_tcgen05_bf16_gemm(M, N, K):
+    g = np.random.default_rng(M + N + K)
+    A = to_bf16_bits(g.standard_normal((M, K)))
+    B = to_bf16_bits(g.standard_normal((N, K)))
+    D = binding.ising_hmc_selftest_gemm(A, B)
+    ref = from_bf16_bits(B) @ from_bf16_bits(A).T   # (N, M)
+    err = np.abs(D - ref).max() / np.abs(ref).max()
+    assert err < 1e-5, err   # FP32 accumulation over K terms
+
+
+# ---------------------------------------------------------------- HMC with dense couplings
+import oracle
+import workloads
+
+BF16 = pkg.ISING_PREC_BF16
+
+
+def _dense_parity(N, n_chains, samples, beta=0.5, n_md=8, eps=0.06, traj=2, seed=5, h=True,
+                  psi_scale=0.4):
+    J = workloads.dense_couplings(N, seed=1)
+    hv = workloads.dense_fields(N, 0.1) if h else 0.0
+    lam = np.linalg.eigvalsh(J)[0]
+    C = beta * abs(lam) + 0.1
+    psi0 = workloads.start_psi(n_chains, N, scale=psi_scale, seed=23).astype(np.float32).astype(np.float64)
+    sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=eps, n_md=n_md,
+                       n_chains=n_chains, precision=BF16)
+    try:
+        sim.set_state(psi0, next_traj=traj)
+        sim.trajectories(1, seed)
+        rec = sim.records()
+        got = {c: (sim.chains(pkg.ISING_STATE_PSI_PROPOSAL, c, 1)[0],
+                   sim.chains(pkg.ISING_STATE_P_END, c, 1)[0],
+                   sim.momenta(seed, traj, c, 1)[0]) for c in samples}
+    finally:
+        sim.close()
+    model = oracle.Model(kind="dense", J=J, h=hv, beta=beta, C=C)
+    for c in samples:
+        prop, pend, p0 = got[c]
+        ch = oracle.Chain(model, form=oracle.FORM_FP32, seed=seed, chain=c, psi0=psi0[c])
+        ch.traj = traj
+        r = ch.trajectory(eps, n_md)
+        rel = np.abs(prop - r["psi_prop"]).max() / np.abs(r["psi_prop"]).max()
+        assert rel <= 2e-2, (c, rel)          # BF16 force
+        H0 = oracle.kinetic(p0) + oracle.action(model, psi0[c])
+        H1 = oracle.kinetic(pend) + oracle.action(model, prop)
+        assert abs(rec[c, 0] - (H1 - H0)) <= 1e-6, (c, rec[c, 0], H1 - H0)   # FP64-accurate dH
+        assert abs(rec[c, 4] - oracle.action(model, psi0[c])) <= 1e-6
+        assert abs(rec[c, 1] - r["logu"]) <= 1e-14
+
+
+def test_dense_bf16_parity_small_ragged_chains():
+    _dense_parity(256, 130, samples=(0, 77, 129))
+
+
+def test_dense_bf16_parity_config_size():
+    """N = 4096 SK couplings, 1024 chains (the dense workload), sampled chains."""
+    _dense_parity(4096, 1024, samples=(0, 1023), n_md=8, eps=0.05)
+
+
+def test_dense_bf16_statistics_small_against_brute_force():
+    """N = 128 SK model is too large to enumerate; the same J distribution at
+    N = 128 is checked against the plain FP64 form statistically instead."""
+    N, beta = 128, 0.5
+    J = workloads.dense_couplings(N, seed=3)
+    hv = workloads.dense_fields(N, 0.1, seed=4)
+    C = beta * abs(np.linalg.eigvalsh(J)[0]) + 0.1
+    res = {}
+    for prec, chains in ((BF16, 256), (pkg.ISING_PREC_PLAIN_FP64, 8)):
+        sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=0.1, n_md=6,
+                           n_chains=chains, precision=prec, n_therm=50)
+        try:
+            sim.trajectories(350 if prec == BF16 else 300, 7)
+            res[prec] = sim.observables()
+        finally:
+            sim.close()
+    a, b = res[BF16], res[pkg.ISING_PREC_PLAIN_FP64]
+    assert a["acceptance"] > 0.5
+    for key in ("E", "m"):
+        err = np.hypot(a[key + "_err"], b[key + "_err"])
+        assert abs(a[key] - b[key]) <= 4 * err + 1e-3, (key, a[key], b[key], err)
