@@ -40,25 +40,28 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 }
 
 // ------------------------------------------------------- force epilogues
-__device__ __forceinline__ float hprime_f(const DenseArgs &d, const ChainParams &pr, int m) {
-    return d.hdf ? pr.betaf * d.hdf[m].x : pr.hpf;
-}
-
-// u = tanh(beta G + C psi + h') - psi for the 32 chains n0.. of site m.
+// u = tanh(beta G + C psi + h') - psi for the 32 chains n0.. of site m.  All
+// loads of the 32 columns are issued before any use, so each thread keeps 32
+// independent reads in flight (the epilogue is memory-bound).
 struct Epi1 {
     const DenseArgs *d;
     __device__ void operator()(int m, int n0, const float (&v)[32]) const {
         const DenseArgs &D = *d;
-#pragma unroll 4
+        float ps[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            ps[j] = (n0 + j < D.n_chains) ? D.psi[(int64_t)(n0 + j) * D.N + m] : 0.0f;
+        const float hm = D.hdf ? D.hdf[m].x : 0.0f;
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
             const int n = n0 + j;
             const int64_t idx = (int64_t)n * D.N + m;
             float u = 0.0f;
             if (n < D.n_chains) {
                 const ChainParams &pr = D.params[n];
-                const float ps = D.psi[idx];
-                const float a = fmaf(pr.betaf, v[j], pr.Cf * ps);
-                u = tanh_f(a + hprime_f(D, pr, m)) - ps;
+                const float a = fmaf(pr.betaf, v[j], pr.Cf * ps[j]);
+                const float hp = D.hdf ? pr.betaf * hm : pr.hpf;
+                u = tanh_f(a + hp) - ps[j];
             }
             D.u32[idx] = u;
             D.u16[idx] = __float2bfloat16_rn(u);
@@ -73,19 +76,28 @@ struct Epi2 {
     bool do_drift;
     __device__ void operator()(int m, int n0, const float (&v)[32]) const {
         const DenseArgs &D = *d;
-#pragma unroll 4
+        float uu[32], pp[32], ps[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const bool live = n0 + j < D.n_chains;
+            const int64_t idx = (int64_t)(n0 + j) * D.N + m;
+            uu[j] = live ? D.u32[idx] : 0.0f;
+            pp[j] = live ? D.p[idx] : 0.0f;
+            ps[j] = (live && do_drift) ? D.psi[idx] : 0.0f;
+        }
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
             const int n = n0 + j;
             if (n >= D.n_chains) continue;
             const int64_t idx = (int64_t)n * D.N + m;
             const ChainParams &pr = D.params[n];
-            const float F = fmaf(pr.betaf, v[j], pr.Cf * D.u32[idx]);
-            const float p = fmaf(kick * pr.epsf, F, D.p[idx]);
+            const float F = fmaf(pr.betaf, v[j], pr.Cf * uu[j]);
+            const float p = fmaf(kick * pr.epsf, F, pp[j]);
             D.p[idx] = p;
             if (do_drift) {
-                const float ps = fmaf(drift * pr.epsf, p, D.psi[idx]);
-                D.psi[idx] = ps;
-                D.psi16[idx] = __float2bfloat16_rn(ps);
+                const float psn = fmaf(drift * pr.epsf, p, ps[j]);
+                D.psi[idx] = psn;
+                D.psi16[idx] = __float2bfloat16_rn(psn);
             }
         }
     }

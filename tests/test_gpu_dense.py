@@ -59,9 +59,10 @@ def _dense_parity(N, n_chains, samples, beta=0.5, n_md=8, eps=0.06, traj=2, seed
         sim.set_state(psi0, next_traj=traj)
         sim.trajectories(1, seed)
         rec = sim.records()
-        got = {c: (sim.chains(pkg.ISING_STATE_PSI_PROPOSAL, c, 1)[0],
-                   sim.chains(pkg.ISING_STATE_P_END, c, 1)[0],
-                   sim.momenta(seed, traj, c, 1)[0]) for c in samples}
+        ends = {c: (sim.chains(pkg.ISING_STATE_PSI_PROPOSAL, c, 1)[0],
+                    sim.chains(pkg.ISING_STATE_P_END, c, 1)[0]) for c in samples}
+        # the momenta call overwrites the stored end momenta: fetch those first
+        got = {c: ends[c] + (sim.momenta(seed, traj, c, 1)[0],) for c in samples}
     finally:
         sim.close()
     model = oracle.Model(kind="dense", J=J, h=hv, beta=beta, C=C)
