@@ -23,37 +23,39 @@ namespace ihmc {
 namespace {
 
 // ---------------------------------------------------------------- GEMM tests
+constexpr int W = tc::EPI_W;
+
 struct StoreEpi {
     float *out;
     int M;
-    __device__ void operator()(int m, int n0, const float (&v)[32]) const {
+    __device__ void operator()(int m, int n0, const float (&v)[W]) const {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) out[(int64_t)(n0 + j) * M + m] = v[j];
+        for (int j = 0; j < W; ++j) out[(int64_t)(n0 + j) * M + m] = v[j];
     }
 };
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
     gemm_store_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
-                      float *out, int M, int K, int *err) {
+                      float *out, int M, int N, int K, int *err) {
     StoreEpi epi{out, M};
-    tc::gemm_tile(&ta, &tb, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K / tc::BK, epi, err);
+    tc::gemm_persistent(&ta, &tb, M / tc::BM, N / tc::BN, K / tc::BK, epi, err);
 }
 
 // ------------------------------------------------------- force epilogues
-// u = tanh(beta G + C psi + h') - psi for the 32 chains n0.. of site m.  All
-// loads of the 32 columns are issued before any use, so each thread keeps 32
+// u = tanh(beta G + C psi + h') - psi for the W chains n0.. of site m.  All
+// loads of the W columns are issued before any use, so each thread keeps W
 // independent reads in flight (the epilogue is memory-bound).
 struct Epi1 {
     const DenseArgs *d;
-    __device__ void operator()(int m, int n0, const float (&v)[32]) const {
+    __device__ void operator()(int m, int n0, const float (&v)[W]) const {
         const DenseArgs &D = *d;
-        float ps[32];
+        float ps[W];
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
+        for (int j = 0; j < W; ++j)
             ps[j] = (n0 + j < D.n_chains) ? D.psi[(int64_t)(n0 + j) * D.N + m] : 0.0f;
         const float hm = D.hdf ? D.hdf[m].x : 0.0f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < W; ++j) {
             const int n = n0 + j;
             const int64_t idx = (int64_t)n * D.N + m;
             float u = 0.0f;
@@ -74,11 +76,11 @@ struct Epi2 {
     const DenseArgs *d;
     float kick, drift;   // schedule coefficients (times each chain's eps)
     bool do_drift;
-    __device__ void operator()(int m, int n0, const float (&v)[32]) const {
+    __device__ void operator()(int m, int n0, const float (&v)[W]) const {
         const DenseArgs &D = *d;
-        float uu[32], pp[32], ps[32];
+        float uu[W], pp[W], ps[W];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < W; ++j) {
             const bool live = n0 + j < D.n_chains;
             const int64_t idx = (int64_t)(n0 + j) * D.N + m;
             uu[j] = live ? D.u32[idx] : 0.0f;
@@ -86,7 +88,7 @@ struct Epi2 {
             ps[j] = (live && do_drift) ? D.psi[idx] : 0.0f;
         }
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < W; ++j) {
             const int n = n0 + j;
             if (n >= D.n_chains) continue;
             const int64_t idx = (int64_t)n * D.N + m;
@@ -107,14 +109,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     force1_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tpsi,
                   const __grid_constant__ DenseArgs d) {
     Epi1 epi{&d};
-    tc::gemm_tile(&tj, &tpsi, blockIdx.x * tc::BM, blockIdx.y * tc::BN, d.N / tc::BK, epi, d.err);
+    tc::gemm_persistent(&tj, &tpsi, d.N / tc::BM, d.b_pad / tc::BN, d.N / tc::BK, epi, d.err);
 }
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force2_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tu,
                   const __grid_constant__ DenseArgs d, float kick, float drift, int do_drift) {
     Epi2 epi{&d, kick, drift, do_drift != 0};
-    tc::gemm_tile(&tj, &tu, blockIdx.x * tc::BM, blockIdx.y * tc::BN, d.N / tc::BK, epi, d.err);
+    tc::gemm_persistent(&tj, &tu, d.N / tc::BM, d.b_pad / tc::BN, d.N / tc::BK, epi, d.err);
 }
 
 // ------------------------------------------------------------- state helpers
@@ -329,6 +331,18 @@ cudaError_t smem_attr(K kern, int bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// One CTA per SM (at most one per tile).
+int persistent_grid(int tiles) {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm < 1) nsm = 1;
+    }
+    return tiles < nsm ? tiles : nsm;
+}
+
 }  // namespace
 
 // Tensor map of a row-major BF16 matrix (rows x cols, cols contiguous) read in
@@ -372,8 +386,8 @@ cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    gemm_store_kernel<<<dim3(M / tc::BM, N / tc::BN), tc::THREADS, tc::SMEM_BYTES, s>>>(ta, tb, D, M,
-                                                                                      K, err);
+    gemm_store_kernel<<<persistent_grid((M / tc::BM) * (N / tc::BN)), tc::THREADS, tc::SMEM_BYTES,
+                        s>>>(ta, tb, D, M, N, K, err);
     return cudaGetLastError();
 }
 
@@ -399,7 +413,7 @@ static int grid_elems(int64_t n) {
 cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
                              int measure, cudaStream_t s, int64_t *launches) {
     const int64_t nel = (int64_t)d.b_pad * d.N;
-    const dim3 gg(d.N / tc::BM, d.b_pad / tc::BN);
+    const int gg = persistent_grid((d.N / tc::BM) * (d.b_pad / tc::BN));
     int64_t n = 0;
     k_copy_state<<<grid_elems(nel), 256, 0, s>>>(d.psi_cur, d.psi, d.psi16, nel); ++n;
     k_dense_momenta<<<grid_elems(nel / 4), 256, 0, s>>>(d.p, d.N, d.n_chains, d.b_pad, seed, traj); ++n;
@@ -434,7 +448,7 @@ cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream
 // One force evaluation of the dense path alone (two GEMMs with epilogues), for
 // timing the tensor-core kernels.
 cudaError_t dense_force_once(DenseArgs &d, cudaStream_t s) {
-    const dim3 gg(d.N / tc::BM, d.b_pad / tc::BN);
+    const int gg = persistent_grid((d.N / tc::BM) * (d.b_pad / tc::BN));
     force1_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_psi, d);
     force2_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_u, d, 0.0f, 0.0f, 0);
     return cudaGetLastError();

@@ -21,7 +21,8 @@ constexpr int STAGES = 6;
 constexpr int A_BYTES = BM * BK * 2;   // 16 KB
 constexpr int B_BYTES = BN * BK * 2;   // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = BN;          // FP32 accumulator: 128 lanes x 128 columns
+constexpr int TMEM_COLS = 2 * BN;      // two FP32 accumulators of 128 lanes x 128 columns
+constexpr int EPI_W = 16;              // columns per epilogue chunk
 constexpr int THREADS = 192;           // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 // bounded waits: try_wait polls before the kernel gives up and flags an error
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
@@ -127,6 +128,26 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
@@ -152,28 +173,37 @@ struct Smem {
     uint8_t stage[STAGES][STAGE_BYTES];
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
-    uint64_t acc_full;
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
     uint32_t tmem_base;
 };
 constexpr int SMEM_BYTES = (int)sizeof(Smem) + 1024;
 
-// One BM x BN tile of D = A B^T for K = nk * BK, then epi(row, col0, v[32],
-// chunk) on each 32-column chunk of each row (called by the 128 epilogue
-// threads, one TMEM lane = one row each).  Returns false (after flagging
-// *err) if a wait ran out.
+// Persistent GEMM D = A B^T over an m_tiles x n_tiles grid of BM x BN tiles
+// (K = nk * BK): CTA b takes tiles b, b + gridDim.x, ...  Warp 0 streams A and
+// B tiles by TMA through the stage ring, warp 1 issues the MMAs into one of
+// two TMEM accumulators, warps 2..5 run epi(row, col0, v[EPI_W]) on each
+// 16-column chunk of each row of the other accumulator, so the epilogue of one
+// tile overlaps the MMAs of the next.  Every wait is bounded; on a timeout
+// the CTA flags *err and stops issuing work.
 template <class Epi>
-__device__ __forceinline__ void gemm_tile(const CUtensorMap *ta, const CUtensorMap *tb, int m0,
-                                          int n0, int nk, Epi &epi, int *err) {
+__device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUtensorMap *tb,
+                                                int m_tiles, int n_tiles, int nk, Epi &epi,
+                                                int *err) {
     extern __shared__ uint8_t smem_raw[];
     Smem &s = *reinterpret_cast<Smem *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = m_tiles * n_tiles;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&s.full[i], 1);
             mbar_init(&s.empty[i], 1);
         }
-        mbar_init(&s.acc_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&s.acc_full[b], 1);
+            mbar_init(&s.acc_empty[b], 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -186,49 +216,67 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *ta, const CUtensorM
 
     if (warp == 0) {
         if (lane == 0) {
-            // producer: TMA loads of A and B tiles into the stage ring
-            for (int kb = 0; kb < nk && ok; ++kb) {
-                const int st = kb % STAGES;
-                if (kb >= STAGES) ok = mbar_wait(&s.empty[st], ((kb / STAGES) & 1) ^ 1);
-                if (!ok) break;
-                mbar_expect_tx(&s.full[st], STAGE_BYTES);
-                tma_load_2d(s.stage[st], ta, kb * BK, m0, &s.full[st]);
-                tma_load_2d(s.stage[st] + A_BYTES, tb, kb * BK, n0, &s.full[st]);
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int m0 = (t % m_tiles) * BM, n0 = (t / m_tiles) * BN;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const uint32_t st = it % STAGES;
+                    if (it >= STAGES) ok = mbar_wait(&s.empty[st], ((it / STAGES) & 1) ^ 1);
+                    if (!ok) break;
+                    mbar_expect_tx(&s.full[st], STAGE_BYTES);
+                    tma_load_2d(s.stage[st], ta, kb * BK, m0, &s.full[st]);
+                    tma_load_2d(s.stage[st] + A_BYTES, tb, kb * BK, n0, &s.full[st]);
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer: four K = 16 steps per stage, accumulator in TMEM
             constexpr uint32_t idesc = idesc_bf16(BM, BN);
-            for (int kb = 0; kb < nk && ok; ++kb) {
-                const int st = kb % STAGES;
-                ok = mbar_wait(&s.full[st], (kb / STAGES) & 1);
+            uint32_t it = 0, lt = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
+                const uint32_t buf = lt & 1;
+                if (lt >= 2) ok = mbar_wait(&s.acc_empty[buf], ((lt >> 1) & 1) ^ 1);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t a_addr = smem_u32(s.stage[st]);
-                const uint32_t b_addr = a_addr + A_BYTES;
+                const uint32_t acc = tmem + buf * BN;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const uint32_t st = it % STAGES;
+                    ok = mbar_wait(&s.full[st], (it / STAGES) & 1);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(s.stage[st]);
+                    const uint32_t b_addr = a_addr + A_BYTES;
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k) {
-                    tc_mma(tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32),
-                           idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < BK / 16; ++k)
+                        tc_mma(acc, smem_desc_sw128(a_addr + k * 32),
+                               smem_desc_sw128(b_addr + k * 32), idesc,
+                               (kb > 0 || k > 0) ? 1u : 0u);
+                    tc_commit(&s.empty[st]);
                 }
-                tc_commit(&s.empty[st]);
+                if (!ok) break;
+                tc_commit(&s.acc_full[buf]);
             }
-            tc_commit(&s.acc_full);
         }
     } else {
         // epilogue warps 2..5: warp w reads TMEM lanes 32*(w%4) .. +31
         const int q = warp & 3;
-        ok = mbar_wait(&s.acc_full, 0);
-        tc_fence_after();
-        if (ok) {
+        uint32_t lt = 0;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
+            const uint32_t buf = lt & 1;
+            ok = mbar_wait(&s.acc_full[buf], (lt >> 1) & 1);
+            if (!ok) break;
+            tc_fence_after();
+            const int m0 = (t % m_tiles) * BM, n0 = (t / m_tiles) * BN;
             const int row = q * 32 + lane;
+            const uint32_t base = tmem + buf * BN + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
-                epi(m0 + row, n0 + c * 32, v);
+            for (int c = 0; c < BN / EPI_W; ++c) {
+                float v[EPI_W];
+                tc_ld16(base + (uint32_t)(c * EPI_W), v);
+                epi(m0 + row, n0 + c * EPI_W, v);
             }
+            tc_fence_before();
+            mbar_arrive(&s.acc_empty[buf]);
         }
     }
     if (!ok) atomicOr(err, 1);
