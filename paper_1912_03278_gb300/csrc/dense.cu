@@ -28,11 +28,12 @@ constexpr int W = tc::EPI_W;
 struct StoreEpi {
     float *out;
     int M;
-    __device__ void operator()(int m, int n0, const float (&v)[W]) const {
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
 #pragma unroll
         for (int j = 0; j < W; ++j) out[(int64_t)(n0 + j) * M + m] = v[j];
     }
 };
+
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
     gemm_store_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
@@ -42,64 +43,84 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 }
 
 // ------------------------------------------------------- force epilogues
-// u = tanh(beta G + C psi + h') - psi for the W chains n0.. of site m.  All
-// loads of the W columns are issued before any use, so each thread keeps W
-// independent reads in flight (the epilogue is memory-bound).
+// Each epilogue call handles W chains n0.. of one site m per thread; a warp
+// covers 32 consecutive sites, so every load and store below is one 128-byte
+// (64-byte for BF16) coalesced access per warp.  The kernel's pointers live in
+// registers; lane j < W reads chain n0+j's (beta, C, eps, h') as one float4
+// and the other lanes take it by shuffle.  All loads are issued before the
+// first store, so each thread keeps its W (or 3W) reads in flight at once.
+__device__ __forceinline__ float4 chain_coef(const ChainParams *params, int n0, int n_chains) {
+    const int n = n0 + (int)(threadIdx.x & (W - 1));
+    return n < n_chains ? *reinterpret_cast<const float4 *>(&params[n].betaf)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// u = tanh(beta G + C psi + h') - psi  ->  U (FP32 and BF16).
 struct Epi1 {
-    const DenseArgs *d;
-    __device__ void operator()(int m, int n0, const float (&v)[W]) const {
-        const DenseArgs &D = *d;
+    const float *psi;
+    float *u32;
+    __nv_bfloat16 *u16;
+    const float2 *hdf;
+    const ChainParams *params;
+    int N, n_chains;
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
+        const float4 cf = chain_coef(params, n0, n_chains);
+        const int64_t base = (int64_t)n0 * N + m;   // column j sits j*N further (N*W < 2^31)
+        const float *ps_in = psi + base;
         float ps[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j)
-            ps[j] = (n0 + j < D.n_chains) ? D.psi[(int64_t)(n0 + j) * D.N + m] : 0.0f;
-        const float hm = D.hdf ? D.hdf[m].x : 0.0f;
+        for (int j = 0; j < W; ++j) ps[j] = (n0 + j < n_chains) ? ps_in[j * N] : 0.0f;
+        const float hm = hdf ? hdf[m].x : 0.0f;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const int n = n0 + j;
-            const int64_t idx = (int64_t)n * D.N + m;
-            float u = 0.0f;
-            if (n < D.n_chains) {
-                const ChainParams &pr = D.params[n];
-                const float a = fmaf(pr.betaf, v[j], pr.Cf * ps[j]);
-                const float hp = D.hdf ? pr.betaf * hm : pr.hpf;
-                u = tanh_f(a + hp) - ps[j];
+            const float bj = __shfl_sync(0xffffffffu, cf.x, j);
+            const float cj = __shfl_sync(0xffffffffu, cf.y, j);
+            const float hj = __shfl_sync(0xffffffffu, cf.w, j);
+            const float a = fmaf(bj, v[j], cj * ps[j]);
+            const float u = tanh_f(a + (hdf ? bj * hm : hj)) - ps[j];
+            if (n0 + j < n_chains) {
+                u32[base + j * N] = u;
+                u16[base + j * N] = __float2bfloat16_rn(u);
             }
-            D.u32[idx] = u;
-            D.u16[idx] = __float2bfloat16_rn(u);
         }
     }
 };
 
-// F = beta (J U) + C u; p += kick F; psi += drift p.
+// F = beta (J U) + C u;  p += kick eps F;  psi += drift eps p (FP32 and BF16).
 struct Epi2 {
-    const DenseArgs *d;
+    const float *u32;
+    float *p, *psi;
+    __nv_bfloat16 *psi16;
+    const ChainParams *params;
+    int N, n_chains;
     float kick, drift;   // schedule coefficients (times each chain's eps)
     bool do_drift;
-    __device__ void operator()(int m, int n0, const float (&v)[W]) const {
-        const DenseArgs &D = *d;
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
+        const float4 cf = chain_coef(params, n0, n_chains);
+        const int64_t base = (int64_t)n0 * N + m;   // column j sits j*N further (N*W < 2^31)
+        const float *u_in = u32 + base;
+        float *p_io = p + base, *ps_io = psi + base;
         float uu[W], pp[W], ps[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const bool live = n0 + j < D.n_chains;
-            const int64_t idx = (int64_t)(n0 + j) * D.N + m;
-            uu[j] = live ? D.u32[idx] : 0.0f;
-            pp[j] = live ? D.p[idx] : 0.0f;
-            ps[j] = (live && do_drift) ? D.psi[idx] : 0.0f;
+            const bool live = n0 + j < n_chains;
+            uu[j] = live ? u_in[j * N] : 0.0f;
+            pp[j] = live ? p_io[j * N] : 0.0f;
+            ps[j] = (live && do_drift) ? ps_io[j * N] : 0.0f;
         }
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const int n = n0 + j;
-            if (n >= D.n_chains) continue;
-            const int64_t idx = (int64_t)n * D.N + m;
-            const ChainParams &pr = D.params[n];
-            const float F = fmaf(pr.betaf, v[j], pr.Cf * uu[j]);
-            const float p = fmaf(kick * pr.epsf, F, pp[j]);
-            D.p[idx] = p;
+            const float bj = __shfl_sync(0xffffffffu, cf.x, j);
+            const float cj = __shfl_sync(0xffffffffu, cf.y, j);
+            const float ej = __shfl_sync(0xffffffffu, cf.z, j);
+            if (n0 + j >= n_chains) continue;
+            const float F = fmaf(bj, v[j], cj * uu[j]);
+            const float pn = fmaf(kick * ej, F, pp[j]);
+            p_io[j * N] = pn;
             if (do_drift) {
-                const float psn = fmaf(drift * pr.epsf, p, ps[j]);
-                D.psi[idx] = psn;
-                D.psi16[idx] = __float2bfloat16_rn(psn);
+                const float psn = fmaf(drift * ej, pn, ps[j]);
+                ps_io[j * N] = psn;
+                psi16[base + j * N] = __float2bfloat16_rn(psn);
             }
         }
     }
@@ -108,14 +129,14 @@ struct Epi2 {
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force1_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tpsi,
                   const __grid_constant__ DenseArgs d) {
-    Epi1 epi{&d};
+    Epi1 epi{d.psi, d.u32, d.u16, d.hdf, d.params, d.N, d.n_chains};
     tc::gemm_persistent(&tj, &tpsi, d.N / tc::BM, d.b_pad / tc::BN, d.N / tc::BK, epi, d.err);
 }
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force2_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tu,
                   const __grid_constant__ DenseArgs d, float kick, float drift, int do_drift) {
-    Epi2 epi{&d, kick, drift, do_drift != 0};
+    Epi2 epi{d.u32, d.p, d.psi, d.psi16, d.params, d.N, d.n_chains, kick, drift, do_drift != 0};
     tc::gemm_persistent(&tj, &tu, d.N / tc::BM, d.b_pad / tc::BN, d.N / tc::BK, epi, d.err);
 }
 

@@ -10,10 +10,10 @@
 namespace ihmc {
 
 // Per-chain parameters (device).  hp = beta*h0 is the uniform part of h'.
-struct ChainParams {
+struct __align__(16) ChainParams {
     double beta, bJ, C, eps, hp;
-    float betaf, bJf, Cf, epsf, hpf;
-    float pad[3];
+    float bJf, pad;
+    float betaf, Cf, epsf, hpf;   // one aligned float4 (read whole by the dense epilogues)
 };
 
 // Per-chain Markov-chain state (device).

@@ -23,7 +23,15 @@ constexpr int B_BYTES = BN * BK * 2;   // 16 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;      // two FP32 accumulators of 128 lanes x 128 columns
 constexpr int EPI_W = 16;              // columns per epilogue chunk
-constexpr int THREADS = 192;           // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+// The epilogue is memory-bound: EPI_GROUPS groups of four warps (one warp per
+// TMEM lane quadrant) split a tile's column chunks, so that enough loads are
+// in flight per SM to cover DRAM latency.
+#ifndef IHMC_EPI_GROUPS
+#define IHMC_EPI_GROUPS 3
+#endif
+constexpr int EPI_GROUPS = IHMC_EPI_GROUPS;
+constexpr int EPI_WARPS = 4 * EPI_GROUPS;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, then the epilogue
 // bounded waits: try_wait polls before the kernel gives up and flags an error
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
@@ -181,8 +189,8 @@ constexpr int SMEM_BYTES = (int)sizeof(Smem) + 1024;
 
 // Persistent GEMM D = A B^T over an m_tiles x n_tiles grid of BM x BN tiles
 // (K = nk * BK): CTA b takes tiles b, b + gridDim.x, ...  Warp 0 streams A and
-// B tiles by TMA through the stage ring, warp 1 issues the MMAs into one of
-// two TMEM accumulators, warps 2..5 run epi(row, col0, v[EPI_W]) on each
+// B tiles by TMA through the stage ring, warp 1 issues the MMAs into one of two TMEM
+// accumulators, the epilogue warps run epi(row, col0, v[EPI_W]) on each
 // 16-column chunk of each row of the other accumulator, so the epilogue of one
 // tile overlaps the MMAs of the next.  Every wait is bounded; on a timeout
 // the CTA flags *err and stops issuing work.
@@ -202,7 +210,7 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s.acc_full[b], 1);
-            mbar_init(&s.acc_empty[b], 128);
+            mbar_init(&s.acc_empty[b], EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -215,10 +223,10 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
     bool ok = true;
 
     if (warp == 0) {
-        if (lane == 0) {
-            uint32_t it = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const int m0 = (t % m_tiles) * BM, n0 = (t / m_tiles) * BN;
+        uint32_t it = 0;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            const int m0 = (t % m_tiles) * BM, n0 = (t / m_tiles) * BN;
+            if (lane == 0) {
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const uint32_t st = it % STAGES;
                     if (it >= STAGES) ok = mbar_wait(&s.empty[st], ((it / STAGES) & 1) ^ 1);
@@ -228,6 +236,7 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
                     tma_load_2d(s.stage[st] + A_BYTES, tb, kb * BK, n0, &s.full[st]);
                 }
             }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -258,8 +267,10 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
             }
         }
     } else {
-        // epilogue warps 2..5: warp w reads TMEM lanes 32*(w%4) .. +31
+        // epilogue warps: warp w reads TMEM lanes 32*(w%4) .. +31 and belongs
+        // to group (w-2)/4, which takes chunks g, g + EPI_GROUPS, ...
         const int q = warp & 3;
+        const int g = (warp - 2) >> 2;
         uint32_t lt = 0;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++lt) {
             const uint32_t buf = lt & 1;
@@ -270,13 +281,14 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
             const int row = q * 32 + lane;
             const uint32_t base = tmem + buf * BN + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-            for (int c = 0; c < BN / EPI_W; ++c) {
+            for (int c = g; c < BN / EPI_W; c += EPI_GROUPS) {
                 float v[EPI_W];
                 tc_ld16(base + (uint32_t)(c * EPI_W), v);
                 epi(m0 + row, n0 + c * EPI_W, v);
             }
             tc_fence_before();
-            mbar_arrive(&s.acc_empty[buf]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.acc_empty[buf]);
         }
     }
     if (!ok) atomicOr(err, 1);
