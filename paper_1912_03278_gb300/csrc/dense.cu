@@ -23,9 +23,8 @@ namespace ihmc {
 namespace {
 
 // ---------------------------------------------------------------- GEMM tests
-constexpr int W = tc::EPI_W;
-
 struct StoreEpi {
+    static constexpr int W = 16;
     float *out;
     int M;
     __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
@@ -35,11 +34,13 @@ struct StoreEpi {
 };
 
 
+template <bool PAIR>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     gemm_store_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                       float *out, int M, int N, int K, int *err) {
     StoreEpi epi{out, M};
-    tc::gemm_persistent(&ta, &tb, M / tc::BM, N / tc::BN, K / tc::BK, epi, err);
+    using Md = tc::Mode<PAIR>;
+    tc::gemm_persistent<PAIR>(&ta, &tb, M / Md::TILE_M, N / Md::TILE_N, K / tc::BK, epi, err);
 }
 
 // ------------------------------------------------------- force epilogues
@@ -49,14 +50,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // registers; lane j < W reads chain n0+j's (beta, C, eps, h') as one float4
 // and the other lanes take it by shuffle.  All loads are issued before the
 // first store, so each thread keeps its W (or 3W) reads in flight at once.
+template <int W>
 __device__ __forceinline__ float4 chain_coef(const ChainParams *params, int n0, int n_chains) {
     const int n = n0 + (int)(threadIdx.x & (W - 1));
     return n < n_chains ? *reinterpret_cast<const float4 *>(&params[n].betaf)
                         : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// u = tanh(beta G + C psi + h') - psi  ->  U (FP32 and BF16).
+// u = tanh(beta G + C psi + h') - psi  ->  U (FP32 and BF16).  One load per
+// element, so 32 columns per chunk keep enough reads in flight.
 struct Epi1 {
+    static constexpr int W = 32;
     const float *psi;
     float *u32;
     __nv_bfloat16 *u16;
@@ -64,7 +68,7 @@ struct Epi1 {
     const ChainParams *params;
     int N, n_chains;
     __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
-        const float4 cf = chain_coef(params, n0, n_chains);
+        const float4 cf = chain_coef<W>(params, n0, n_chains);
         const int64_t base = (int64_t)n0 * N + m;   // column j sits j*N further (N*W < 2^31)
         const float *ps_in = psi + base;
         float ps[W];
@@ -88,6 +92,7 @@ struct Epi1 {
 
 // F = beta (J U) + C u;  p += kick eps F;  psi += drift eps p (FP32 and BF16).
 struct Epi2 {
+    static constexpr int W = 16;
     const float *u32;
     float *p, *psi;
     __nv_bfloat16 *psi16;
@@ -96,7 +101,7 @@ struct Epi2 {
     float kick, drift;   // schedule coefficients (times each chain's eps)
     bool do_drift;
     __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
-        const float4 cf = chain_coef(params, n0, n_chains);
+        const float4 cf = chain_coef<W>(params, n0, n_chains);
         const int64_t base = (int64_t)n0 * N + m;   // column j sits j*N further (N*W < 2^31)
         const float *u_in = u32 + base;
         float *p_io = p + base, *ps_io = psi + base;
@@ -126,18 +131,24 @@ struct Epi2 {
     }
 };
 
+template <bool PAIR>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force1_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tpsi,
                   const __grid_constant__ DenseArgs d) {
     Epi1 epi{d.psi, d.u32, d.u16, d.hdf, d.params, d.N, d.n_chains};
-    tc::gemm_persistent(&tj, &tpsi, d.N / tc::BM, d.b_pad / tc::BN, d.N / tc::BK, epi, d.err);
+    using Md = tc::Mode<PAIR>;
+    tc::gemm_persistent<PAIR>(&tj, &tpsi, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK,
+                              epi, d.err);
 }
 
+template <bool PAIR>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force2_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tu,
                   const __grid_constant__ DenseArgs d, float kick, float drift, int do_drift) {
     Epi2 epi{d.u32, d.p, d.psi, d.psi16, d.params, d.N, d.n_chains, kick, drift, do_drift != 0};
-    tc::gemm_persistent(&tj, &tu, d.N / tc::BM, d.b_pad / tc::BN, d.N / tc::BK, epi, d.err);
+    using Md = tc::Mode<PAIR>;
+    tc::gemm_persistent<PAIR>(&tj, &tu, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK, epi,
+                              d.err);
 }
 
 // ------------------------------------------------------------- state helpers
@@ -347,21 +358,58 @@ __global__ void __launch_bounds__(256) k_dense_finalize(DenseArgs d, int mode, u
     }
 }
 
-template <class K>
-cudaError_t smem_attr(K kern, int bytes) {
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// CTA-pair tiles (256 x 256) where both GEMM output dimensions allow them,
+// else single-CTA 128 x 128 tiles.
+#ifndef IHMC_NO_PAIR
+static bool use_pair(int M, int N) { return M % 256 == 0 && N % 256 == 0; }
+#else
+static bool use_pair(int, int) { return false; }
+#endif
+
+// Cluster of cn CTAs; with pdl, programmatic dependent launch (the kernel
+// waits on the previous grid itself, after its set-up).
+static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute *at, int cn, int grid, cudaStream_t s,
+                                         bool pdl = false) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = tc::SMEM_BYTES;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cn;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cfg;
 }
 
-// One CTA per SM (at most one per tile).
-int persistent_grid(int tiles) {
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm < 1) nsm = 1;
-    }
-    return tiles < nsm ? tiles : nsm;
+// How many clusters of cn CTAs of kern fit on the GPU at once (one CTA per SM).
+template <class K>
+cudaError_t max_clusters(K kern, int cn, int *out) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = cluster_config(at, cn, cn, 0);
+    e = cudaOccupancyMaxActiveClusters(out, kern, &cfg);
+    if (e == cudaSuccess && *out < 1) e = cudaErrorInvalidConfiguration;
+    return e;
+}
+
+#ifndef IHMC_PDL
+#define IHMC_PDL true
+#endif
+// Persistent launch in clusters of cn CTAs: as many clusters as fit at once
+// (nclu), at most one per tile.
+template <class... KArgs, class... Args>
+cudaError_t launch_gemm(void (*kern)(KArgs...), int cn, int nclu, int units, cudaStream_t s,
+                        Args... args) {
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = cluster_config(at, cn, (units < nclu ? units : nclu) * cn, s, IHMC_PDL);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 }  // namespace
@@ -395,35 +443,61 @@ cudaError_t make_tmap_bf16(CUtensorMap *map, const void *base, int64_t rows, int
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+template <bool PAIR>
+static cudaError_t gemm_store_mode(const CUtensorMap &ta, const CUtensorMap &tb, float *D, int M,
+                                   int N, int K, int *err, cudaStream_t s) {
+    using Md = tc::Mode<PAIR>;
+    const int cs = PAIR ? 2 : 1;
+    int nclu = 0;
+    cudaError_t e = max_clusters(gemm_store_kernel<PAIR>, cs, &nclu);
+    if (e != cudaSuccess) return e;
+    return launch_gemm(gemm_store_kernel<PAIR>, cs, nclu, (M / Md::TILE_M) * (N / Md::TILE_N), s,
+                       ta, tb, D, M, N, K, err);
+}
+
 cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int N, int K, int *err,
                               cudaStream_t s) {
     CUtensorMap ta, tb;
     cudaError_t e = make_tmap_bf16(&ta, A, M, K, tc::BM);
-    if (e == cudaSuccess) e = make_tmap_bf16(&tb, B, N, K, tc::BN);
+    if (e == cudaSuccess) e = make_tmap_bf16(&tb, B, N, K, tc::BR);
     if (e != cudaSuccess) return e;
-    static bool configured = false;
-    if (!configured) {
-        e = smem_attr(gemm_store_kernel, tc::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    gemm_store_kernel<<<persistent_grid((M / tc::BM) * (N / tc::BN)), tc::THREADS, tc::SMEM_BYTES,
-                        s>>>(ta, tb, D, M, N, K, err);
-    return cudaGetLastError();
+    return use_pair(M, N) ? gemm_store_mode<true>(ta, tb, D, M, N, K, err, s)
+                          : gemm_store_mode<false>(ta, tb, D, M, N, K, err, s);
+}
+
+template <bool PAIR>
+static cudaError_t force_clusters(int *nclu) {
+    const int cs = PAIR ? 2 : 1;
+    int a = 0, b = 0;
+    cudaError_t e = max_clusters(force1_kernel<PAIR>, cs, &a);
+    if (e == cudaSuccess) e = max_clusters(force2_kernel<PAIR>, cs, &b);
+    *nclu = a < b ? a : b;
+    return e;
 }
 
 cudaError_t dense_setup(DenseArgs &d) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = smem_attr(force1_kernel, tc::SMEM_BYTES);
-        if (e == cudaSuccess) e = smem_attr(force2_kernel, tc::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    cudaError_t e = make_tmap_bf16(&d.tm_J, d.J16, d.N, d.N, tc::BM);
-    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_psi, d.psi16, d.b_pad, d.N, tc::BN);
-    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_u, d.u16, d.b_pad, d.N, tc::BN);
+    d.pair = use_pair(d.N, d.b_pad) ? 1 : 0;
+    cudaError_t e = d.pair ? force_clusters<true>(&d.nclu) : force_clusters<false>(&d.nclu);
+    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_J, d.J16, d.N, d.N, tc::BM);
+    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_psi, d.psi16, d.b_pad, d.N, tc::BR);
+    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_u, d.u16, d.b_pad, d.N, tc::BR);
     return e;
+}
+
+// G = J Psi^T with the pass-1 epilogue (u), then G = J U^T with the pass-2
+// epilogue (kick, drift).
+static cudaError_t launch_force(const DenseArgs &d, int pass, float kick, float drift, int do_drift,
+                                cudaStream_t s) {
+    if (d.pair) {
+        const int units = (d.N / 256) * (d.b_pad / 256);
+        return pass == 0 ? launch_gemm(force1_kernel<true>, 2, d.nclu, units, s, d.tm_J, d.tm_psi, d)
+                         : launch_gemm(force2_kernel<true>, 2, d.nclu, units, s, d.tm_J, d.tm_u, d,
+                                       kick, drift, do_drift);
+    }
+    const int units = (d.N / 128) * (d.b_pad / 128);
+    return pass == 0 ? launch_gemm(force1_kernel<false>, 1, d.nclu, units, s, d.tm_J, d.tm_psi, d)
+                     : launch_gemm(force2_kernel<false>, 1, d.nclu, units, s, d.tm_J, d.tm_u, d, kick,
+                                   drift, do_drift);
 }
 
 static int grid_elems(int64_t n) {
@@ -434,15 +508,19 @@ static int grid_elems(int64_t n) {
 cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
                              int measure, cudaStream_t s, int64_t *launches) {
     const int64_t nel = (int64_t)d.b_pad * d.N;
-    const int gg = persistent_grid((d.N / tc::BM) * (d.b_pad / tc::BN));
     int64_t n = 0;
     k_copy_state<<<grid_elems(nel), 256, 0, s>>>(d.psi_cur, d.psi, d.psi16, nel); ++n;
     k_dense_momenta<<<grid_elems(nel / 4), 256, 0, s>>>(d.p, d.N, d.n_chains, d.b_pad, seed, traj); ++n;
     for (int j = 0; j < sched.n_pass; ++j) {
-        force1_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_psi, d); ++n;
+        cudaError_t e = launch_force(d, 0, 0.f, 0.f, 0, s); ++n;
         const bool drift = j + 1 < sched.n_pass;
-        force2_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(
-            d.tm_J, d.tm_u, d, (float)sched.kick[j], (float)sched.drift[j], drift ? 1 : 0); ++n;
+        if (e == cudaSuccess)
+            e = launch_force(d, 1, (float)sched.kick[j], (float)sched.drift[j], drift ? 1 : 0, s);
+        ++n;
+        if (e != cudaSuccess) {
+            *launches += n;
+            return e;
+        }
     }
     k_df_gemm<<<dim3(d.N / DG_T, d.b_pad / DG_T), 256, 0, s>>>(d.Jhi, d.Jlo, d.psi, d.Ghi, d.Glo, d.N); ++n;
     k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 0, traj, seed, measure); ++n;
@@ -469,10 +547,8 @@ cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream
 // One force evaluation of the dense path alone (two GEMMs with epilogues), for
 // timing the tensor-core kernels.
 cudaError_t dense_force_once(DenseArgs &d, cudaStream_t s) {
-    const int gg = persistent_grid((d.N / tc::BM) * (d.b_pad / tc::BN));
-    force1_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_psi, d);
-    force2_kernel<<<gg, tc::THREADS, tc::SMEM_BYTES, s>>>(d.tm_J, d.tm_u, d, 0.0f, 0.0f, 0);
-    return cudaGetLastError();
+    cudaError_t e = launch_force(d, 0, 0.f, 0.f, 0, s);
+    return e == cudaSuccess ? launch_force(d, 1, 0.f, 0.f, 0, s) : e;
 }
 
 }  // namespace ihmc

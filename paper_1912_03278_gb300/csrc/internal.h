@@ -116,6 +116,7 @@ struct DenseArgs {
     const ChainParams *params;
     ChainState *state;
     int N, n_chains, b_pad;
+    int pair, nclu;             // CTA-pair GEMM tiles (1) or single-CTA (0); clusters resident at once
     int *err;
     CUtensorMap tm_J, tm_psi, tm_u;
 };

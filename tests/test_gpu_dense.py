@@ -27,8 +27,10 @@ def from_bf16_bits(b):
     return (b.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
 
 
+# 128-multiples run single-CTA 128 x 128 tiles, 256-multiples CTA-pair 256 x 256
+# tiles; 4096 x 1280 has more pair tiles (80) than pairs fit on the GPU at once.
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (512, 256, 4096),
-                                   (1024, 1024, 1024)])
+                                   (1024, 1024, 1024), (4096, 1280, 256)])
 def test_tcgen05_bf16_gemm(M, N, K):
     g = np.random.default_rng(M + N + K)
     A = to_bf16_bits(g.standard_normal((M, K)))
