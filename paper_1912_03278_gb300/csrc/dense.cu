@@ -27,7 +27,9 @@ struct StoreEpi {
     static constexpr int W = 16;
     float *out;
     int M;
-    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
+    __device__ int a_off(int) const { return 0; }
+    __device__ int b_off(int) const { return 0; }
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W], int) const {
 #pragma unroll
         for (int j = 0; j < W; ++j) out[(int64_t)(n0 + j) * M + m] = v[j];
     }
@@ -40,7 +42,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                       float *out, int M, int N, int K, int *err) {
     StoreEpi epi{out, M};
     using Md = tc::Mode<PAIR>;
-    tc::gemm_persistent<PAIR>(&ta, &tb, M / Md::TILE_M, N / Md::TILE_N, K / tc::BK, epi, err);
+    tc::gemm_persistent<PAIR>(&ta, &tb, M / Md::TILE_M, N / Md::TILE_N, K / tc::BK, 1, epi, err);
 }
 
 // ------------------------------------------------------- force epilogues
@@ -67,7 +69,9 @@ struct Epi1 {
     const float2 *hdf;
     const ChainParams *params;
     int N, n_chains;
-    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
+    __device__ int a_off(int) const { return 0; }
+    __device__ int b_off(int) const { return 0; }
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W], int) const {
         const float4 cf = chain_coef<W>(params, n0, n_chains);
         const int64_t base = (int64_t)n0 * N + m;   // column j sits j*N further (N*W < 2^31)
         const float *ps_in = psi + base;
@@ -100,7 +104,9 @@ struct Epi2 {
     int N, n_chains;
     float kick, drift;   // schedule coefficients (times each chain's eps)
     bool do_drift;
-    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W]) const {
+    __device__ int a_off(int) const { return 0; }
+    __device__ int b_off(int) const { return 0; }
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W], int) const {
         const float4 cf = chain_coef<W>(params, n0, n_chains);
         const int64_t base = (int64_t)n0 * N + m;   // column j sits j*N further (N*W < 2^31)
         const float *u_in = u32 + base;
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                   const __grid_constant__ DenseArgs d) {
     Epi1 epi{d.psi, d.u32, d.u16, d.hdf, d.params, d.N, d.n_chains};
     using Md = tc::Mode<PAIR>;
-    tc::gemm_persistent<PAIR>(&tj, &tpsi, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK,
+    tc::gemm_persistent<PAIR>(&tj, &tpsi, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK, 1,
                               epi, d.err);
 }
 
@@ -147,8 +153,95 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                   const __grid_constant__ DenseArgs d, float kick, float drift, int do_drift) {
     Epi2 epi{d.u32, d.p, d.psi, d.psi16, d.params, d.N, d.n_chains, kick, drift, do_drift != 0};
     using Md = tc::Mode<PAIR>;
-    tc::gemm_persistent<PAIR>(&tj, &tu, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK, epi,
+    tc::gemm_persistent<PAIR>(&tj, &tu, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK, 1, epi,
                               d.err);
+}
+
+// ------------------------------------------ FP64-accurate G = J Psi^T (action)
+// Exact digit products on the tensor cores.  Each row i of J is scaled by
+// 2^e_i and each chain c of Psi by 2^f_c so that all entries lie in
+// [-1/2, 1/2], then written in base 128 with ACT_DIGITS = 6 signed digits in
+// [-64, 64] (exact in BF16):  J_ij = 2^e_i sum_s d_s 2^(-7(s+1)),
+// psi_cj = 2^f_c sum_t q_t 2^(-7(t+1)).  One digit-plane product sums N terms
+// of magnitude <= 2^12, so for N <= 4096 every partial sum is an integer
+// of magnitude <= 2^24 and the FP32 accumulator holds it exactly.  The
+// epilogue adds the ACT_PAIRS = 21 products with s + t <= 5,
+// 2^(-7(s+t)) I_st, in FP64:
+//   G_raw = sum_{s+t<=5} 2^(-7(s+t)) sum_j d_s,ij q_t,cj,
+//   (J psi)_ic = 2^(e_i + f_c - 14) G_raw.
+// The dropped products (s+t >= 6) and the digit truncation weigh below
+// 2^-40 of 2^(e_i+f_c), far under the accuracy the action needs (Sec. 3:
+// dH decides the Metropolis test).
+__constant__ int c_pair_s[ACT_PAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0,
+                                        1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ int c_pair_t[ACT_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4,
+                                        3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+
+struct EpiG {
+    static constexpr int W = 16;
+    double *G;
+    int N, n_chains, b_pad;
+    __device__ int a_off(int r) const { return c_pair_s[r] * N; }
+    __device__ int b_off(int r) const { return c_pair_t[r] * b_pad; }
+    __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W], int r) const {
+        const double sc = ldexp(1.0, -ACT_BITS * (c_pair_s[r] + c_pair_t[r]));
+        double *g = G + (int64_t)n0 * N + m;
+        if (r == 0) {
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (n0 + j < n_chains) g[j * N] = (double)v[j] * sc;
+        } else {
+            double old[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) old[j] = (n0 + j < n_chains) ? g[j * N] : 0.0;
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (n0 + j < n_chains) g[j * N] = fma((double)v[j], sc, old[j]);
+        }
+    }
+};
+
+template <bool PAIR>
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    action_kernel(const __grid_constant__ CUtensorMap tjd, const __grid_constant__ CUtensorMap tpd,
+                  const __grid_constant__ DenseArgs d) {
+    EpiG epi{d.G64, d.N, d.n_chains, d.b_pad};
+    using Md = tc::Mode<PAIR>;
+    tc::gemm_persistent<PAIR>(&tjd, &tpd, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK,
+                              ACT_PAIRS, epi, d.err);
+}
+
+// Digits of Psi (chain c = block): f_c from max |psi_c|, then ACT_DIGITS
+// base-128 digits of psi * 2^-f_c per site, each digit plane b_pad x N
+// (padding chains get zero digits).  All steps are exact in FP64.
+__global__ void __launch_bounds__(256) k_psi_digits(const float *__restrict__ psi,
+                                                    __nv_bfloat16 *__restrict__ dig,
+                                                    int *__restrict__ chain_exp, int N,
+                                                    int n_chains, int b_pad) {
+    __shared__ float red[8];
+    const int n = blockIdx.x;
+    const bool live = n < n_chains;
+    float mx = 0.0f;
+    if (live)
+        for (int m = threadIdx.x; m < N; m += blockDim.x)
+            mx = fmaxf(mx, fabsf(psi[(int64_t)n * N + m]));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    const int f = mx > 0.0f ? ilogbf(mx) + 2 : 0;   // max |psi| * 2^-f < 1/2
+    if (threadIdx.x == 0) chain_exp[n] = f;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        double x = live ? ldexp((double)psi[(int64_t)n * N + m], -f) : 0.0;
+#pragma unroll
+        for (int t = 0; t < ACT_DIGITS; ++t) {
+            x *= (double)(1 << ACT_BITS);
+            const double q = rint(x);
+            x -= q;
+            dig[((int64_t)t * b_pad + n) * N + m] = __float2bfloat16_rn((float)q);
+        }
+    }
 }
 
 // ------------------------------------------------------------- state helpers
@@ -274,7 +367,10 @@ __global__ void __launch_bounds__(256) k_dense_finalize(DenseArgs d, int mode, u
             const int m = 4 * q + k;
             const int64_t idx = (int64_t)n * d.N + m;
             const float ps = psi[m];
-            const f2 G{d.Ghi[idx], d.Glo[idx]};
+            const f2 G = d.action_tc
+                             ? df_from_double(ldexp(d.G64[idx], d.row_exp[m] + d.chain_exp[n] -
+                                                                    2 * ACT_BITS))
+                             : f2{d.Ghi[idx], d.Glo[idx]};
             const f2 a = df_add(df_mul(beta2, G), df_mul_f(C2, ps));
             f2 x = a;
             float hq = pr.hpf;
@@ -468,10 +564,11 @@ cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int
 template <bool PAIR>
 static cudaError_t force_clusters(int *nclu) {
     const int cs = PAIR ? 2 : 1;
-    int a = 0, b = 0;
+    int a = 0, b = 0, c = 0;
     cudaError_t e = max_clusters(force1_kernel<PAIR>, cs, &a);
     if (e == cudaSuccess) e = max_clusters(force2_kernel<PAIR>, cs, &b);
-    *nclu = a < b ? a : b;
+    if (e == cudaSuccess) e = max_clusters(action_kernel<PAIR>, cs, &c);
+    *nclu = a < b ? (a < c ? a : c) : (b < c ? b : c);
     return e;
 }
 
@@ -481,7 +578,33 @@ cudaError_t dense_setup(DenseArgs &d) {
     if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_J, d.J16, d.N, d.N, tc::BM);
     if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_psi, d.psi16, d.b_pad, d.N, tc::BR);
     if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_u, d.u16, d.b_pad, d.N, tc::BR);
+    if (e == cudaSuccess && d.action_tc) {
+        e = make_tmap_bf16(&d.tm_Jdig, d.Jdig, (int64_t)ACT_DIGITS * d.N, d.N, tc::BM);
+        if (e == cudaSuccess)
+            e = make_tmap_bf16(&d.tm_psidig, d.psidig, (int64_t)ACT_DIGITS * d.b_pad, d.N, tc::BR);
+    }
     return e;
+}
+
+// G = J psi to FP64 accuracy for the chains' psi (proposal or current).
+static cudaError_t launch_action_product(DenseArgs &d, const float *psi, cudaStream_t s,
+                                         int64_t *n) {
+    if (!d.action_tc) {
+        k_df_gemm<<<dim3(d.N / DG_T, d.b_pad / DG_T), 256, 0, s>>>(d.Jhi, d.Jlo, psi, d.Ghi, d.Glo,
+                                                                  d.N);
+        ++*n;
+        return cudaGetLastError();
+    }
+    k_psi_digits<<<d.b_pad, 256, 0, s>>>(psi, d.psidig, d.chain_exp, d.N, d.n_chains, d.b_pad);
+    ++*n;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++*n;
+    if (d.pair)
+        return launch_gemm(action_kernel<true>, 2, d.nclu, (d.N / 256) * (d.b_pad / 256), s,
+                           d.tm_Jdig, d.tm_psidig, d);
+    return launch_gemm(action_kernel<false>, 1, d.nclu, (d.N / 128) * (d.b_pad / 128), s, d.tm_Jdig,
+                       d.tm_psidig, d);
 }
 
 // G = J Psi^T with the pass-1 epilogue (u), then G = J U^T with the pass-2
@@ -522,18 +645,26 @@ cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed,
             return e;
         }
     }
-    k_df_gemm<<<dim3(d.N / DG_T, d.b_pad / DG_T), 256, 0, s>>>(d.Jhi, d.Jlo, d.psi, d.Ghi, d.Glo, d.N); ++n;
+    cudaError_t e = launch_action_product(d, d.psi, s, &n);
+    if (e != cudaSuccess) {
+        *launches += n;
+        return e;
+    }
     k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 0, traj, seed, measure); ++n;
     *launches += n;
     return cudaGetLastError();
 }
 
 cudaError_t dense_eval(DenseArgs &d, cudaStream_t s, int64_t *launches) {
-    k_df_gemm<<<dim3(d.N / DG_T, d.b_pad / DG_T), 256, 0, s>>>(d.Jhi, d.Jlo, d.psi_cur, d.Ghi, d.Glo,
-                                                              d.N);
-    k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 1, 0, 0, 0);
-    *launches += 2;
-    return cudaGetLastError();
+    int64_t n = 0;
+    cudaError_t e = launch_action_product(d, d.psi_cur, s, &n);
+    if (e == cudaSuccess) {
+        k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 1, 0, 0, 0);
+        ++n;
+        e = cudaGetLastError();
+    }
+    *launches += n;
+    return e;
 }
 
 cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream_t s,

@@ -47,6 +47,8 @@ struct ising_hmc {
     DenseArgs dense{};
     void *dJ16 = nullptr, *dJhi = nullptr, *dJlo = nullptr, *dpsi16 = nullptr, *du32 = nullptr,
          *du16 = nullptr, *dGhi = nullptr, *dGlo = nullptr;
+    void *dJdig = nullptr, *dpsidig = nullptr, *drow_exp = nullptr, *dchain_exp = nullptr,
+         *dG64 = nullptr;
     // counters
     int64_t traj = 0;
     int64_t launches = 0;
@@ -201,7 +203,8 @@ static void free_all(ising_hmc *h) {
     }
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
                     h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err, h->dJ16,
-                    h->dJhi, h->dJlo, h->dpsi16, h->du32, h->du16, h->dGhi, h->dGlo};
+                    h->dJhi, h->dJlo, h->dpsi16, h->du32, h->du16, h->dGhi, h->dGlo,
+                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dG64};
     for (void *b : bufs)
         if (b) cudaFree(b);
     h->p = nullptr;
@@ -214,8 +217,13 @@ static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_
     int64_t b = 0;
     if (kind == ISING_KIND_DENSE && prec == ISING_PREC_BF16) {
         const int64_t Bp = (C + 127) / 128 * 128;
-        b += Bp * N * (3 * 4 + 2 + 4 + 2 + 8);          // psi x2, p, psi16, u32, u16, G hi/lo
-        b += N * N * (2 + 4 + 4);                        // J in BF16 and as two FP32
+        b += Bp * N * (3 * 4 + 2 + 4 + 2);              // psi x2, p, psi16, u32, u16
+        b += N * N * 2;                                  // J in BF16
+        if (N <= ACT_MAX_N) {                            // digit planes, exponents, G in FP64
+            b += (int64_t)ACT_DIGITS * (N * N + Bp * N) * 2 + Bp * N * 8 + (N + Bp) * 4;
+        } else {                                         // J as two FP32, G hi/lo
+            b += N * N * 8 + Bp * N * 8;
+        }
         b += C * (int64_t)(sizeof(ChainParams) + sizeof(ChainState) + 2 * sizeof(int));
         if (has_h) b += N * (int64_t)(2 * sizeof(float) + sizeof(double));
         return b + 4 * LOG1PEXP_NODES * 4;
@@ -506,27 +514,68 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         if ((st = dalloc(h, &h->dpsi16, bn * 2)) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->du32, bn * 4)) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->du16, bn * 2)) != ISING_OK) return bail(st);
-        if ((st = dalloc(h, &h->dGhi, bn * 4)) != ISING_OK) return bail(st);
-        if ((st = dalloc(h, &h->dGlo, bn * 4)) != ISING_OK) return bail(st);
+        const bool act_tc = N <= ACT_MAX_N;
         if ((st = dalloc(h, &h->dJ16, (size_t)N * N * 2)) != ISING_OK) return bail(st);
-        if ((st = dalloc(h, &h->dJhi, (size_t)N * N * 4)) != ISING_OK) return bail(st);
-        if ((st = dalloc(h, &h->dJlo, (size_t)N * N * 4)) != ISING_OK) return bail(st);
         std::vector<uint16_t> j16((size_t)N * N);
-        std::vector<float> jhi((size_t)N * N), jlo((size_t)N * N);
         for (size_t i = 0; i < (size_t)N * N; ++i) {
             const float f = (float)cfg->J[i];
-            jhi[i] = f;
-            jlo[i] = (float)(cfg->J[i] - (double)f);
             uint32_t b;
             std::memcpy(&b, &f, 4);
             j16[i] = (uint16_t)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);   // round to nearest even
         }
         if (cudaMemcpy(h->dJ16, j16.data(), j16.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(h->dJhi, jhi.data(), jhi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(h->dJlo, jlo.data(), jlo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(h->dpsi16, 0, bn * 2) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
             cudaMemset(h->du16, 0, bn * 2) != cudaSuccess || cudaMemset(h->psi[1], 0, bn * 4) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "dense upload failed"));
+        if (act_tc) {
+            // J in ACT_DIGITS base-2^ACT_BITS digit planes of row-scaled J (exact)
+            const size_t nn = (size_t)N * N;
+            if ((st = dalloc(h, &h->dJdig, (size_t)ACT_DIGITS * nn * 2)) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->dpsidig, (size_t)ACT_DIGITS * bn * 2)) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->drow_exp, (size_t)N * sizeof(int))) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->dchain_exp, (size_t)h->b_pad * sizeof(int))) != ISING_OK)
+                return bail(st);
+            if ((st = dalloc(h, &h->dG64, bn * 8)) != ISING_OK) return bail(st);
+            std::vector<uint16_t> dig((size_t)ACT_DIGITS * nn);
+            std::vector<int> rexp((size_t)N);
+            for (int64_t i = 0; i < N; ++i) {
+                const double *row = cfg->J + i * N;
+                double mx = 0.0;
+                for (int64_t j = 0; j < N; ++j) mx = std::max(mx, std::fabs(row[j]));
+                const int e = mx > 0.0 ? std::ilogb(mx) + 2 : 0;   // max |J_i.| 2^-e < 1/2
+                rexp[i] = e;
+                for (int64_t j = 0; j < N; ++j) {
+                    double x = std::ldexp(row[j], -e);
+                    for (int s = 0; s < ACT_DIGITS; ++s) {
+                        x *= (double)(1 << ACT_BITS);
+                        const double q = std::nearbyint(x);
+                        x -= q;
+                        const float f = (float)q;   // |q| <= 64: exact in BF16
+                        uint32_t b;
+                        std::memcpy(&b, &f, 4);
+                        dig[(size_t)s * nn + (size_t)i * N + j] = (uint16_t)(b >> 16);
+                    }
+                }
+            }
+            if (cudaMemcpy(h->dJdig, dig.data(), dig.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(h->drow_exp, rexp.data(), rexp.size() * sizeof(int),
+                           cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemset(h->dpsidig, 0, (size_t)ACT_DIGITS * bn * 2) != cudaSuccess)
+                return bail(fail(h, ISING_ECUDA, "dense upload failed"));
+        } else {
+            if ((st = dalloc(h, &h->dGhi, bn * 4)) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->dGlo, bn * 4)) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->dJhi, (size_t)N * N * 4)) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->dJlo, (size_t)N * N * 4)) != ISING_OK) return bail(st);
+            std::vector<float> jhi((size_t)N * N), jlo((size_t)N * N);
+            for (size_t i = 0; i < (size_t)N * N; ++i) {
+                jhi[i] = (float)cfg->J[i];
+                jlo[i] = (float)(cfg->J[i] - (double)jhi[i]);
+            }
+            if (cudaMemcpy(h->dJhi, jhi.data(), jhi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(h->dJlo, jlo.data(), jlo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(h, ISING_ECUDA, "dense upload failed"));
+        }
         DenseArgs &d = h->dense;
         d.J16 = (const __nv_bfloat16 *)h->dJ16;
         d.Jhi = (const float *)h->dJhi;
@@ -539,6 +588,12 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         d.u16 = (__nv_bfloat16 *)h->du16;
         d.Ghi = (float *)h->dGhi;
         d.Glo = (float *)h->dGlo;
+        d.action_tc = act_tc ? 1 : 0;
+        d.Jdig = (const __nv_bfloat16 *)h->dJdig;
+        d.psidig = (__nv_bfloat16 *)h->dpsidig;
+        d.row_exp = (const int *)h->drow_exp;
+        d.chain_exp = (int *)h->dchain_exp;
+        d.G64 = (double *)h->dG64;
         d.hdf = h->has_h ? (const float2 *)h->d_h32 : nullptr;
         d.lpe_tab = (const float4 *)h->d_lpe;
         d.params = h->d_params;

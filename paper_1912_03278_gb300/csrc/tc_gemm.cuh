@@ -317,17 +317,20 @@ struct Smem {
 constexpr int SMEM_BYTES = (int)sizeof(Smem) + 1024;
 
 // Persistent GEMM D = A B^T over m_units x n_units tiles of the mode's
-// TILE_M x TILE_N (K = nk * BK).  Single mode: CTA b takes tiles b, b +
-// gridDim.x, ...  Pair mode: clusters of two CTAs take tiles likewise; CTA r
-// of a pair stages A rows TILE_M*um + 128 r .. +127 and B rows TILE_N*un +
-// 128 r .. +127, signalling the leader's (rank 0) full barrier, whose MMA
-// thread computes the whole 256 x 256 tile into both CTAs' TMEM.
+// TILE_M x TILE_N (K = nk * BK), each computed reps times: repetition r reads
+// A from row epi.a_off(r) on and B from row epi.b_off(r) on (stacked operand
+// planes) and hands r to the epilogue.  Single mode: CTA b takes tiles b, b +
+// gridDim.x, ..., each with all its repetitions in order.  Pair mode:
+// clusters of two CTAs take tiles likewise; CTA r of a pair stages A rows
+// TILE_M*um + 128 r .. +127 and B rows TILE_N*un + 128 r .. +127, signalling
+// the leader's (rank 0) full barrier, whose MMA thread computes the whole
+// 256 x 256 tile into both CTAs' TMEM.
 //
 // Warp 0 streams the stage ring by TMA, warp 1 (leader) issues the MMAs into
 // one of two TMEM accumulators, and the epilogue warps of each CTA run
 // epi(row, col0, v[Epi::W]) on each Epi::W-column chunk of each of its 128
-// rows of the other accumulator, so the epilogue of one tile overlaps the MMAs of the
-// next.  MMA completion releases a stage (and, per tile, an accumulator) on
+// rows of the other accumulator, so the epilogue of one tile (or repetition)
+// overlaps the MMAs of the next.  MMA completion releases a stage (and, per tile, an accumulator) on
 // both CTAs of a pair; an accumulator is reused only after the epilogue warps
 // of both CTAs have read it.  Every wait is bounded; on a timeout the CTA
 // flags *err and stops issuing work.  Before teardown the producer waits for
@@ -338,8 +341,8 @@ constexpr int SMEM_BYTES = (int)sizeof(Smem) + 1024;
 // launch it overlaps that grid's tail.
 template <bool PAIR, class Epi>
 __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUtensorMap *tb,
-                                                int m_units, int n_units, int nk, Epi &epi,
-                                                int *err) {
+                                                int m_units, int n_units, int nk, int reps,
+                                                Epi &epi, int *err) {
     using Md = Mode<PAIR>;
     constexpr int TN = Md::TILE_N;
     extern __shared__ uint8_t smem_raw[];
@@ -350,7 +353,7 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
     const bool leader = rank == 0;
     const int c0 = PAIR ? (int)cluster_id() : (int)blockIdx.x;
     const int nclu = PAIR ? (int)cluster_count() : (int)gridDim.x;
-    const int units = m_units * n_units;
+    const int tiles = m_units * n_units;
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&s.full[i], 1);
@@ -377,9 +380,10 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
     if (warp == 0) {
         if (lane == 0) {
             uint32_t it = 0;
-            for (int u = c0; u < units && ok; u += nclu) {
-                const int a_row = (u % m_units) * Md::TILE_M + (int)rank * BM;
-                const int b_row = (u / m_units) * TN + (int)rank * BR;
+            for (int u = c0; u < tiles && ok; u += nclu)
+            for (int r = 0; r < reps && ok; ++r) {
+                const int a_row = (u % m_units) * Md::TILE_M + (int)rank * BM + epi.a_off(r);
+                const int b_row = (u / m_units) * TN + (int)rank * BR + epi.b_off(r);
                 for (int kb = 0; kb < nk; ++kb, ++it) {
                     const uint32_t st = it % STAGES;
                     if (it >= STAGES) ok = mbar_wait(&s.empty[st], ((it / STAGES) & 1) ^ 1);
@@ -405,7 +409,8 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
         if (lane == 0 && leader) {
             constexpr uint32_t idesc = idesc_bf16(Md::TILE_M, TN);
             uint32_t it = 0, lt = 0;
-            for (int u = c0; u < units && ok; u += nclu, ++lt) {
+            for (int u = c0; u < tiles && ok; u += nclu)
+            for (int r = 0; r < reps && ok; ++r, ++lt) {
                 const uint32_t buf = lt & 1;
                 if (lt >= 2)
                     ok = PAIR ? mbar_wait_cluster(&s.acc_empty[buf], ((lt >> 1) & 1) ^ 1)
@@ -444,7 +449,8 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
         const int g = (warp - 2) >> 2;
         const uint32_t empty0 = PAIR ? peer_addr(smem_u32(&s.acc_empty[0]), 0) : 0;
         uint32_t lt = 0;
-        for (int u = c0; u < units && ok; u += nclu, ++lt) {
+        for (int u = c0; u < tiles && ok; u += nclu)
+        for (int r = 0; r < reps && ok; ++r, ++lt) {
             const uint32_t buf = lt & 1;
             ok = mbar_wait(&s.acc_full[buf], (lt >> 1) & 1);
             if (!ok) break;
@@ -458,7 +464,7 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
             for (int c = g; c < TN / EW; c += EPI_GROUPS) {
                 float v[EW];
                 tc_ld<EW>(base + (uint32_t)(c * EW), v);
-                epi(m0 + row, n0 + c * EW, v);
+                epi(m0 + row, n0 + c * EW, v, r);
             }
             tc_fence_before();
             __syncwarp();
