@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // psi_cj = 2^f_c sum_t q_t 2^(-7(t+1)).  One digit-plane product sums N terms
 // of magnitude <= 2^12, so for N <= 4096 every partial sum is an integer
 // of magnitude <= 2^24 and the FP32 accumulator holds it exactly.  The
-// epilogue adds the ACT_PAIRS = 21 products with s + t <= 5,
-// 2^(-7(s+t)) I_st, in FP64:
-//   G_raw = sum_{s+t<=5} 2^(-7(s+t)) sum_j d_s,ij q_t,cj,
-//   (J psi)_ic = 2^(e_i + f_c - 14) G_raw.
+// epilogue adds the ACT_PAIRS = 21 products with s + t <= 5 exactly, as
+// 64-bit integers (no FP64 arithmetic, which is slow on this GPU):
+//   G_int = sum_{s+t<=5} 2^(7(5-s-t)) sum_j d_s,ij q_t,cj   (|G_int| < 2^60),
+//   (J psi)_ic = 2^(e_i + f_c - 49) G_int.
 // The dropped products (s+t >= 6) and the digit truncation weigh below
 // 2^-40 of 2^(e_i+f_c), far under the accuracy the action needs (Sec. 3:
 // dH decides the Metropolis test).
@@ -178,25 +178,25 @@ __constant__ int c_pair_t[ACT_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4,
                                         3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
 
 struct EpiG {
-    static constexpr int W = 16;
-    double *G;
+    static constexpr int W = 32;   // 32 reads of 8 bytes in flight per thread
+    long long *G;
     int N, n_chains, b_pad;
     __device__ int a_off(int r) const { return c_pair_s[r] * N; }
     __device__ int b_off(int r) const { return c_pair_t[r] * b_pad; }
     __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[W], int r) const {
-        const double sc = ldexp(1.0, -ACT_BITS * (c_pair_s[r] + c_pair_t[r]));
-        double *g = G + (int64_t)n0 * N + m;
+        const int sh = ACT_BITS * (ACT_DIGITS - 1 - c_pair_s[r] - c_pair_t[r]);
+        long long *g = G + (int64_t)n0 * N + m;
         if (r == 0) {
 #pragma unroll
             for (int j = 0; j < W; ++j)
-                if (n0 + j < n_chains) g[j * N] = (double)v[j] * sc;
+                if (n0 + j < n_chains) g[j * N] = (long long)__float2int_rn(v[j]) << sh;
         } else {
-            double old[W];
+            long long old[W];
 #pragma unroll
-            for (int j = 0; j < W; ++j) old[j] = (n0 + j < n_chains) ? g[j * N] : 0.0;
+            for (int j = 0; j < W; ++j) old[j] = (n0 + j < n_chains) ? g[j * N] : 0;
 #pragma unroll
             for (int j = 0; j < W; ++j)
-                if (n0 + j < n_chains) g[j * N] = fma((double)v[j], sc, old[j]);
+                if (n0 + j < n_chains) g[j * N] = old[j] + ((long long)__float2int_rn(v[j]) << sh);
         }
     }
 };
@@ -205,15 +205,17 @@ template <bool PAIR>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     action_kernel(const __grid_constant__ CUtensorMap tjd, const __grid_constant__ CUtensorMap tpd,
                   const __grid_constant__ DenseArgs d) {
-    EpiG epi{d.G64, d.N, d.n_chains, d.b_pad};
+    EpiG epi{d.Gint, d.N, d.n_chains, d.b_pad};
     using Md = tc::Mode<PAIR>;
     tc::gemm_persistent<PAIR>(&tjd, &tpd, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK,
                               ACT_PAIRS, epi, d.err);
 }
 
 // Digits of Psi (chain c = block): f_c from max |psi_c|, then ACT_DIGITS
-// base-128 digits of psi * 2^-f_c per site, each digit plane b_pad x N
-// (padding chains get zero digits).  All steps are exact in FP64.
+// base-128 digits in [-64, 64] of X = round(psi 2^(42 - f_c)), the integer
+// taken from the FP32 bit pattern, per site; each digit plane is b_pad x N
+// (padding chains get zero digits).  |psi 2^-f_c| < 1/2, so |X| <= 2^41 and
+// six digits represent it exactly.
 __global__ void __launch_bounds__(256) k_psi_digits(const float *__restrict__ psi,
                                                     __nv_bfloat16 *__restrict__ dig,
                                                     int *__restrict__ chain_exp, int N,
@@ -232,15 +234,30 @@ __global__ void __launch_bounds__(256) k_psi_digits(const float *__restrict__ ps
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
     const int f = mx > 0.0f ? ilogbf(mx) + 2 : 0;   // max |psi| * 2^-f < 1/2
     if (threadIdx.x == 0) chain_exp[n] = f;
+    constexpr int FRAC = ACT_BITS * ACT_DIGITS;   // 42 fraction bits
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
-        double x = live ? ldexp((double)psi[(int64_t)n * N + m], -f) : 0.0;
+        long long X = 0;
+        if (live) {
+            const uint32_t b = __float_as_uint(psi[(int64_t)n * N + m]);
+            const int be = (int)((b >> 23) & 0xFF);
+            if (be) {   // normal (subnormals lie far below the last digit)
+                const long long M = (long long)((b & 0x7FFFFFu) | 0x800000u);
+                const int sh = be - 150 - f + FRAC;   // psi 2^(FRAC-f) = M 2^sh
+                if (sh >= 0)
+                    X = M << sh;
+                else if (sh > -40)
+                    X = (M + (1ll << (-sh - 1))) >> (-sh);
+                if (b >> 31) X = -X;
+            }
+        }
+        // low digits in [-64, 63]; the top digit takes the rest, |rest| <= 64
 #pragma unroll
-        for (int t = 0; t < ACT_DIGITS; ++t) {
-            x *= (double)(1 << ACT_BITS);
-            const double q = rint(x);
-            x -= q;
+        for (int t = ACT_DIGITS - 1; t >= 1; --t) {
+            const int q = (int)(((X + 64) & 127) - 64);
+            X = (X - q) >> ACT_BITS;
             dig[((int64_t)t * b_pad + n) * N + m] = __float2bfloat16_rn((float)q);
         }
+        dig[(int64_t)n * N + m] = __float2bfloat16_rn((float)(int)X);
     }
 }
 
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(256) k_df_gemm(const float *__restrict__ Jhi,
 // mode 0: end of a trajectory (psi_w = proposal, p = end momenta, K0 from the
 // regenerated momenta, Metropolis test, copy to psi_cur on accept);
 // mode 1: evaluate S and the estimators of psi_cur (G computed from psi_cur).
-__global__ void __launch_bounds__(256) k_dense_finalize(DenseArgs d, int mode, uint32_t traj,
+__global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode, uint32_t traj,
                                                         uint64_t seed, int measure) {
     __shared__ float4 tab[LOG1PEXP_NODES];
     __shared__ double red[32 * 8];
@@ -367,10 +384,16 @@ __global__ void __launch_bounds__(256) k_dense_finalize(DenseArgs d, int mode, u
             const int m = 4 * q + k;
             const int64_t idx = (int64_t)n * d.N + m;
             const float ps = psi[m];
-            const f2 G = d.action_tc
-                             ? df_from_double(ldexp(d.G64[idx], d.row_exp[m] + d.chain_exp[n] -
-                                                                    2 * ACT_BITS))
-                             : f2{d.Ghi[idx], d.Glo[idx]};
+            f2 G;
+            if (d.action_tc) {   // exact integer digit sum -> double-float (48 bits)
+                const long long gi = d.Gint[idx];
+                const float ghi = __ll2float_rn(gi);
+                const float glo = __ll2float_rn(gi - __float2ll_rn(ghi));
+                const int sh = d.row_exp[m] + d.chain_exp[n] - ACT_BITS * (ACT_DIGITS + 1);
+                G = f2{ldexpf(ghi, sh), ldexpf(glo, sh)};
+            } else {
+                G = f2{d.Ghi[idx], d.Glo[idx]};
+            }
             const f2 a = df_add(df_mul(beta2, G), df_mul_f(C2, ps));
             f2 x = a;
             float hq = pr.hpf;

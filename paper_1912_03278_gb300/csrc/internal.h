@@ -102,8 +102,8 @@ constexpr int LOG1PEXP_NODES = 36 * 32 + 1;
 // action).  Arrays are chain-major with b_pad >= n_chains rows (a multiple of
 // 128; padded chains stay zero) and N sites (a multiple of 128).
 // Exact digit-sliced action product: ACT_DIGITS signed base-2^ACT_BITS
-// digits per operand, ACT_PAIRS digit-plane products (all with s + t <= 5),
-// exact in the FP32 accumulator up to ACT_MAX_N sites.
+// digits per operand, ACT_PAIRS digit-plane products (all with s + t <=
+// ACT_DIGITS - 1), exact in the FP32 accumulator up to ACT_MAX_N sites.
 constexpr int ACT_BITS = 7, ACT_DIGITS = 6, ACT_PAIRS = 21, ACT_MAX_N = 4096;
 
 struct DenseArgs {
@@ -117,13 +117,13 @@ struct DenseArgs {
     __nv_bfloat16 *u16;         // BF16 copy of u (GEMM operand)
     float *Ghi, *Glo;           // J psi as a double-float pair (action, N > 4096)
     // action product on the tensor cores (N <= 4096): digit planes of J and
-    // psi, exponents of their row / chain scales, FP64 digit sum
+    // psi, exponents of their row / chain scales, exact integer digit sum
     int action_tc;
     const __nv_bfloat16 *Jdig;  // ACT_DIGITS planes of N x N
     __nv_bfloat16 *psidig;      // ACT_DIGITS planes of b_pad x N
     const int *row_exp;         // N
     int *chain_exp;             // b_pad
-    double *G64;                // b_pad x N, chain-major
+    long long *Gint;            // b_pad x N, chain-major
     const float2 *hdf;          // per-site h_i as hi/lo floats, or null
     const float4 *lpe_tab;      // log(1 + exp(-y)) table (global)
     const ChainParams *params;

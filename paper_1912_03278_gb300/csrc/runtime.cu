@@ -48,7 +48,7 @@ struct ising_hmc {
     void *dJ16 = nullptr, *dJhi = nullptr, *dJlo = nullptr, *dpsi16 = nullptr, *du32 = nullptr,
          *du16 = nullptr, *dGhi = nullptr, *dGlo = nullptr;
     void *dJdig = nullptr, *dpsidig = nullptr, *drow_exp = nullptr, *dchain_exp = nullptr,
-         *dG64 = nullptr;
+         *dGint = nullptr;
     // counters
     int64_t traj = 0;
     int64_t launches = 0;
@@ -204,7 +204,7 @@ static void free_all(ising_hmc *h) {
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
                     h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err, h->dJ16,
                     h->dJhi, h->dJlo, h->dpsi16, h->du32, h->du16, h->dGhi, h->dGlo,
-                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dG64};
+                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dGint};
     for (void *b : bufs)
         if (b) cudaFree(b);
     h->p = nullptr;
@@ -219,7 +219,7 @@ static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_
         const int64_t Bp = (C + 127) / 128 * 128;
         b += Bp * N * (3 * 4 + 2 + 4 + 2);              // psi x2, p, psi16, u32, u16
         b += N * N * 2;                                  // J in BF16
-        if (N <= ACT_MAX_N) {                            // digit planes, exponents, G in FP64
+        if (N <= ACT_MAX_N) {                            // digit planes, exponents, G as int64
             b += (int64_t)ACT_DIGITS * (N * N + Bp * N) * 2 + Bp * N * 8 + (N + Bp) * 4;
         } else {                                         // J as two FP32, G hi/lo
             b += N * N * 8 + Bp * N * 8;
@@ -535,7 +535,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             if ((st = dalloc(h, &h->drow_exp, (size_t)N * sizeof(int))) != ISING_OK) return bail(st);
             if ((st = dalloc(h, &h->dchain_exp, (size_t)h->b_pad * sizeof(int))) != ISING_OK)
                 return bail(st);
-            if ((st = dalloc(h, &h->dG64, bn * 8)) != ISING_OK) return bail(st);
+            if ((st = dalloc(h, &h->dGint, bn * 8)) != ISING_OK) return bail(st);
             std::vector<uint16_t> dig((size_t)ACT_DIGITS * nn);
             std::vector<int> rexp((size_t)N);
             for (int64_t i = 0; i < N; ++i) {
@@ -593,7 +593,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         d.psidig = (__nv_bfloat16 *)h->dpsidig;
         d.row_exp = (const int *)h->drow_exp;
         d.chain_exp = (int *)h->dchain_exp;
-        d.G64 = (double *)h->dG64;
+        d.Gint = (long long *)h->dGint;
         d.hdf = h->has_h ? (const float2 *)h->d_h32 : nullptr;
         d.lpe_tab = (const float4 *)h->d_lpe;
         d.params = h->d_params;
