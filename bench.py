@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -133,6 +134,14 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def measured_peaks_all():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def traffic_record(kernel, workload):
@@ -359,6 +368,8 @@ def run_ours(args):
     if rank == 0:
         if not args.no_mixed:
             line["mixed_3d"] = mixed_3d_rate(pkg)
+        if not args.no_dense:
+            line["dense"] = dense_rate(pkg, stream)
         if not args.no_serve:
             line["serve"] = serve_run(pkg, args.serve_seconds)
         if not args.no_cpu:
@@ -401,6 +412,95 @@ def plain_rate(pkg, L, betas, C, tuned, stream):
                 "acceptance_sample": acc}
     finally:
         sim.close()
+
+
+def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10):
+    """Dense all-to-all couplings: SK model N = 4096, J_ij ~ N(0, 1/N) symmetric
+    with J_ii = 0, h_i ~ N(0, 0.1^2), beta = 0.5, C = beta |lambda_min(J)| + 0.1,
+    1024 chains, BF16 tensor-core force with FP32 state, FP64-accurate action
+    (exact digit-sliced tensor-core product), N_md = 10, eps tuned towards 80%
+    acceptance.  Times whole trajectories and, separately, force evaluations
+    (two 4096 x 4096 x 1024 GEMMs each), both with CUDA events on the
+    handle's stream."""
+    import torch
+    N, B, beta = 4096, 1024, 0.5
+    J = workloads.dense_couplings(N, seed=1)
+    hv = workloads.dense_fields(N, 0.1, seed=2)
+    try:
+        from scipy.sparse.linalg import eigsh
+        lam = float(eigsh(J, k=1, which="SA", return_eigenvectors=False)[0])
+    except Exception:
+        lam = float(np.linalg.eigvalsh(J)[0])
+    C = beta * abs(lam) + 0.1
+    sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=0.05, n_md=n_md, n_chains=B,
+                       precision=pkg.ISING_PREC_BF16, stream=stream.cuda_stream)
+    try:
+        eps = 0.05
+        trace = []
+        sim.trajectories(4, seed)   # leave psi = 0
+        for _ in range(tune_rounds):
+            sim.trajectories(2, seed)
+            acc = float(sim.records()[:, 2].mean())
+            trace.append((round(eps, 5), round(acc, 3)))
+            eps *= 1.35 if acc > 0.93 else 1.12 if acc > 0.85 else 0.75 if acc < 0.6 else \
+                0.92 if acc < 0.75 else 1.0
+            sim.set_eps(np.full(B, eps))
+        sim.trajectories(2, seed)
+        sim.reset_sums()
+        torch.cuda.synchronize()
+        l0 = sim.launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.trajectories(steps, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_traj = e0.elapsed_time(e1) / steps
+        launches = sim.launches - l0
+        obs = sim.observables()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sim.dense_forces(2)
+        f0.record(stream)
+        sim.dense_forces(n_force)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_force = f0.elapsed_time(f1) / n_force
+    finally:
+        sim.close()
+    flops_force = 2 * 2.0 * N * N * B
+    tf = flops_force / (ms_force * 1e-3) / 1e12
+    peaks = measured_peaks_all()
+    peak = peaks.get("bf16_tflops") or 1900.0
+    out = {"workload": "dense SK couplings N=%d, J~N(0,1/N), h~N(0,0.01), beta=%g, "
+                       "C=beta|lambda_min|+0.1=%.4f, %d chains, N_md=%d, eps tuned"
+                       % (N, beta, C, B, n_md),
+           "value": N * B * n_md / (ms_traj * 1e-3), "unit": UNIT, "ms_per_trajectory": ms_traj,
+           "acceptance": obs["acceptance"], "eps": eps, "tuning": trace,
+           "gpu_launches_per_trajectory": launches / steps,
+           "fixed_ms_per_trajectory": ms_traj - (n_md + 1) * ms_force,
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                        "frac": tf / peak, "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"
+                        if peaks.get("bf16_tflops") else "fallback",
+                        "kernel": "force1_kernel + force2_kernel (one force evaluation)",
+                        "algorithmic_flops_per_force": flops_force, "ms_per_force": ms_force}}
+    # plain one-chain-per-launch FP64 form on a few chains of the same model
+    try:
+        k = 2
+        pl = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=eps, n_md=n_md, n_chains=k,
+                          precision=pkg.ISING_PREC_PLAIN_FP64, stream=stream.cuda_stream)
+        pl.trajectories(1, seed)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pl.trajectories(1, seed)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        rate = N * k * n_md / (p0.elapsed_time(p1) * 1e-3)
+        pl.close()
+        out["plain_form"] = {"value": rate, "unit": UNIT, "chains": k}
+        out["speedup_vs_plain"] = out["value"] / rate
+    except Exception as e:   # report, do not hide
+        out["plain_form"] = {"error": str(e)}
+    return out
 
 
 def mixed_3d_rate(pkg, steps=4, seed=31):

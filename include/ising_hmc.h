@@ -318,6 +318,15 @@ const char *ising_hmc_energy_noalloc_error(void);
 ising_status ising_hmc_selftest_gemm(int M, int N, int K, const uint16_t *A, const uint16_t *B,
                                      float *D);
 
+/* Timing aid for the BF16 dense form (no counterpart in the paper): n
+ * evaluations of the force F = A(tanh(A psi + h') - psi) (Sec. 3) on the
+ * handle's working configurations, each the two tensor-core GEMMs with their
+ * epilogues, queued on the handle's stream.  It overwrites only the working
+ * buffers a trajectory re-initialises (proposal, momenta, u); the chains'
+ * configurations, records and sums are untouched.  Asynchronous.  Errors:
+ * EINVAL (not the BF16 dense form, n < 0), ECUDA. */
+ising_status ising_hmc_dense_forces(ising_hmc_t *h, int n);
+
 void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);

@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "ising_hmc_sync": (c_int, [P]),
         "ising_hmc_selftest": (c_int, [c_int, P, P, c_int64]),
         "ising_hmc_selftest_gemm": (c_int, [c_int, c_int, c_int, P, P, P]),
+        "ising_hmc_dense_forces": (c_int, [P, c_int]),
         "ising_hmc_set_launch": (c_int, [P, c_int, c_int]),
         "ising_hmc_get_launch": (c_int, [P, P, P]),
         "ising_hmc_autotune": (c_int, [P, c_int, P]),
@@ -335,6 +336,10 @@ def ising_hmc_autotune(h, reps=2) -> float:
     ms = c_double()
     _check(h, load().ising_hmc_autotune(h, int(reps), ctypes.byref(ms)))
     return ms.value
+
+
+def ising_hmc_dense_forces(h, n):
+    _check(h, load().ising_hmc_dense_forces(h, int(n)))
 
 
 def _gcheck(g, st):
@@ -606,6 +611,10 @@ class IsingHMC:
 
     def autotune(self, reps=2):
         return ising_hmc_autotune(self.h, reps)
+
+    def dense_forces(self, n):
+        """Queue n force evaluations (BF16 dense form; timing aid)."""
+        ising_hmc_dense_forces(self.h, n)
 
     def set_launch(self, threads, depth):
         ising_hmc_set_launch(self.h, threads, depth)

@@ -995,6 +995,18 @@ ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth
 // Autotuner: time one trajectory of every valid (threads, depth) on a
 // temporary copy of the handle's geometry and parameters (so the handle's own
 // chains do not move) and keep the fastest.
+ising_status ising_hmc_dense_forces(ising_hmc_t *h, int n) {
+    if (!h) return ISING_EINVAL;
+    if (!is_dense_tc(h)) return fail(h, ISING_EINVAL, "dense_forces applies to the BF16 dense form");
+    if (n < 0) return fail(h, ISING_EINVAL, "n must be >= 0");
+    for (int i = 0; i < n; ++i) {
+        const cudaError_t e = dense_force_once(h->dense, h->stream);
+        h->launches += 2;
+        if (e != cudaSuccess) return fail(h, ISING_ECUDA, "dense force: %s", cudaGetErrorString(e));
+    }
+    return ISING_OK;
+}
+
 ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     if (!h) return ISING_EINVAL;
     if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "autotune applies to the FP32 lattice form");

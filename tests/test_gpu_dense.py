@@ -112,3 +112,25 @@ def test_dense_bf16_statistics_small_against_brute_force():
     for key in ("E", "m"):
         err = np.hypot(a[key + "_err"], b[key + "_err"])
         assert abs(a[key] - b[key]) <= 4 * err + 1e-3, (key, a[key], b[key], err)
+
+
+def test_dense_forces_timing_aid_leaves_chains_untouched():
+    """ising_hmc_dense_forces overwrites only working buffers: a trajectory
+    after it is bitwise the trajectory without it."""
+    N, B, beta = 256, 130, 0.5
+    J = workloads.dense_couplings(N, seed=3)
+    C = beta * abs(np.linalg.eigvalsh(J)[0]) + 0.1
+    mk = lambda: binding.IsingHMC(kind="dense", J=J, beta=beta, C=C, eps=0.05, n_md=4, n_chains=B,
+                                  precision=binding.ISING_PREC_BF16)
+    a, b = mk(), mk()
+    try:
+        a.trajectories(2, 11)
+        b.trajectories(2, 11)
+        a.dense_forces(3)
+        a.trajectories(1, 11)
+        b.trajectories(1, 11)
+        assert np.array_equal(a.state(), b.state())
+        assert np.array_equal(a.records(), b.records())
+    finally:
+        a.close()
+        b.close()
