@@ -52,6 +52,7 @@ struct Request {
 
 struct ising_server {
     int64_t budget = 0, in_use = 0;
+    int admitting = 0;   // taken off the queue, handle being created (not yet active)
     int quantum = 1;
     int device = 0;
     std::mutex mu;
@@ -127,12 +128,14 @@ static void worker_loop(ising_server *s) {
                 if (s->in_use + r.bytes > s->budget) break;
                 s->in_use += r.bytes;
                 s->queue.pop_front();
+                s->admitting += 1;
                 to_admit.push_back(&r);
             }
         }
         for (Request *r : to_admit) {
             ising_status st = ising_hmc_create(&r->cfg, &r->sim);
             std::lock_guard<std::mutex> lk(s->mu);
+            s->admitting -= 1;
             if (st != ISING_OK) {
                 r->state = 3;
                 r->status = st;
@@ -302,7 +305,10 @@ ising_status ising_server_drain(ising_server_t *s, double timeout_s) {
     if (!s) return ISING_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     const bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
-                                        [&] { return s->queue.empty() && s->active.empty(); });
+                                        [&] {
+                                            return s->queue.empty() && s->admitting == 0 &&
+                                                   s->active.empty();
+                                        });
     return ok ? ISING_OK : sfail(s, ISING_ETIMEOUT, "drain: work remains");
 }
 
