@@ -181,16 +181,114 @@ __device__ __forceinline__ Acc acc_zero() {
 struct PassCfg {
     int src, dst;
     float kick, drift;   // already multiplied by eps
-    bool first, last;    // first pass sums K0; last pass has no drift and sums K1
+    bool first, last;    // first pass draws p and sums K0; last pass has no drift, sums K1
+                         // and evaluates the action of its configuration
+    uint32_t traj;       // trajectory index (momenta and spin draws)
 };
 
 __device__ __forceinline__ float *sel3(const FusedArgs &A, int i) {
     return i == 0 ? A.psi[0] : (i == 1 ? A.psi[1] : A.psi[2]);
 }
 
-template <int DIM, int VEC, int D>
+// Per-chain constants of the action in double-float form.
+struct ActConst {
+    f2 C2, bJ2, hp2, beta2;
+    float Cf, bJf;
+    bool hzero;
+};
+
+__device__ __forceinline__ ActConst act_const(const ChainParams &prm) {
+    ActConst k;
+    k.C2 = df_from_double(prm.C);
+    k.bJ2 = df_from_double(prm.bJ);
+    k.hp2 = df_from_double(prm.hp);
+    k.beta2 = df_from_double(prm.beta);
+    k.Cf = prm.Cf;
+    k.bJf = prm.bJf;
+    k.hzero = prm.hp == 0.0;
+    return k;
+}
+
+// Action terms of the VEC sites site0.. of S(sign*psi), whose neighbourhood n
+// has been gathered:  S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),
+// x = a + h', a = A psi, in double-float arithmetic; the Sec. 4 estimators
+// (tanh(x) sums) and one conditional spin draw per site.
+template <int DIM, int VEC>
+__device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst &kc,
+                                              const Nbr<DIM, VEC> &n, int64_t site0, float sign,
+                                              uint32_t spin_traj, uint64_t seed, int chain,
+                                              const float4 *tab, Acc &acc) {
+    float su[4];
+    if constexpr (VEC == 4) {
+        const float4 w = spin_u4_f32((uint32_t)(site0 >> 2), spin_traj, (uint32_t)chain, seed);
+        su[0] = w.x; su[1] = w.y; su[2] = w.z; su[3] = w.w;
+    }
+    f2 sv{0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+        const float ps = sign * n.c.v[q];
+        const f2 nbd = exact_nb<DIM, VEC>(n, q);
+        const f2 a = df_add(df_mul_f(kc.C2, ps), df_mul(kc.bJ2, f2{sign * nbd.hi, sign * nbd.lo}));
+        f2 x = a;
+        float hq = 0.0f;
+        if (A.hdf) {
+            const float2 hh = A.hdf[site0 + q];
+            const f2 hp = df_mul(kc.beta2, f2{hh.x, hh.y});
+            x = df_add(a, hp);
+            hq = hp.hi;
+        } else if (!kc.hzero) {
+            x = df_add(a, kc.hp2);
+            hq = kc.hp2.hi;
+        }
+        const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
+        const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, tab);
+        // S_i for this site, summed over the vector first (short chains)
+        const f2 si = df_add(df_mul_f(a, 0.5f * ps), df_neg(df_add(ax, gl)));
+        sv = df_add(sv, si);
+        const float tq = tanh_f(fmaf(kc.Cf, ps, sign * kc.bJf * n.nb.v[q]) + hq);
+        kahan_add(acc.sT, acc.cT, tq);
+        kahan_add(acc.sAT, acc.cAT, a.hi * tq);
+        kahan_add(acc.sHT, acc.cHT, hq * tq);
+        float uu;
+        if constexpr (VEC == 4) {
+            uu = su[q];
+        } else {
+            const float4 w = spin_u4_f32((uint32_t)((site0 + q) >> 2), spin_traj, (uint32_t)chain,
+                                         seed);
+            const int qq = (int)((site0 + q) & 3);
+            uu = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
+        }
+        acc.sS += (uu < (1.0f + tq) * 0.5f) ? 1 : -1;
+    }
+    acc_add(acc.S, acc.Slo, sv);
+}
+
+// FP32 momenta of the VEC sites site0.. (Sec. 3 momentum refresh): the same
+// Philox draws as the momentum sweep.
+template <int VEC>
+__device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, int chain,
+                                                 uint64_t seed) {
+    Vec<VEC> pv;
+    if constexpr (VEC == 4) {
+        const float4 w = momenta4_f32((uint32_t)(site0 >> 2), traj, (uint32_t)chain, seed);
+        pv.v[0] = w.x; pv.v[1] = w.y; pv.v[2] = w.z; pv.v[3] = w.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const float4 w = momenta4_f32((uint32_t)((site0 + q) >> 2), traj, (uint32_t)chain, seed);
+            const int qq = (int)((site0 + q) & 3);
+            pv.v[q] = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
+        }
+    }
+    return pv;
+}
+
+// FIRST: the first pass of the trajectory (draws the momenta, sums K0);
+// LAST: the final pass (no drift; sums K1 and evaluates the proposal's
+// action).  Both are compiled apart so the other passes keep a lean loop.
+template <int DIM, int VEC, int D, bool FIRST, bool LAST>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
-                         const Slots &sl, float *smem, Acc &acc) {
+                         const Slots &sl, float *smem, const float4 *tab, Acc &acc) {
     constexpr int R = D + 4;   // psi ring slots
     constexpr int RP = D + 2;  // p ring slots
     const Geometry &g = A.g;
@@ -220,7 +318,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
             }
         }
         const int zp = s - 4;
-        if (zp >= 0 && zp < nz) {
+        if (zp >= 0 && zp < nz && !FIRST) {   // the first pass draws p itself
             const float *src = gp + (int64_t)zp * P;
             float *dst = p_ring + (unsigned)s % RP * P;
             if constexpr (VEC == 4) {
@@ -239,6 +337,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     int s_next = D + 3;
 
     const float Cf = prm.Cf, bJf = prm.bJf;
+    ActConst kc;
+    if constexpr (LAST) kc = act_const(prm);
 
     for (int it = -1; it <= nz; ++it) {
         cp_wait<D>();
@@ -270,6 +370,13 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
 #pragma unroll
                     for (int q = 0; q < VEC; ++q) u.v[q] = t.v[q] - n.c.v[q];
                     stv<VEC>(uo + e0, u);
+                    // the last pass's configuration is the proposal: its action
+                    // from the neighbourhood already gathered (each plane once)
+                    if constexpr (LAST) {
+                        if (it >= 0 && it < nz)
+                            vector_action<DIM, VEC>(A, kc, n, (int64_t)it * P + e0, 1.0f, pc.traj,
+                                                    A.seed, chain, tab, acc);
+                    }
                 }
             }
         }
@@ -288,8 +395,12 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 const int e0 = sl.e0[k];
                 Nbr<DIM, VEC> n;
                 gather<DIM, VEC>(g, um, uc, uq, e0, sl.x0[k], n);
-                Vec<VEC> pv = ldv<VEC>(ppz + e0);
-                if (pc.first && sl.valid[k]) {
+                Vec<VEC> pv;
+                if constexpr (FIRST)
+                    pv = draw_momenta<VEC>((int64_t)z * P + e0, pc.traj, chain, A.seed);
+                else
+                    pv = ldv<VEC>(ppz + e0);
+                if (FIRST && sl.valid[k]) {
 #pragma unroll
                     for (int q = 0; q < VEC; ++q)
                         acc_add(acc.K0, acc.K0lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
@@ -301,7 +412,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 }
                 if (sl.valid[k]) {
                     stv<VEC>(gpz + e0, pv);
-                    if (pc.last) {
+                    if constexpr (LAST) {
 #pragma unroll
                         for (int q = 0; q < VEC; ++q)
                             acc_add(acc.K1, acc.K1lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
@@ -353,10 +464,11 @@ __device__ void momenta_sweep(const FusedArgs &A, int chain, uint32_t traj, cons
 // Action S(sign*psi) (Sec. 2, Eq. phi_psi_substitution in the form
 // S = 1/2 psi.A psi - sum_i log 2cosh((A psi)_i + h'_i)) to FP64 accuracy in
 // double-float arithmetic, and the Sec. 4 estimators with one conditional
-// spin draw, over the chain stored in buffer `buf`:
-//   S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),  x = a + h'.
-// No barriers: every thread streams its own vectors, neighbours come from
-// global memory (L1/L2).
+// spin draw, over the chain stored in buffer `buf`.  No barriers: every
+// thread streams its own vectors, neighbours come from global memory (L1/L2).
+// (The proposal's action at the end of a trajectory is evaluated inside the
+// last force pass instead; this sweep serves the sign flip and the current
+// state.)
 template <int DIM, int VEC>
 __device__ void action_sweep(const FusedArgs &A, const ChainParams &prm, int chain, int buf,
                              float sign, uint32_t spin_traj, uint64_t seed, const Slots &sl,
@@ -364,10 +476,7 @@ __device__ void action_sweep(const FusedArgs &A, const ChainParams &prm, int cha
     const Geometry &g = A.g;
     const int P = g.P, nz = g.nplanes;
     const float *psi = sel3(A, buf) + (int64_t)chain * g.N;
-    const float Cf = prm.Cf, bJf = prm.bJf;
-    const f2 C2 = df_from_double(prm.C), bJ2 = df_from_double(prm.bJ);
-    const f2 hp2 = df_from_double(prm.hp), beta2 = df_from_double(prm.beta);
-    const bool hzero = prm.hp == 0.0;
+    const ActConst kc = act_const(prm);
     for (int z = 0; z < nz; ++z) {
         const float *pc = psi + (int64_t)z * P;
         const float *pm = psi + (int64_t)(z == 0 ? nz - 1 : z - 1) * P;
@@ -379,50 +488,8 @@ __device__ void action_sweep(const FusedArgs &A, const ChainParams &prm, int cha
             const int e0 = sl.e0[k];
             Nbr<DIM, VEC> n;
             gather<DIM, VEC>(g, pm, pc, pq, e0, sl.x0[k], n);
-            const int64_t site0 = (int64_t)z * P + e0;
-            float su[4];
-            if constexpr (VEC == 4) {
-                const float4 w = spin_u4_f32((uint32_t)(site0 >> 2), spin_traj, (uint32_t)chain, seed);
-                su[0] = w.x; su[1] = w.y; su[2] = w.z; su[3] = w.w;
-            }
-            f2 sv{0.0f, 0.0f};
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                const float ps = sign * n.c.v[q];
-                const f2 nbd = exact_nb<DIM, VEC>(n, q);
-                const f2 a = df_add(df_mul_f(C2, ps), df_mul(bJ2, f2{sign * nbd.hi, sign * nbd.lo}));
-                f2 x = a;
-                float hq = 0.0f;
-                if (A.hdf) {
-                    const float2 hh = A.hdf[site0 + q];
-                    const f2 hp = df_mul(beta2, f2{hh.x, hh.y});
-                    x = df_add(a, hp);
-                    hq = hp.hi;
-                } else if (!hzero) {
-                    x = df_add(a, hp2);
-                    hq = hp2.hi;
-                }
-                const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
-                const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, tab);
-                // S_i for this site, summed over the vector first (short chains)
-                const f2 si = df_add(df_mul_f(a, 0.5f * ps), df_neg(df_add(ax, gl)));
-                sv = df_add(sv, si);
-                const float tq = tanh_f(fmaf(Cf, ps, sign * bJf * n.nb.v[q]) + hq);
-                kahan_add(acc.sT, acc.cT, tq);
-                kahan_add(acc.sAT, acc.cAT, a.hi * tq);
-                kahan_add(acc.sHT, acc.cHT, hq * tq);
-                float uu;
-                if constexpr (VEC == 4) {
-                    uu = su[q];
-                } else {
-                    const float4 w = spin_u4_f32((uint32_t)((site0 + q) >> 2), spin_traj,
-                                                 (uint32_t)chain, seed);
-                    const int qq = (int)((site0 + q) & 3);
-                    uu = qq == 0 ? w.x : qq == 1 ? w.y : qq == 2 ? w.z : w.w;
-                }
-                acc.sS += (uu < (1.0f + tq) * 0.5f) ? 1 : -1;
-            }
-            acc_add(acc.S, acc.Slo, sv);
+            vector_action<DIM, VEC>(A, kc, n, (int64_t)z * P + e0, sign, spin_traj, seed, chain,
+                                    tab, acc);
         }
     }
 }
@@ -442,7 +509,7 @@ __device__ __forceinline__ void set_obs(ChainState *st, const ChainParams &prm, 
 }
 
 template <int DIM, int VEC, int D>
-__global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedule S) {
+__global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Schedule S) {
     extern __shared__ float4 smem_f4[];
     float *smem = reinterpret_cast<float *>(smem_f4);
     constexpr int R = D + 4, RP = D + 2;
@@ -485,9 +552,8 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
     for (int k = 0; k < A.n_traj; ++k) {
         const uint32_t traj = A.traj0 + (uint32_t)k;
         Acc acc = acc_zero();
-        // momentum refresh, then the integrator's force passes
-        momenta_sweep<VEC>(A, chain, traj, sl);
-        __syncthreads();
+        // the integrator's force passes; the first draws the momenta (Sec. 3
+        // refresh), the last evaluates the proposal's action
         for (int j = 0; j < S.n_pass; ++j) {
             PassCfg pc;
             pc.src = buf_loc(start, j);
@@ -496,10 +562,17 @@ __global__ void __launch_bounds__(256) fused_lattice_kernel(FusedArgs A, Schedul
             pc.drift = (float)(S.drift[j] * prm.eps);
             pc.first = (j == 0);
             pc.last = (j == S.n_pass - 1);
-            run_pass<DIM, VEC, D>(A, pc, prm, chain, sl, smem, acc);
+            pc.traj = traj;
+            if (pc.first && pc.last)
+                run_pass<DIM, VEC, D, true, true>(A, pc, prm, chain, sl, smem, tab, acc);
+            else if (pc.first)
+                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc);
+            else if (pc.last)
+                run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc);
+            else
+                run_pass<DIM, VEC, D, false, false>(A, pc, prm, chain, sl, smem, tab, acc);
         }
         const int prop = buf_loc(start, S.n_pass - 1);
-        action_sweep<DIM, VEC>(A, prm, chain, prop, 1.0f, traj, A.seed, sl, tab, acc);
         double v[7] = {acc_val(acc.K0, acc.K0lo), acc_val(acc.K1, acc.K1lo),
                        acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
                        kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
