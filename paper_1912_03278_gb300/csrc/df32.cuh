@@ -44,6 +44,14 @@ __device__ __forceinline__ f2 df_add(f2 a, f2 b) {
     return fast_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
 }
 
+// Quicker sum (one TwoSum, the low words added in FP32): its error is a few
+// units of 2^-48 of max(|a|, |b|) in absolute terms -- the accuracy the action
+// sums need -- though not relative to a small result.
+__device__ __forceinline__ f2 df_add_q(f2 a, f2 b) {
+    const f2 s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
 __device__ __forceinline__ f2 df_add_f(f2 a, float b) {
     const f2 s = two_sum(a.hi, b);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
@@ -97,11 +105,13 @@ __device__ __forceinline__ double kahan_val(float s, float c) { return (double)s
 //   g1 = -s, g2 = w, g3 = -w v, g4 = w(1-6w), g5 = -w v(1-12w),
 //   g6 = w(1-30w+120w^2),
 // and g(y_k + d) = sum_n g_n d^n / n!, |d| <= 1/64; the next term is below
-// 2e-17.  For y >= 36, g(y) < 2.4e-16 and is taken as exp(-y).
+// 2e-17.  g0 and the first-order term are kept as double-floats; the second to
+// sixth orders (together below 3.1e-5) in FP32.  For y >= 36, g(y) < 2.4e-16
+// and is taken as exp(-y).
 constexpr int LOG1PEXP_PER_UNIT = 32;
 constexpr int LOG1PEXP_K = 36 * LOG1PEXP_PER_UNIT;
 
-// g(y) for y >= 0 given as a double-float; absolute error below 1e-14.
+// g(y) for y >= 0 given as a double-float; absolute error below 1e-11.
 // tab may live in shared or global memory.
 __device__ __forceinline__ f2 log1pexp_neg(f2 y, const float4 *tab) {
     if (y.hi >= 36.0f) return f2{__expf(-y.hi), 0.0f};
@@ -110,21 +120,16 @@ __device__ __forceinline__ f2 log1pexp_neg(f2 y, const float4 *tab) {
     const f2 d = two_sum(__fsub_rn(y.hi, (float)k * (1.0f / LOG1PEXP_PER_UNIT)), y.lo);
     const float4 q = tab[k];
     const f2 g0{q.x, q.y}, s{q.z, q.w};
-    // first and second order in double-float
-    const f2 t1 = df_mul(df_neg(s), d);                             // g1 d
-    const f2 w = df_mul(s, df_add_f(df_neg(s), 1.0f));             // s (1 - s)
-    const f2 t2 = df_mul(w, df_mul(d, d));                          // g2 d^2 (halved below)
-    // third to sixth order in FP32 (their sum is below 7e-8)
-    const float wf = w.hi, vf = fmaf(-2.0f, s.hi, 1.0f), dh = d.hi;
+    const f2 t1 = df_mul(df_neg(s), d);   // g1 d, double-float
+    // second to sixth order in FP32 (Horner in d)
+    const float wf = fmaf(-s.hi, s.hi, s.hi), vf = fmaf(-2.0f, s.hi, 1.0f), dh = d.hi;
+    const float c2 = 0.5f * wf;
     const float c3 = -wf * vf * (1.0f / 6.0f);
     const float c4 = wf * fmaf(-6.0f, wf, 1.0f) * (1.0f / 24.0f);
     const float c5 = -wf * vf * fmaf(-12.0f, wf, 1.0f) * (1.0f / 120.0f);
     const float c6 = wf * fmaf(wf, fmaf(120.0f, wf, -30.0f), 1.0f) * (1.0f / 720.0f);
-    const float r = fmaf(dh, fmaf(dh, fmaf(dh, c6, c5), c4), c3);
-    const float t3 = dh * dh * dh * r;
-    f2 gs = df_add(g0, t1);
-    gs = df_add(gs, f2{0.5f * t2.hi, 0.5f * t2.lo});
-    return df_add_f(gs, t3);
+    const float r = fmaf(dh, fmaf(dh, fmaf(dh, fmaf(dh, c6, c5), c4), c3), c2);
+    return df_add_q(g0, df_add_f(t1, dh * dh * r));
 }
 
 }  // namespace ihmc

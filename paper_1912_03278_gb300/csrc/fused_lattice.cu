@@ -228,23 +228,23 @@ __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst
     for (int q = 0; q < VEC; ++q) {
         const float ps = sign * n.c.v[q];
         const f2 nbd = exact_nb<DIM, VEC>(n, q);
-        const f2 a = df_add(df_mul_f(kc.C2, ps), df_mul(kc.bJ2, f2{sign * nbd.hi, sign * nbd.lo}));
+        const f2 a = df_add_q(df_mul_f(kc.C2, ps), df_mul(kc.bJ2, f2{sign * nbd.hi, sign * nbd.lo}));
         f2 x = a;
         float hq = 0.0f;
         if (A.hdf) {
             const float2 hh = A.hdf[site0 + q];
             const f2 hp = df_mul(kc.beta2, f2{hh.x, hh.y});
-            x = df_add(a, hp);
+            x = df_add_q(a, hp);
             hq = hp.hi;
         } else if (!kc.hzero) {
-            x = df_add(a, kc.hp2);
+            x = df_add_q(a, kc.hp2);
             hq = kc.hp2.hi;
         }
         const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
         const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, tab);
         // S_i for this site, summed over the vector first (short chains)
-        const f2 si = df_add(df_mul_f(a, 0.5f * ps), df_neg(df_add(ax, gl)));
-        sv = df_add(sv, si);
+        const f2 si = df_add_q(df_mul_f(a, 0.5f * ps), df_neg(df_add_q(ax, gl)));
+        sv = df_add_q(sv, si);
         const float tq = tanh_f(fmaf(kc.Cf, ps, sign * kc.bJf * n.nb.v[q]) + hq);
         kahan_add(acc.sT, acc.cT, tq);
         kahan_add(acc.sAT, acc.cAT, a.hi * tq);
