@@ -28,6 +28,13 @@ namespace ihmc {
 namespace {
 
 constexpr int NVMAX = 4;
+constexpr int RED_BYTES = 32 * 8 * 8 + 16;   // block reduction + broadcast words
+
+// Shared memory of a launch: the plane rings, optionally the log(1 + e^-y)
+// table, the reduction words.
+__host__ __device__ inline size_t ring_bytes(int P, int D) {
+    return (((size_t)(D + 4 + D + 2 + 3) * P + 3) & ~(size_t)3) * 4;
+}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -514,9 +521,18 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
     float *smem = reinterpret_cast<float *>(smem_f4);
     constexpr int R = D + 4, RP = D + 2;
     const Geometry &g = A.g;
-    const size_t ring_floats = ((size_t)(R + RP + 3) * g.P + 3) & ~(size_t)3;
-    float4 *tab = reinterpret_cast<float4 *>(smem + ring_floats);
-    double *red = reinterpret_cast<double *>(tab + LOG1PEXP_NODES);
+    static_assert(R + RP + 3 == 2 * D + 9, "ring layout");
+    const size_t rb = ring_bytes(g.P, D);
+    // The launch's shared-memory size says where the log(1 + e^-y) table
+    // lives: copied into shared memory when the host gave room for it (it
+    // does when that costs no resident CTAs), else read through L1 from
+    // global memory.
+    uint32_t dsm;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+    const bool tab_in_smem = dsm >= rb + LOG1PEXP_NODES * 16 + RED_BYTES;
+    float4 *tab_s = reinterpret_cast<float4 *>(smem + rb / 4);
+    const float4 *tab = tab_in_smem ? tab_s : A.lpe_tab;
+    double *red = reinterpret_cast<double *>(smem + rb / 4 + (tab_in_smem ? LOG1PEXP_NODES * 4 : 0));
     int *bcast = reinterpret_cast<int *>(red + 32 * 8);
 
     const int chain = A.chain0 + blockIdx.x;
@@ -530,8 +546,10 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
         momenta_sweep<VEC>(A, chain, A.traj0, sl);
         return;
     }
-    for (int i = threadIdx.x; i < LOG1PEXP_NODES; i += blockDim.x) tab[i] = A.lpe_tab[i];
-    __syncthreads();
+    if (tab_in_smem) {
+        for (int i = threadIdx.x; i < LOG1PEXP_NODES; i += blockDim.x) tab_s[i] = A.lpe_tab[i];
+        __syncthreads();
+    }
 
     if (A.mode == MODE_EVAL) {
         Acc acc = acc_zero();
@@ -650,9 +668,35 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
     }
 }
 
+// Shared-memory size of a launch: with the table if that leaves as many CTAs
+// resident per SM as without it (the occupancy calculator decides), else
+// without.  The last answers are cached per thread.
+template <class K>
+static int launch_smem(K kern, const Geometry &g, int D, int threads) {
+    struct Memo {
+        int P, D, threads, smem;
+    };
+    thread_local Memo memo[8] = {};
+    thread_local int next = 0;
+    for (const Memo &m : memo)
+        if (m.smem && m.P == g.P && m.D == D && m.threads == threads) return m.smem;
+    const int base = (int)(ring_bytes(g.P, D) + RED_BYTES);
+    const int with_tab = base + LOG1PEXP_NODES * 16;
+    int n_with = 0, n_without = 0;
+    int smem = base;
+    if (with_tab <= 227 * 1024 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n_with, kern, threads, with_tab) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n_without, kern, threads, base) == cudaSuccess &&
+        n_with >= n_without)
+        smem = with_tab;
+    cudaGetLastError();
+    memo[next] = Memo{g.P, D, threads, smem};
+    next = (next + 1) % 8;
+    return smem;
+}
+
 template <int DIM, int VEC, int D>
 cudaError_t kernel_node(const FusedArgs &a, int threads, cudaKernelNodeParams *np, void **args) {
-    const int smem = fused_lattice_smem_bytes(a.g, D, VEC);
     static bool configured = false;
     auto kern = fused_lattice_kernel<DIM, VEC, D>;
     if (!configured) {
@@ -661,6 +705,7 @@ cudaError_t kernel_node(const FusedArgs &a, int threads, cudaKernelNodeParams *n
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    const int smem = launch_smem(kern, a.g, D, threads);
     np->func = reinterpret_cast<void *>(kern);
     np->gridDim = dim3((unsigned)(a.n_chains - a.chain0), 1, 1);
     np->blockDim = dim3((unsigned)threads, 1, 1);
@@ -699,11 +744,10 @@ __global__ void log1pexp_selftest_kernel(const double *y, double *out, int64_t n
 
 }  // namespace
 
+// Least shared memory a launch needs (the table read from global memory).
 int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec) {
     (void)vec;
-    const size_t ring = (size_t)(depth + 4 + depth + 2 + 3) * g.P;
-    const size_t floats = ((ring + 3) & ~(size_t)3);
-    return (int)(floats * 4 + LOG1PEXP_NODES * 16 + 32 * 8 * 8 + 16);
+    return (int)(ring_bytes(g.P, depth) + RED_BYTES);
 }
 
 // Launch shape: VEC = 4 when rows split into float4s; threads = one per vector
