@@ -70,6 +70,26 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank):
+    """Seed of rank `rank`'s chains: replicas run independent Markov chains."""
+    return 1234 + 7919 * rank
+
+
+def job_rate(units_local, elapsed_local, ws, device=None):
+    """Whole-job throughput of `ws` replicas that each processed `units_local`
+    units in `elapsed_local` seconds: all units over the slowest rank's time
+    (max over ranks; no collective when ws == 1).  Returns (rate, max time)."""
+    elapsed = float(elapsed_local)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return units_local * ws / elapsed, elapsed
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -236,27 +256,45 @@ def tune_eps(sims, betas_per_chain, rounds, seed, therm=6):
     second-order integrator the mean energy violation grows as eps^4 and the
     acceptance is erfc(sqrt(<dH>)/2); each round estimates the acceptance per
     beta group from the smooth mean of min(1, exp(-dH)), converts it to an
-    effective <dH>, and rescales eps by (0.128 / <dH>)^(1/4) (0.128 gives 80%),
-    clamped to [1/2, 2]."""
+    effective <dH> and proposes eps * (0.128 / <dH>)^(1/4) (0.128 gives 80%),
+    clamped to [1/2, 2].  Each group keeps a bracket [lo, hi] of step sizes
+    measured above / below the target; a proposal outside it is replaced by
+    the bracket's geometric mean, so the steps do not jump across the
+    integrator's stability edge and back.  The group ends on the largest eps
+    measured at or above the target (the smallest tried if none was)."""
     from scipy.special import erfcinv
     target = 4.0 * erfcinv(TARGET_ACC) ** 2
     ub = np.unique(betas_per_chain)
     trace = {}
     for L, sim in sims.items():
         eps = np.full(len(betas_per_chain), EPS0.get(L, 0.05))
+        lo = {b: None for b in ub}
+        hi = {b: None for b in ub}
         sim.trajectories(therm, seed + 999)
         trace[str(L)] = []
         for r in range(rounds):
+            sim.set_eps(eps)
             sim.trajectories(1, seed + 1000 + r)
             dH = sim.records()[:, 0]
             pacc = np.minimum(1.0, np.exp(-np.clip(dH, -50, 50)))
             trace[str(L)].append(round(float(pacc.mean()), 3))
             for b in ub:
                 sel = betas_per_chain == b
+                e = float(eps[sel][0])
                 a = float(np.clip(pacc[sel].mean(), 1e-3, 1 - 1e-6))
+                if a >= TARGET_ACC:
+                    lo[b] = e if lo[b] is None else max(lo[b], e)
+                else:
+                    hi[b] = e if hi[b] is None else min(hi[b], e)
                 eff = 4.0 * erfcinv(a) ** 2
-                eps[sel] *= float(np.clip((target / eff) ** 0.25, 0.5, 2.0))
-            sim.set_eps(eps)
+                prop = e * float(np.clip((target / eff) ** 0.25, 0.5, 2.0))
+                if lo[b] is not None and hi[b] is not None and not lo[b] < prop < hi[b]:
+                    prop = math.sqrt(lo[b] * hi[b])
+                eps[sel] = prop
+        for b in ub:
+            sel = betas_per_chain == b
+            eps[sel] = lo[b] if lo[b] is not None else (hi[b] if hi[b] is not None else eps[sel][0])
+        sim.set_eps(eps)
         sim._eps = eps.copy()
         trace[str(L)].append([round(float(eps.min()), 4), round(float(eps.max()), 4)])
     return trace
@@ -281,7 +319,7 @@ def run_ours(args):
         sims[L] = pkg.IsingHMC(dim=2, L=(L, L), beta=betas, C=C, eps=EPS0.get(L, 0.02), n_md=N_MD,
                                n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
                                stream=stream.cuda_stream)
-    seed = 1234 + 7919 * rank
+    seed = replica_seed(rank)
     hot_start(pkg, sims, seed, C)
     tune_trace = tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
@@ -321,12 +359,8 @@ def run_ours(args):
     launches = sum(s.launches for s in sims.values()) - launches0
     big_ms = [a.elapsed_time(b) for a, b in ev]
     obs = {L: sims[L].observables() for L in Ls}
-    if ws > 1:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    site_steps = sum(L * L for L in Ls) * n_chains * N_MD * args.steps * ws
-    value = site_steps / elapsed
+    value, elapsed = job_rate(sum(L * L for L in Ls) * n_chains * N_MD * args.steps, elapsed, ws,
+                              device="cuda")
 
     # dominant kernel: one launch = one trajectory of all chains of the largest lattice
     alg_bytes = 16.0 * N_MD * big * big * n_chains
