@@ -40,7 +40,7 @@ METRIC = "leapfrog site-steps/s chosen vs plain form, same GPU; %roofline; serve
 UNIT = "site-steps/s"
 LS = (256, 1024)
 N_MD = 20
-EPS0 = {256: 0.05, 1024: 0.05}
+EPS0 = {256: 0.10, 1024: 0.05}   # tuner start: acceptance at fixed eps falls with N (<dH> ~ N eps^4)
 TARGET_ACC = 0.80
 
 
@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chains-per-beta", type=int, default=256)
     ap.add_argument("--L", type=str, default="256,1024")
-    ap.add_argument("--tune-rounds", type=int, default=8)
+    ap.add_argument("--tune-rounds", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -228,44 +228,67 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm ----
-def hot_start(pkg, sims, seed, C):
+def hot_start(pkg, sims, seed, betas, C, batch=256):
     """Start every chain from random spins s = +-1 dressed with the HS field's
-    conditional fluctuation: given s, phi = A psi ~ N(A s, A) (Sec. 2,
-    Eq. did_HS_trafo), i.e. psi = s + A^{-1/2} xi, taken as s + xi/sqrt(C).
-    Local fluctuations are then already typical, so step-size tuning sees
-    representative energy violations.  Generated on the device."""
+    exact conditional fluctuation: given s, phi = A psi ~ N(A s, A) (Sec. 2,
+    Eq. did_HS_trafo), i.e. psi = s + A^{-1/2} xi with xi ~ N(0, 1).  On the
+    periodic square lattice A = beta J K + C is circulant, so A^{-1/2} is
+    applied in Fourier space (eigenvalues C + 2 beta J (cos kx + cos ky)).
+    Set-up only (torch on the device, before any timed region)."""
     import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
+    betas = np.asarray(betas, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
     for L, sim in sims.items():
         n_chains = pkg.binding.load().ising_hmc_n_chains(sim.h)
-        n = n_chains * L * L
-        psi = torch.randint(0, 2, (n,), device="cuda", generator=g, dtype=torch.int8)
-        psi = psi.to(torch.float32).mul_(2.0).sub_(1.0)
-        scale = torch.tensor(1.0 / np.sqrt(C), dtype=torch.float32, device="cuda")
-        noise = torch.randn(n_chains, L * L, device="cuda", generator=g, dtype=torch.float32)
-        psi.view(n_chains, L * L).add_(noise.mul_(scale[:, None]))
-        del noise
+        k = torch.arange(L, device="cuda", dtype=torch.float64) * (2.0 * math.pi / L)
+        lam_k = 2.0 * (torch.cos(k)[:, None] + torch.cos(k[: L // 2 + 1])[None, :])
+        psi = torch.empty(n_chains, L, L, device="cuda", dtype=torch.float32)
+        for c0 in range(0, n_chains, batch):
+            c1 = min(n_chains, c0 + batch)
+            b = torch.tensor(betas[c0:c1], device="cuda")[:, None, None]
+            c = torch.tensor(C[c0:c1], device="cuda")[:, None, None]
+            xi = torch.randn(c1 - c0, L, L, device="cuda", generator=g, dtype=torch.float32)
+            f = torch.fft.rfft2(xi)
+            f *= (c + b * lam_k[None]).rsqrt().to(torch.float32)
+            spins = torch.randint(0, 2, (c1 - c0, L, L), device="cuda", generator=g,
+                                  dtype=torch.int8).to(torch.float32).mul_(2.0).sub_(1.0)
+            psi[c0:c1] = spins + torch.fft.irfft2(f, s=(L, L))
+            del xi, f, spins
         torch.cuda.synchronize()
         pkg.ising_hmc_set_state_native(sim.h, psi.data_ptr(), 0)
         del psi
 
 
-def tune_eps(sims, betas_per_chain, rounds, seed, therm=6):
+def tune_eps(sims, betas_per_chain, rounds, seed, therm=6, lo_acc=0.75, hi_acc=0.90, checks=8):
     """Step-size tuning during equilibration only (frozen afterwards).  For a
     second-order integrator the mean energy violation grows as eps^4 and the
-    acceptance is erfc(sqrt(<dH>)/2); each round estimates the acceptance per
-    beta group from the smooth mean of min(1, exp(-dH)), converts it to an
+    acceptance is erfc(sqrt(<dH>)/2).  Each round runs one trajectory at the
+    new step sizes to settle, then estimates the acceptance per beta group
+    from the mean of min(1, exp(-dH)) over two more, converts it to an
     effective <dH> and proposes eps * (0.128 / <dH>)^(1/4) (0.128 gives 80%),
-    clamped to [1/2, 2].  Each group keeps a bracket [lo, hi] of step sizes
-    measured above / below the target; a proposal outside it is replaced by
-    the bracket's geometric mean, so the steps do not jump across the
-    integrator's stability edge and back.  The group ends on the largest eps
-    measured at or above the target (the smallest tried if none was)."""
+    clamped to [0.85, 1] (the chains still relax while the tuner runs and
+    their acceptance drifts down, so early readings would push eps up; a
+    large step can also push chains into states they leave only slowly: the
+    action is not convex); a proposal outside the
+    group's bracket of step sizes measured above / below 80% is replaced by
+    the bracket's geometric mean.  Last, each group's step is nudged by 8%
+    until its measured acceptance lies in [lo_acc, hi_acc] on two checks in a
+    row (at most `checks`)."""
     from scipy.special import erfcinv
     target = 4.0 * erfcinv(TARGET_ACC) ** 2
     ub = np.unique(betas_per_chain)
     trace = {}
+
+    def measure(sim, s0, n=2):
+        acc = np.zeros(len(betas_per_chain))
+        for m in range(n):
+            sim.trajectories(1, s0 + m)
+            dH = sim.records()[:, 0]
+            acc += np.minimum(1.0, np.exp(-np.clip(dH, -50, 50)))
+        return acc / n
+
     for L, sim in sims.items():
         eps = np.full(len(betas_per_chain), EPS0.get(L, 0.05))
         lo = {b: None for b in ub}
@@ -274,9 +297,8 @@ def tune_eps(sims, betas_per_chain, rounds, seed, therm=6):
         trace[str(L)] = []
         for r in range(rounds):
             sim.set_eps(eps)
-            sim.trajectories(1, seed + 1000 + r)
-            dH = sim.records()[:, 0]
-            pacc = np.minimum(1.0, np.exp(-np.clip(dH, -50, 50)))
+            sim.trajectories(1, seed + 1000 + 10 * r)
+            pacc = measure(sim, seed + 1001 + 10 * r)
             trace[str(L)].append(round(float(pacc.mean()), 3))
             for b in ub:
                 sel = betas_per_chain == b
@@ -287,13 +309,32 @@ def tune_eps(sims, betas_per_chain, rounds, seed, therm=6):
                 else:
                     hi[b] = e if hi[b] is None else min(hi[b], e)
                 eff = 4.0 * erfcinv(a) ** 2
-                prop = e * float(np.clip((target / eff) ** 0.25, 0.5, 2.0))
+                prop = e * float(np.clip((target / eff) ** 0.25, 0.85, 1.0))
                 if lo[b] is not None and hi[b] is not None and not lo[b] < prop < hi[b]:
                     prop = math.sqrt(lo[b] * hi[b])
                 eps[sel] = prop
         for b in ub:
             sel = betas_per_chain == b
-            eps[sel] = lo[b] if lo[b] is not None else (hi[b] if hi[b] is not None else eps[sel][0])
+            eps[sel] = lo[b] if lo[b] is not None else 0.9 * hi[b]
+        in_band = 0
+        for k in range(checks):
+            sim.set_eps(eps)
+            sim.trajectories(1, seed + 2000 + 10 * k)
+            pacc = measure(sim, seed + 2001 + 10 * k)
+            trace[str(L)].append(round(float(pacc.mean()), 3))
+            done = True
+            for b in ub:
+                sel = betas_per_chain == b
+                a = float(pacc[sel].mean())
+                if a < lo_acc:
+                    eps[sel] *= 0.92
+                    done = False
+                elif a > hi_acc:
+                    eps[sel] *= 1.08
+                    done = False
+            in_band = in_band + 1 if done else 0
+            if in_band >= 2:
+                break
         sim.set_eps(eps)
         sim._eps = eps.copy()
         trace[str(L)].append([round(float(eps.min()), 4), round(float(eps.max()), 4)])
@@ -320,7 +361,7 @@ def run_ours(args):
                                n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
                                stream=stream.cuda_stream)
     seed = replica_seed(rank)
-    hot_start(pkg, sims, seed, C)
+    hot_start(pkg, sims, seed, betas, C)
     tune_trace = tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
         sims[L].reset_sums()
