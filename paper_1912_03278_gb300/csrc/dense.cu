@@ -485,6 +485,81 @@ static bool use_pair(int M, int N) { return M % 256 == 0 && N % 256 == 0; }
 static bool use_pair(int, int) { return false; }
 #endif
 
+// ------------------------------------------------- set-up of the dense form
+// y = J x in FP64 (Lanczos estimate of lambda_min at creation), one warp per row.
+__global__ void k_matvec_f64(const double *__restrict__ J, const double *__restrict__ x,
+                             double *__restrict__ y, int64_t N) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < N; r += nwarps) {
+        const double *row = J + r * N;
+        double acc = 0.0;
+        for (int64_t j = lane; j < N; j += 32) acc = fma(row[j], x[j], acc);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) y[r] = acc;
+    }
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float f) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// Per row i of the FP64 couplings (one CTA): the BF16 copy (round to nearest
+// even of the FP32 value) and either the ACT_DIGITS base-128 digit planes of
+// J_i. 2^-e_i, e_i = ilogb(max_j |J_ij|) + 2 (so every entry lies in
+// (-1/2, 1/2)), from X = round(J_ij 2^(42 - e_i)) taken from the FP64 bit
+// pattern with integer arithmetic, or the double-float pair (N > 4096).
+__global__ void __launch_bounds__(256) k_dense_prepare(const double *__restrict__ J, int64_t N,
+                                                       uint16_t *__restrict__ J16,
+                                                       uint16_t *__restrict__ dig,
+                                                       int *__restrict__ row_exp,
+                                                       float *__restrict__ Jhi,
+                                                       float *__restrict__ Jlo) {
+    __shared__ double red[8];
+    const int64_t i = blockIdx.x;
+    const double *row = J + i * N;
+    double mx = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) mx = fmax(mx, fabs(row[j]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    const int e = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (threadIdx.x == 0 && row_exp) row_exp[i] = e;
+    constexpr int FRAC = ACT_BITS * ACT_DIGITS;   // 42 fraction bits
+    const int64_t nn = N * N;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        const double x = row[j];
+        J16[i * N + j] = bf16_bits((float)x);
+        if (dig) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+            const int be = (int)((b >> 52) & 0x7FF);
+            long long X = 0;
+            if (be) {   // normal (subnormals lie far below the last digit)
+                const long long M = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+                const int sh = be - 1075 - e + FRAC;   // x 2^(FRAC-e) = M 2^sh, sh < -11
+                if (sh > -63) X = (M + (1ll << (-sh - 1))) >> (-sh);
+                if (b >> 63) X = -X;
+            }
+            // low digits in [-64, 63]; the top digit takes the rest, |rest| <= 64
+#pragma unroll
+            for (int t = ACT_DIGITS - 1; t >= 1; --t) {
+                const int q = (int)(((X + 64) & 127) - 64);
+                X = (X - q) >> ACT_BITS;
+                dig[(int64_t)t * nn + i * N + j] = bf16_bits((float)q);
+            }
+            dig[i * N + j] = bf16_bits((float)(int)X);
+        }
+        if (Jhi) {
+            const float hi = (float)x;
+            Jhi[i * N + j] = hi;
+            Jlo[i * N + j] = (float)(x - (double)hi);
+        }
+    }
+}
+
 // Cluster of cn CTAs; with pdl, programmatic dependent launch (the kernel
 // waits on the previous grid itself, after its set-up).
 static cudaLaunchConfig_t cluster_config(cudaLaunchAttribute *at, int cn, int grid, cudaStream_t s,
@@ -695,6 +770,19 @@ cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream
     const int64_t nel = (int64_t)d.b_pad * d.N;
     k_dense_momenta<<<grid_elems(nel / 4), 256, 0, s>>>(d.p, d.N, d.n_chains, d.b_pad, seed, traj);
     *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t dense_matvec_f64(const double *J, const double *x, double *y, int64_t N,
+                             cudaStream_t s) {
+    const int64_t blocks = (N + 7) / 8;   // 8 warps (rows) per block
+    k_matvec_f64<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(J, x, y, N);
+    return cudaGetLastError();
+}
+
+cudaError_t dense_prepare(const double *J, int64_t N, uint16_t *J16, uint16_t *dig, int *row_exp,
+                          float *Jhi, float *Jlo, cudaStream_t s) {
+    k_dense_prepare<<<(unsigned)N, 256, 0, s>>>(J, N, J16, dig, row_exp, Jhi, Jlo);
     return cudaGetLastError();
 }
 

@@ -135,6 +135,14 @@ struct DenseArgs {
 };
 
 cudaError_t dense_setup(DenseArgs &d);
+// y = J x in FP64 (Lanczos at creation).
+cudaError_t dense_matvec_f64(const double *J, const double *x, double *y, int64_t N,
+                             cudaStream_t s);
+// From FP64 couplings on the device: BF16 copy, and the action's digit planes
+// and row exponents (dig, row_exp) or its double-float pair (Jhi, Jlo); null
+// outputs are skipped.
+cudaError_t dense_prepare(const double *J, int64_t N, uint16_t *J16, uint16_t *dig, int *row_exp,
+                          float *Jhi, float *Jlo, cudaStream_t s);
 cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
                              int measure, cudaStream_t s, int64_t *launches);
 cudaError_t dense_eval(DenseArgs &d, cudaStream_t s, int64_t *launches);

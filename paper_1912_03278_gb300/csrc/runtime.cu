@@ -111,10 +111,34 @@ static void make_schedule(int integrator, int n_md, Schedule &s) {
 
 // Smallest eigenvalue of a dense symmetric matrix by Lanczos with full
 // reorthogonalisation (Lanczos 1950), then Sturm-sequence bisection on the
-// tridiagonal matrix.  Used only to validate the shift C (Sec. 2).
-static double lanczos_lambda_min(const double *J, int64_t N, int steps) {
+// tridiagonal matrix.  Used only to validate the shift C (Sec. 2).  The
+// products J q run on the device from dJ (the FP64 couplings already there)
+// when given, else on the host from J.
+static double lanczos_lambda_min(const double *J, const double *dJ, int64_t N, int steps) {
     steps = (int)std::min<int64_t>(steps, N);
     std::vector<double> Q((size_t)steps * N), w(N), alpha(steps), beta(steps);
+    double *dq = nullptr, *dw = nullptr;
+    if (dJ && (cudaMalloc(&dq, N * sizeof(double)) != cudaSuccess ||
+               cudaMalloc(&dw, N * sizeof(double)) != cudaSuccess)) {
+        cudaGetLastError();
+        dJ = nullptr;
+    }
+    auto matvec = [&](const double *q) {
+        if (dJ) {
+            if (cudaMemcpy(dq, q, N * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                dense_matvec_f64(dJ, dq, dw, N, 0) == cudaSuccess &&
+                cudaMemcpy(w.data(), dw, N * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess)
+                return;
+            cudaGetLastError();
+            dJ = nullptr;   // the host loop below takes over
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            double s = 0;
+            const double *row = J + i * N;
+            for (int64_t j = 0; j < N; ++j) s += row[j] * q[j];
+            w[i] = s;
+        }
+    };
     // deterministic start vector
     double nrm = 0;
     for (int64_t i = 0; i < N; ++i) {
@@ -126,12 +150,7 @@ static double lanczos_lambda_min(const double *J, int64_t N, int steps) {
     int k = 0;
     for (; k < steps; ++k) {
         const double *q = &Q[(size_t)k * N];
-        for (int64_t i = 0; i < N; ++i) {
-            double s = 0;
-            const double *row = J + i * N;
-            for (int64_t j = 0; j < N; ++j) s += row[j] * q[j];
-            w[i] = s;
-        }
+        matvec(q);
         double a = 0;
         for (int64_t i = 0; i < N; ++i) a += w[i] * q[i];
         alpha[k] = a;
@@ -178,6 +197,8 @@ static double lanczos_lambda_min(const double *J, int64_t N, int steps) {
         if (count_below(mid) >= 1) hi = mid;
         else lo = mid;
     }
+    if (dq) cudaFree(dq);
+    if (dw) cudaFree(dw);
     return 0.5 * (lo + hi);
 }
 
@@ -417,7 +438,19 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
                 if (cfg->J[i * N + j] != cfg->J[j * N + i])
                     return bail(fail(h, ISING_EINVAL, "J must be symmetric"));
         }
-        lam_min = lanczos_lambda_min(cfg->J, N, (int)std::min<int64_t>(N, 96));
+        // FP64 couplings on the device (the plain form keeps them, the BF16
+        // form derives its operands from them), also used by the Lanczos check
+        const size_t jb = (size_t)N * N * sizeof(double);
+        int dev0 = 0;
+        if (cudaGetDevice(&dev0) == cudaSuccess && cudaMalloc((void **)&h->d_J, jb) == cudaSuccess &&
+            cudaMemcpy(h->d_J, cfg->J, jb, cudaMemcpyHostToDevice) == cudaSuccess) {
+            h->bytes += (int64_t)jb;
+        } else {
+            cudaGetLastError();
+            if (h->d_J) cudaFree(h->d_J);
+            h->d_J = nullptr;
+        }
+        lam_min = lanczos_lambda_min(cfg->J, h->d_J, N, (int)std::min<int64_t>(N, 96));
     }
     h->params.resize(h->n_chains);
     for (int c = 0; c < h->n_chains; ++c) {
@@ -515,16 +548,9 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         if ((st = dalloc(h, &h->du32, bn * 4)) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->du16, bn * 2)) != ISING_OK) return bail(st);
         const bool act_tc = N <= ACT_MAX_N;
+        if (!h->d_J) return bail(fail(h, ISING_ECUDA, "coupling upload failed"));
         if ((st = dalloc(h, &h->dJ16, (size_t)N * N * 2)) != ISING_OK) return bail(st);
-        std::vector<uint16_t> j16((size_t)N * N);
-        for (size_t i = 0; i < (size_t)N * N; ++i) {
-            const float f = (float)cfg->J[i];
-            uint32_t b;
-            std::memcpy(&b, &f, 4);
-            j16[i] = (uint16_t)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);   // round to nearest even
-        }
-        if (cudaMemcpy(h->dJ16, j16.data(), j16.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemset(h->dpsi16, 0, bn * 2) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
+        if (cudaMemset(h->dpsi16, 0, bn * 2) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
             cudaMemset(h->du16, 0, bn * 2) != cudaSuccess || cudaMemset(h->psi[1], 0, bn * 4) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "dense upload failed"));
         if (act_tc) {
@@ -536,46 +562,24 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             if ((st = dalloc(h, &h->dchain_exp, (size_t)h->b_pad * sizeof(int))) != ISING_OK)
                 return bail(st);
             if ((st = dalloc(h, &h->dGint, bn * 8)) != ISING_OK) return bail(st);
-            std::vector<uint16_t> dig((size_t)ACT_DIGITS * nn);
-            std::vector<int> rexp((size_t)N);
-            for (int64_t i = 0; i < N; ++i) {
-                const double *row = cfg->J + i * N;
-                double mx = 0.0;
-                for (int64_t j = 0; j < N; ++j) mx = std::max(mx, std::fabs(row[j]));
-                const int e = mx > 0.0 ? std::ilogb(mx) + 2 : 0;   // max |J_i.| 2^-e < 1/2
-                rexp[i] = e;
-                for (int64_t j = 0; j < N; ++j) {
-                    double x = std::ldexp(row[j], -e);
-                    for (int s = 0; s < ACT_DIGITS; ++s) {
-                        x *= (double)(1 << ACT_BITS);
-                        const double q = std::nearbyint(x);
-                        x -= q;
-                        const float f = (float)q;   // |q| <= 64: exact in BF16
-                        uint32_t b;
-                        std::memcpy(&b, &f, 4);
-                        dig[(size_t)s * nn + (size_t)i * N + j] = (uint16_t)(b >> 16);
-                    }
-                }
-            }
-            if (cudaMemcpy(h->dJdig, dig.data(), dig.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(h->drow_exp, rexp.data(), rexp.size() * sizeof(int),
-                           cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemset(h->dpsidig, 0, (size_t)ACT_DIGITS * bn * 2) != cudaSuccess)
+            if (cudaMemset(h->dpsidig, 0, (size_t)ACT_DIGITS * bn * 2) != cudaSuccess)
                 return bail(fail(h, ISING_ECUDA, "dense upload failed"));
         } else {
             if ((st = dalloc(h, &h->dGhi, bn * 4)) != ISING_OK) return bail(st);
             if ((st = dalloc(h, &h->dGlo, bn * 4)) != ISING_OK) return bail(st);
             if ((st = dalloc(h, &h->dJhi, (size_t)N * N * 4)) != ISING_OK) return bail(st);
             if ((st = dalloc(h, &h->dJlo, (size_t)N * N * 4)) != ISING_OK) return bail(st);
-            std::vector<float> jhi((size_t)N * N), jlo((size_t)N * N);
-            for (size_t i = 0; i < (size_t)N * N; ++i) {
-                jhi[i] = (float)cfg->J[i];
-                jlo[i] = (float)(cfg->J[i] - (double)jhi[i]);
-            }
-            if (cudaMemcpy(h->dJhi, jhi.data(), jhi.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(h->dJlo, jlo.data(), jlo.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-                return bail(fail(h, ISING_ECUDA, "dense upload failed"));
         }
+        // BF16 copy and the action's operands, derived on the device; the FP64
+        // couplings are not needed afterwards
+        if (dense_prepare(h->d_J, N, (uint16_t *)h->dJ16, (uint16_t *)h->dJdig, (int *)h->drow_exp,
+                          (float *)h->dJhi, (float *)h->dJlo, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return bail(fail(h, ISING_ECUDA, "dense set-up failed: %s",
+                             cudaGetErrorString(cudaGetLastError())));
+        cudaFree(h->d_J);
+        h->d_J = nullptr;
+        h->bytes -= (int64_t)N * N * (int64_t)sizeof(double);
         DenseArgs &d = h->dense;
         d.J16 = (const __nv_bfloat16 *)h->dJ16;
         d.Jhi = (const float *)h->dJhi;
@@ -605,10 +609,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         if (dense_setup(d) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "tensor map setup failed"));
     } else if (h->kind == ISING_KIND_DENSE) {
-        if ((st = dalloc(h, &h->d_J, (size_t)N * N * sizeof(double))) != ISING_OK) return bail(st);
-        if (cudaMemcpy(h->d_J, cfg->J, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-            return bail(fail(h, ISING_ECUDA, "coupling upload failed"));
+        if (!h->d_J) return bail(fail(h, ISING_ECUDA, "coupling upload failed"));
     }
     // zero state, psi = 0
     std::vector<ChainState> hs(h->n_chains);
