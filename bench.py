@@ -614,27 +614,62 @@ def mixed_3d_rate(pkg, steps=4, seed=31):
             s.close()
 
 
-def serve_requests(rng, n, scale):
-    """Requests drawn as in the serving workload: 2D L in [32,1024] or 3D L in
-    [16,64], beta in [0.15,0.6], h in [0,0.2], 100-5000 trajectories (times
-    `scale`, at least 1), 1-256 chains; N_md = floor(ln N), eps = 1/(N_md
-    sqrt(beta)), C = 2d beta + 0.1.  Dense requests are not drawn."""
+_DENSE_POOL = {}
+
+
+def dense_model(n):
+    """SK couplings of size n for serving requests (a small pool of models, as
+    a service would host; generated once) and |lambda_min|."""
+    if n not in _DENSE_POOL:
+        J = workloads.dense_couplings(n, seed=100 + n)
+        try:
+            from scipy.sparse.linalg import eigsh
+            lam = float(eigsh(J, k=1, which="SA", return_eigenvectors=False)[0])
+        except Exception:
+            lam = float(np.linalg.eigvalsh(J)[0])
+        _DENSE_POOL[n] = (J, abs(lam))
+    return _DENSE_POOL[n]
+
+
+DENSE_SIZES = (512, 1024, 1536, 2048, 3072, 4096)
+
+
+def serve_requests(rng, n, scale, dense_share=0.1):
+    """Requests drawn as in the serving workload: 2D L in [32,1024], 3D L in
+    [16,64] or (with probability `dense_share`) dense SK couplings N in
+    [512,4096] (BF16 tensor-core form, N from a pool of six sizes), beta in
+    [0.15,0.6], h in [0,0.2], 100-5000 trajectories (times `scale`, at least
+    1), 1-256 chains; N_md = floor(ln N), eps = 1/(N_md sqrt(beta)), C = 2d beta
+    + 0.1 (lattices) or beta |lambda_min(J)| + 0.1 (dense)."""
     out = []
     for _ in range(n):
+        beta = float(rng.uniform(0.15, 0.6))
+        chains = int(rng.integers(1, 257))
+        traj = max(1, int(round(int(rng.integers(100, 5001)) * scale)))
+        h0 = float(rng.uniform(0, 0.2))
+        seed = int(rng.integers(1, 2 ** 31))
+        if rng.random() < dense_share:
+            N = int(DENSE_SIZES[int(rng.integers(0, len(DENSE_SIZES)))])
+            J, lam = dense_model(N)
+            n_md = workloads.n_md_default(N)
+            out.append(dict(n_traj=traj, seed=seed, kind="dense", J=J, beta=beta, h=h0,
+                            C=beta * lam + 0.1, eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md,
+                            n_chains=chains, precision=2))   # ISING_PREC_BF16
+            continue
         dim = 2 if rng.random() < 0.5 else 3
         L = int(rng.integers(32, 1025)) if dim == 2 else int(rng.integers(16, 65))
         if dim == 3 and L % 4:
             L += 4 - L % 4   # keep the vector path; the scalar path serves any L
         N = L ** dim
-        beta = float(rng.uniform(0.15, 0.6))
         n_md = workloads.n_md_default(N)
-        chains = int(rng.integers(1, 257))
-        traj = max(1, int(round(int(rng.integers(100, 5001)) * scale)))
-        out.append(dict(n_traj=traj, seed=int(rng.integers(1, 2 ** 31)), dim=dim,
-                        L=(L,) * dim, beta=beta, h=float(rng.uniform(0, 0.2)),
+        out.append(dict(n_traj=traj, seed=seed, dim=dim, L=(L,) * dim, beta=beta, h=h0,
                         C=2 * dim * beta + 0.1, eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md,
                         n_chains=chains))
     return out
+
+
+def request_sites(r):
+    return r["J"].shape[0] if r.get("kind") == "dense" else int(np.prod(r["L"]))
 
 
 def serve_run(pkg, seconds, rate=200.0, rho=0.8, seed=2, budget_gb=120.0):
@@ -642,7 +677,7 @@ def serve_run(pkg, seconds, rate=200.0, rho=0.8, seed=2, budget_gb=120.0):
     Poisson arrivals at `rate` requests/s for `seconds`, with trajectory counts
     scaled so the offered load is `rho` of that capacity; p50/p99 latency."""
     rng = np.random.default_rng(seed)
-    work = lambda r: (np.prod(r["L"]) * r["n_chains"] * r["n_traj"] * r["n_md"])
+    work = lambda r: (request_sites(r) * r["n_chains"] * r["n_traj"] * r["n_md"])
     # mean work of an unscaled request, from a large sample
     mean_w = float(np.mean([work(r) for r in serve_requests(np.random.default_rng(7), 4000, 1.0)]))
     srv = pkg.IsingServer(int(budget_gb * 1e9), 4)
@@ -685,7 +720,7 @@ def serve_run(pkg, seconds, rate=200.0, rho=0.8, seed=2, budget_gb=120.0):
             "site_steps_per_s": done_work / t_all, "capacity_site_steps_per_s": cap,
             "trajectory_scale": scale, "queued_at_end_of_arrivals": int(peak_queue),
             "shared_graph_launches": int(st["group_launches"]), "quanta": int(st["quanta"]),
-            "dense_requests": "not drawn (no dense tensor-core path yet)"}
+            "dense_requests": int(sum(1 for r in reqs if r.get("kind") == "dense"))}
 
 
 def e2e_rate(pkg, sims, Ls, n_chains, seed, stream, steps=3):

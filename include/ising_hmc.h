@@ -238,12 +238,13 @@ void *ising_group_stream(const ising_group_t *g);           /* cudaStream_t of t
 const char *ising_group_last_error(const ising_group_t *g);
 void ising_group_destroy(ising_group_t *g);
 
-/* Serving: a continuous-batching request loop.  A server owns a worker thread
- * on the current device.  Requests (a configuration as for ising_hmc_create,
- * a number of trajectories and a seed) are queued from any host thread and
- * admitted in arrival order while their device memory
- * (ising_hmc_estimate_bytes) fits the budget; their state stays resident
- * until they finish.  Each quantum advances every active request by the same
+/* Serving: a continuous-batching request loop.  A server owns an admission
+ * thread and a worker thread on the current device.  Requests (a
+ * configuration as for ising_hmc_create, a number of trajectories and a seed)
+ * are queued from any host thread and admitted in arrival order while their
+ * device memory (ising_hmc_estimate_bytes) fits the budget; their handles are
+ * created on the admission thread while the worker keeps the device busy, and
+ * their state stays resident until they finish.  Each quantum advances every active request by the same
  * number of trajectories (at most quantum_traj): all FP32 lattice requests in
  * one CUDA-graph launch, others on their own streams.  Finished requests keep
  * their observables and latency and free their memory for waiting ones.  A

@@ -1,11 +1,13 @@
 // serve.cu -- continuous-batching request loop for HMC ensemble jobs.
 //
-// A server owns a worker thread.  Requests (a model configuration, a number of
-// trajectories, a seed) are queued from any host thread; the worker admits
-// them in arrival order while their device memory fits the budget, keeps
-// their state resident (one simulation handle per request), and advances all
-// active FP32 lattice requests together by one CUDA-graph launch per quantum
-// (other requests on their own streams, overlapping on the device).  A request
+// A server owns two threads.  Requests (a model configuration, a number of
+// trajectories, a seed) are queued from any host thread; the admission thread
+// takes them in arrival order while their device memory fits the budget and
+// creates their handles (host set-up and uploads) while the worker keeps the
+// device busy; the worker keeps every admitted request's state resident (one
+// simulation handle per request) and advances all active FP32 lattice
+// requests together by one CUDA-graph launch per quantum (other requests on
+// their own streams, overlapping on the device).  A request
 // leaves the batch when its trajectories are done: its observables are kept,
 // its handle destroyed, and waiting requests are admitted into the freed
 // memory before the next quantum.  Results of a request do not depend on the
@@ -56,13 +58,14 @@ struct ising_server {
     int quantum = 1;
     int device = 0;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_admit, cv_work, cv_done;
     std::deque<int64_t> queue;
     std::map<int64_t, Request> req;
+    std::vector<int64_t> ready;    // handle created, joins the batch at the next quantum
     std::vector<int64_t> active;
     int64_t next_id = 1;
     bool stop = false;
-    std::thread worker;
+    std::thread admitter, worker;
     // statistics
     int64_t admitted = 0, completed = 0, rejected = 0, group_launches = 0, quanta = 0;
     double site_steps = 0.0;
@@ -99,61 +102,72 @@ static void copy_cfg(Request &r, const ising_hmc_config *c) {
     r.cfg.h0_chain = cp(r.h0_c, c->h0_chain, c->n_chains);
 }
 
-// Worker: admit, advance one quantum, retire.  Holds the lock only for queue
-// bookkeeping, never across device work.
+// Admission: in arrival order while the budget allows; a request larger than
+// the whole budget is rejected.  Handle creation runs outside the lock.
+static void admit_loop(ising_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_admit.wait(lk, [&] {
+                if (s->stop) return true;
+                if (s->queue.empty()) return false;
+                const Request &q = s->req[s->queue.front()];
+                return q.bytes > s->budget || s->in_use + q.bytes <= s->budget;
+            });
+            if (s->stop) break;
+            Request &q = s->req[s->queue.front()];
+            s->queue.pop_front();
+            if (q.bytes > s->budget) {  // can never fit
+                q.state = 3;
+                q.status = ISING_ENOMEM;
+                q.t_done = clk::now();
+                s->rejected += 1;
+                s->cv_done.notify_all();
+                continue;
+            }
+            s->in_use += q.bytes;
+            s->admitting += 1;
+            r = &q;
+        }
+        ising_hmc_t *sim = nullptr;
+        const ising_status st = ising_hmc_create(&r->cfg, &sim);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->admitting -= 1;
+        if (st != ISING_OK) {
+            r->state = 3;
+            r->status = st;
+            r->t_done = clk::now();
+            s->in_use -= r->bytes;
+            s->rejected += 1;
+            s->cv_done.notify_all();
+            continue;
+        }
+        r->sim = sim;
+        r->state = 1;
+        r->t_admit = clk::now();
+        r->target = ising_hmc_traj_index(sim) + r->n_traj;
+        s->ready.push_back(r->id);
+        s->admitted += 1;
+        s->cv_work.notify_one();
+    }
+}
+
+// Worker: take in the newly admitted requests, advance one quantum, retire.
+// Holds the lock only for bookkeeping, never across device work.
 static void worker_loop(ising_server *s) {
     cudaSetDevice(s->device);
     ising_group_t *grp = nullptr;
     std::vector<int64_t> grp_members;
     for (;;) {
-        std::vector<Request *> to_admit;
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] {
-                return s->stop || !s->queue.empty() || !s->active.empty();
-            });
-            if (s->stop) break;
-            // admission in arrival order while the memory budget allows
-            while (!s->queue.empty()) {
-                Request &r = s->req[s->queue.front()];
-                if (r.bytes > s->budget) {  // can never fit
-                    r.state = 3;
-                    r.status = ISING_ENOMEM;
-                    r.t_done = clk::now();
-                    s->rejected += 1;
-                    s->queue.pop_front();
-                    s->cv_done.notify_all();
-                    continue;
-                }
-                if (s->in_use + r.bytes > s->budget) break;
-                s->in_use += r.bytes;
-                s->queue.pop_front();
-                s->admitting += 1;
-                to_admit.push_back(&r);
-            }
-        }
-        for (Request *r : to_admit) {
-            ising_status st = ising_hmc_create(&r->cfg, &r->sim);
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->admitting -= 1;
-            if (st != ISING_OK) {
-                r->state = 3;
-                r->status = st;
-                r->t_done = clk::now();
-                s->in_use -= r->bytes;
-                s->rejected += 1;
-                s->cv_done.notify_all();
-                continue;
-            }
-            r->state = 1;
-            r->t_admit = clk::now();
-            r->target = ising_hmc_traj_index(r->sim) + r->n_traj;
-            s->active.push_back(r->id);
-            s->admitted += 1;
-        }
         std::vector<Request *> act;
         {
-            std::lock_guard<std::mutex> lk(s->mu);
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] { return s->stop || !s->ready.empty() || !s->active.empty(); });
+            if (s->stop) break;
+            s->active.insert(s->active.end(), s->ready.begin(), s->ready.end());
+            s->ready.clear();
             for (int64_t id : s->active) act.push_back(&s->req[id]);
         }
         if (act.empty()) continue;
@@ -229,6 +243,7 @@ static void worker_loop(ising_server *s) {
                 s->completed += 1;
                 s->active.erase(std::find(s->active.begin(), s->active.end(), r->id));
                 s->cv_done.notify_all();
+                s->cv_admit.notify_one();   // memory freed
             }
         }
     }
@@ -247,6 +262,7 @@ ising_status ising_server_create(int64_t budget_bytes, int quantum_traj, ising_s
     s->quantum = quantum_traj;
     cudaGetDevice(&s->device);
     s->t0 = clk::now();
+    s->admitter = std::thread(admit_loop, s);
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return ISING_OK;
@@ -269,7 +285,7 @@ ising_status ising_server_submit(ising_server_t *s, const ising_hmc_config *cfg,
     r.t_submit = clk::now();
     s->queue.push_back(id);
     *request_id = id;
-    s->cv_work.notify_one();
+    s->cv_admit.notify_one();
     return ISING_OK;
 }
 
@@ -307,7 +323,7 @@ ising_status ising_server_drain(ising_server_t *s, double timeout_s) {
     const bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
                                         [&] {
                                             return s->queue.empty() && s->admitting == 0 &&
-                                                   s->active.empty();
+                                                   s->ready.empty() && s->active.empty();
                                         });
     return ok ? ISING_OK : sfail(s, ISING_ETIMEOUT, "drain: work remains");
 }
@@ -319,7 +335,7 @@ ising_status ising_server_stats(ising_server_t *s, double *out /* ISING_SERVER_N
     out[1] = (double)s->completed;
     out[2] = (double)s->rejected;
     out[3] = (double)s->queue.size();
-    out[4] = (double)s->active.size();
+    out[4] = (double)(s->active.size() + s->ready.size());
     out[5] = (double)s->in_use;
     out[6] = s->site_steps;
     out[7] = (double)s->group_launches;
@@ -336,7 +352,9 @@ void ising_server_destroy(ising_server_t *s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
     }
+    s->cv_admit.notify_all();
     s->cv_work.notify_all();
+    if (s->admitter.joinable()) s->admitter.join();
     if (s->worker.joinable()) s->worker.join();
     for (auto &kv : s->req)
         if (kv.second.sim) ising_hmc_destroy(kv.second.sim);

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import paper_1912_03278_gb300 as pkg
+import workloads
 from paper_1912_03278_gb300 import binding
 
 pytestmark = pytest.mark.gpu
@@ -28,6 +29,10 @@ REQ = [
          flip_every=4),
     dict(n_traj=5, seed=15, dim=2, L=(8, 8), beta=0.44, eps=0.1, n_md=10, n_chains=1,
          precision=pkg.ISING_PREC_PLAIN_FP64),
+    # dense couplings on the tensor cores (served by its own launches)
+    dict(n_traj=6, seed=16, kind="dense", J=workloads.dense_couplings(256, seed=5), beta=0.5,
+         C=0.5 * 2.2 + 0.1, h=0.05, eps=0.05, n_md=4, n_chains=130,
+         precision=pkg.ISING_PREC_BF16),
 ]
 
 
