@@ -30,10 +30,17 @@ namespace {
 constexpr int NVMAX = 4;
 constexpr int RED_BYTES = 32 * 8 * 8 + 16;   // block reduction + broadcast words
 
-// Shared memory of a launch: the plane rings, optionally the log(1 + e^-y)
-// table, the reduction words.
+// F(z) trails u by LAG planes: with LAG = 1 a plane's force reads only u
+// planes finished in earlier iterations, so one barrier per plane suffices.
+#ifndef IHMC_FL_LAG
+#define IHMC_FL_LAG 1
+#endif
+constexpr int LAG = IHMC_FL_LAG;
+
+// Shared memory of a launch: the plane rings (psi D+4+LAG, p D+2+LAG, u
+// 3+LAG slots), optionally the log(1 + e^-y) table, the reduction words.
 __host__ __device__ inline size_t ring_bytes(int P, int D) {
-    return (((size_t)(D + 4 + D + 2 + 3) * P + 3) & ~(size_t)3) * 4;
+    return (((size_t)(2 * D + 9 + 3 * LAG) * P + 3) & ~(size_t)3) * 4;
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -296,8 +303,9 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 template <int DIM, int VEC, int D, bool FIRST, bool LAST>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
                          const Slots &sl, float *smem, const float4 *tab, Acc &acc) {
-    constexpr int R = D + 4;   // psi ring slots
-    constexpr int RP = D + 2;  // p ring slots
+    constexpr int R = D + 4 + LAG;   // psi ring slots
+    constexpr int RP = D + 2 + LAG;  // p ring slots
+    constexpr int RU = 3 + LAG;      // u ring slots
     const Geometry &g = A.g;
     const int P = g.P;
     float *psi_ring = smem;
@@ -338,7 +346,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     };
     // ring slot of psi plane z (z >= -2) and u plane z (z >= -1)
     auto psi_slot = [&](int z) -> const float * { return psi_ring + (unsigned)(z + 2) % R * P; };
-    auto u_slot = [&](int z) -> float * { return u_ring + (unsigned)(z + 3) % 3 * P; };
+    auto u_slot = [&](int z) -> float * { return u_ring + (unsigned)(z + 4) % RU * P; };
 
     for (int s = 0; s <= D + 2; ++s) issue(s);
     int s_next = D + 3;
@@ -347,12 +355,12 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     ActConst kc;
     if constexpr (LAST) kc = act_const(prm);
 
-    for (int it = -1; it <= nz; ++it) {
+    for (int it = -1; it <= nz + LAG; ++it) {
         cp_wait<D>();
         __syncthreads();
         issue(s_next++);
         // ---- u(it) = tanh(A psi + h') - psi on plane it ----
-        {
+        if (it <= nz) {
             const float *pm = psi_slot(it - 1), *pcen = psi_slot(it), *pq = psi_slot(it + 1);
             float *uo = u_slot(it);
             const int zw = it < 0 ? it + nz : (it >= nz ? it - nz : it);
@@ -387,9 +395,9 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 }
             }
         }
-        __syncthreads();
-        // ---- F(z) = A u, kick and drift on plane z = it - 1 ----
-        const int z = it - 1;
+        if constexpr (LAG == 0) __syncthreads();
+        // ---- F(z) = A u, kick and drift on plane z = it - 1 - LAG ----
+        const int z = it - 1 - LAG;
         if (z >= 0 && z < nz) {
             const float *um = u_slot(z - 1), *uc = u_slot(z), *uq = u_slot(z + 1);
             const float *psz = psi_slot(z);
@@ -519,9 +527,9 @@ template <int DIM, int VEC, int D>
 __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Schedule S) {
     extern __shared__ float4 smem_f4[];
     float *smem = reinterpret_cast<float *>(smem_f4);
-    constexpr int R = D + 4, RP = D + 2;
+    constexpr int R = D + 4 + LAG, RP = D + 2 + LAG;
     const Geometry &g = A.g;
-    static_assert(R + RP + 3 == 2 * D + 9, "ring layout");
+    static_assert(R + RP + 3 + LAG == 2 * D + 9 + 3 * LAG, "ring layout");
     const size_t rb = ring_bytes(g.P, D);
     // The launch's shared-memory size says where the log(1 + e^-y) table
     // lives: copied into shared memory when the host gave room for it (it
