@@ -238,6 +238,8 @@ __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst
         su[0] = w.x; su[1] = w.y; su[2] = w.z; su[3] = w.w;
     }
     f2 sv{0.0f, 0.0f};
+    float vT = 0.0f, vAT = 0.0f, vHT = 0.0f;   // estimator sums over the vector
+    const bool has_h = A.hdf || !kc.hzero;
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
         const float ps = sign * n.c.v[q];
@@ -260,9 +262,9 @@ __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst
         const f2 si = df_add_q(df_mul_f(a, 0.5f * ps), df_neg(df_add_q(ax, gl)));
         sv = df_add_q(sv, si);
         const float tq = tanh_f(fmaf(kc.Cf, ps, sign * kc.bJf * n.nb.v[q]) + hq);
-        kahan_add(acc.sT, acc.cT, tq);
-        kahan_add(acc.sAT, acc.cAT, a.hi * tq);
-        kahan_add(acc.sHT, acc.cHT, hq * tq);
+        vT += tq;
+        vAT = fmaf(a.hi, tq, vAT);
+        if (has_h) vHT = fmaf(hq, tq, vHT);
         float uu;
         if constexpr (VEC == 4) {
             uu = su[q];
@@ -275,6 +277,9 @@ __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst
         acc.sS += (uu < (1.0f + tq) * 0.5f) ? 1 : -1;
     }
     acc_add(acc.S, acc.Slo, sv);
+    kahan_add(acc.sT, acc.cT, vT);
+    kahan_add(acc.sAT, acc.cAT, vAT);
+    if (has_h) kahan_add(acc.sHT, acc.cHT, vHT);
 }
 
 // FP32 momenta of the VEC sites site0.. (Sec. 3 momentum refresh): the same
