@@ -489,30 +489,16 @@ def plain_rate(pkg, L, betas, C, tuned, stream):
         sim.close()
 
 
-def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10):
-    """Dense all-to-all couplings: SK model N = 4096, J_ij ~ N(0, 1/N) symmetric
-    with J_ii = 0, h_i ~ N(0, 0.1^2), beta = 0.5, C = beta |lambda_min(J)| + 0.1,
-    1024 chains, BF16 tensor-core force with FP32 state, FP64-accurate action
-    (exact digit-sliced tensor-core product), N_md = 10, eps tuned towards 80%
-    acceptance.  Times whole trajectories and, separately, force evaluations
-    (two 4096 x 4096 x 1024 GEMMs each), both with CUDA events on the
-    handle's stream."""
+def _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, prec, stream, steps, seed, tune_rounds, n_force):
+    """Tune eps towards ~85% acceptance, then time `steps` trajectories and,
+    separately, `n_force` force evaluations with CUDA events on the stream."""
     import torch
-    N, B, beta = 4096, 1024, 0.5
-    J = workloads.dense_couplings(N, seed=1)
-    hv = workloads.dense_fields(N, 0.1, seed=2)
-    try:
-        from scipy.sparse.linalg import eigsh
-        lam = float(eigsh(J, k=1, which="SA", return_eigenvectors=False)[0])
-    except Exception:
-        lam = float(np.linalg.eigvalsh(J)[0])
-    C = beta * abs(lam) + 0.1
     sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=0.05, n_md=n_md, n_chains=B,
-                       precision=pkg.ISING_PREC_BF16, stream=stream.cuda_stream)
+                       precision=prec, stream=stream.cuda_stream)
     try:
         eps = 0.05
         trace = []
-        sim.trajectories(4, seed)   # leave psi = 0
+        sim.trajectories(4, seed)
         for _ in range(tune_rounds):
             sim.trajectories(2, seed)
             acc = float(sim.records()[:, 2].mean())
@@ -541,22 +527,59 @@ def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10
         ms_force = f0.elapsed_time(f1) / n_force
     finally:
         sim.close()
+    return dict(ms_traj=ms_traj, launches=launches, acc=obs["acceptance"], eps=eps, trace=trace,
+                ms_force=ms_force)
+
+
+def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10):
+    """Dense all-to-all couplings: SK model N = 4096, J_ij ~ N(0, 1/N) symmetric
+    with J_ii = 0, h_i ~ N(0, 0.1^2), beta = 0.5, C = beta |lambda_min(J)| + 0.1,
+    1024 chains, BF16 tensor-core force with FP32 state, FP64-accurate action
+    (exact digit-sliced tensor-core product), N_md = 10, eps tuned towards 85%
+    acceptance.  Times whole trajectories and, separately, force evaluations
+    (two 4096 x 4096 x 1024 GEMMs each), both with CUDA events on the
+    handle's stream.  The FP8 (E4M3) force variant is measured the same way
+    (key `fp8`, its own tuned eps)."""
+    import torch
+    N, B, beta = 4096, 1024, 0.5
+    J = workloads.dense_couplings(N, seed=1)
+    hv = workloads.dense_fields(N, 0.1, seed=2)
+    try:
+        from scipy.sparse.linalg import eigsh
+        lam = float(eigsh(J, k=1, which="SA", return_eigenvectors=False)[0])
+    except Exception:
+        lam = float(np.linalg.eigvalsh(J)[0])
+    C = beta * abs(lam) + 0.1
+    r = _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, pkg.ISING_PREC_BF16, stream, steps, seed,
+                         tune_rounds, n_force)
     flops_force = 2 * 2.0 * N * N * B
-    tf = flops_force / (ms_force * 1e-3) / 1e12
     peaks = measured_peaks_all()
     peak = peaks.get("bf16_tflops") or 1900.0
+    src = "measured bf16 burst (MEASURED_PEAKS.json)" if peaks.get("bf16_tflops") else "fallback"
+    tf = flops_force / (r["ms_force"] * 1e-3) / 1e12
     out = {"workload": "dense SK couplings N=%d, J~N(0,1/N), h~N(0,0.01), beta=%g, "
                        "C=beta|lambda_min|+0.1=%.4f, %d chains, N_md=%d, eps tuned"
                        % (N, beta, C, B, n_md),
-           "value": N * B * n_md / (ms_traj * 1e-3), "unit": UNIT, "ms_per_trajectory": ms_traj,
-           "acceptance": obs["acceptance"], "eps": eps, "tuning": trace,
-           "gpu_launches_per_trajectory": launches / steps,
-           "fixed_ms_per_trajectory": ms_traj - (n_md + 1) * ms_force,
+           "value": N * B * n_md / (r["ms_traj"] * 1e-3), "unit": UNIT,
+           "ms_per_trajectory": r["ms_traj"], "acceptance": r["acc"], "eps": r["eps"],
+           "tuning": r["trace"], "gpu_launches_per_trajectory": r["launches"] / steps,
+           "fixed_ms_per_trajectory": r["ms_traj"] - (n_md + 1) * r["ms_force"],
            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
-                        "frac": tf / peak, "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"
-                        if peaks.get("bf16_tflops") else "fallback",
+                        "frac": tf / peak, "peak_source": src,
                         "kernel": "force1_kernel + force2_kernel (one force evaluation)",
-                        "algorithmic_flops_per_force": flops_force, "ms_per_force": ms_force}}
+                        "algorithmic_flops_per_force": flops_force, "ms_per_force": r["ms_force"]}}
+    r8 = _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, pkg.ISING_PREC_FP8, stream, steps, seed,
+                          tune_rounds, n_force)
+    tf8 = flops_force / (r8["ms_force"] * 1e-3) / 1e12
+    out["fp8"] = {"value": N * B * n_md / (r8["ms_traj"] * 1e-3), "unit": UNIT,
+                  "ms_per_trajectory": r8["ms_traj"], "acceptance": r8["acc"], "eps": r8["eps"],
+                  "tuning": r8["trace"],
+                  "roofline": {"bound": "tensor", "achieved": tf8, "peak": 2.0 * peak,
+                               "unit": "TFLOP/s", "frac": tf8 / (2.0 * peak),
+                               "peak_source": "measured bf16 burst x 2 (nominal FP8:BF16 ratio)",
+                               "kernel": "force1_kernel + force2_kernel, E4M3 operands",
+                               "ms_per_force": r8["ms_force"]}}
+    eps = r["eps"]
     # plain one-chain-per-launch FP64 form on a few chains of the same model
     try:
         k = 2

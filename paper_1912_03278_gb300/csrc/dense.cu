@@ -12,6 +12,7 @@
 // estimators, dH and the Metropolis test (Sec. 3).
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "df32.cuh"
@@ -59,13 +60,32 @@ __device__ __forceinline__ float4 chain_coef(const ChainParams *params, int n0, 
                         : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// u = tanh(beta G + C psi + h') - psi  ->  U (FP32 and BF16).  One load per
-// element, so 32 columns per chunk keep enough reads in flight.
+// Low-precision GEMM operands: BF16, or FP8 E4M3 holding x / FP8_OP_SCALE
+// (a fixed scale, so the force stays a function of psi alone and the
+// integrator reversible; values beyond +-FP8_OP_RANGE saturate).  With FP8 the
+// accumulator of row m is scaled by the row's J scale times FP8_OP_SCALE.
+template <bool FP8>
+struct Low {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
+};
+template <>
+struct Low<true> {
+    using T = uint8_t;
+    static __device__ __forceinline__ T from(float x) {
+        return (T)__nv_cvt_float_to_fp8(x * (1.0f / FP8_OP_SCALE), __NV_SATFINITE, __NV_E4M3);
+    }
+};
+
+// u = tanh(beta G + C psi + h') - psi  ->  U (FP32 and low precision).  One
+// load per element, so 32 columns per chunk keep enough reads in flight.
+template <bool FP8>
 struct Epi1 {
     static constexpr int W = 32;
     const float *psi;
     float *u32;
-    __nv_bfloat16 *u16;
+    typename Low<FP8>::T *ulow;
+    const float *row_scale;   // FP8: per-row scale of J
     const float2 *hdf;
     const ChainParams *params;
     int N, n_chains;
@@ -79,27 +99,31 @@ struct Epi1 {
 #pragma unroll
         for (int j = 0; j < W; ++j) ps[j] = (n0 + j < n_chains) ? ps_in[j * N] : 0.0f;
         const float hm = hdf ? hdf[m].x : 0.0f;
+        const float gs = FP8 ? row_scale[m] * FP8_OP_SCALE : 1.0f;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const float bj = __shfl_sync(0xffffffffu, cf.x, j);
             const float cj = __shfl_sync(0xffffffffu, cf.y, j);
             const float hj = __shfl_sync(0xffffffffu, cf.w, j);
-            const float a = fmaf(bj, v[j], cj * ps[j]);
+            const float a = fmaf(bj, FP8 ? v[j] * gs : v[j], cj * ps[j]);
             const float u = tanh_f(a + (hdf ? bj * hm : hj)) - ps[j];
             if (n0 + j < n_chains) {
                 u32[base + j * N] = u;
-                u16[base + j * N] = __float2bfloat16_rn(u);
+                ulow[base + j * N] = Low<FP8>::from(u);
             }
         }
     }
 };
 
-// F = beta (J U) + C u;  p += kick eps F;  psi += drift eps p (FP32 and BF16).
+// F = beta (J U) + C u;  p += kick eps F;  psi += drift eps p (FP32 and low
+// precision).
+template <bool FP8>
 struct Epi2 {
     static constexpr int W = 16;
     const float *u32;
     float *p, *psi;
-    __nv_bfloat16 *psi16;
+    typename Low<FP8>::T *psilow;
+    const float *row_scale;   // FP8: per-row scale of J
     const ChainParams *params;
     int N, n_chains;
     float kick, drift;   // schedule coefficients (times each chain's eps)
@@ -112,6 +136,7 @@ struct Epi2 {
         const float *u_in = u32 + base;
         float *p_io = p + base, *ps_io = psi + base;
         float uu[W], pp[W], ps[W];
+        const float gs = FP8 ? row_scale[m] * FP8_OP_SCALE : 1.0f;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const bool live = n0 + j < n_chains;
@@ -125,36 +150,46 @@ struct Epi2 {
             const float cj = __shfl_sync(0xffffffffu, cf.y, j);
             const float ej = __shfl_sync(0xffffffffu, cf.z, j);
             if (n0 + j >= n_chains) continue;
-            const float F = fmaf(bj, v[j], cj * uu[j]);
+            const float F = fmaf(bj, FP8 ? v[j] * gs : v[j], cj * uu[j]);
             const float pn = fmaf(kick * ej, F, pp[j]);
             p_io[j * N] = pn;
             if (do_drift) {
                 const float psn = fmaf(drift * ej, pn, ps[j]);
                 ps_io[j * N] = psn;
-                psi16[base + j * N] = __float2bfloat16_rn(psn);
+                psilow[base + j * N] = Low<FP8>::from(psn);
             }
         }
     }
 };
 
-template <bool PAIR>
+template <bool FP8>
+__device__ __forceinline__ typename Low<FP8>::T *low_psi(const DenseArgs &d) {
+    if constexpr (FP8) return d.psi8; else return d.psi16;
+}
+template <bool FP8>
+__device__ __forceinline__ typename Low<FP8>::T *low_u(const DenseArgs &d) {
+    if constexpr (FP8) return d.u8; else return d.u16;
+}
+
+template <bool PAIR, bool FP8>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force1_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tpsi,
                   const __grid_constant__ DenseArgs d) {
-    Epi1 epi{d.psi, d.u32, d.u16, d.hdf, d.params, d.N, d.n_chains};
+    Epi1<FP8> epi{d.psi, d.u32, low_u<FP8>(d), d.sJ8, d.hdf, d.params, d.N, d.n_chains};
     using Md = tc::Mode<PAIR>;
-    tc::gemm_persistent<PAIR>(&tj, &tpsi, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK, 1,
-                              epi, d.err);
+    tc::gemm_persistent<PAIR, Epi1<FP8>, FP8>(&tj, &tpsi, d.N / Md::TILE_M, d.b_pad / Md::TILE_N,
+                                              d.N / tc::Elem<FP8>::BK_ELEMS, 1, epi, d.err);
 }
 
-template <bool PAIR>
+template <bool PAIR, bool FP8>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     force2_kernel(const __grid_constant__ CUtensorMap tj, const __grid_constant__ CUtensorMap tu,
                   const __grid_constant__ DenseArgs d, float kick, float drift, int do_drift) {
-    Epi2 epi{d.u32, d.p, d.psi, d.psi16, d.params, d.N, d.n_chains, kick, drift, do_drift != 0};
+    Epi2<FP8> epi{d.u32,  d.p,        d.psi, low_psi<FP8>(d), d.sJ8,   d.params,
+                  d.N,    d.n_chains, kick,  drift,           do_drift != 0};
     using Md = tc::Mode<PAIR>;
-    tc::gemm_persistent<PAIR>(&tj, &tu, d.N / Md::TILE_M, d.b_pad / Md::TILE_N, d.N / tc::BK, 1, epi,
-                              d.err);
+    tc::gemm_persistent<PAIR, Epi2<FP8>, FP8>(&tj, &tu, d.N / Md::TILE_M, d.b_pad / Md::TILE_N,
+                                              d.N / tc::Elem<FP8>::BK_ELEMS, 1, epi, d.err);
 }
 
 // ------------------------------------------ FP64-accurate G = J Psi^T (action)
@@ -263,12 +298,14 @@ __global__ void __launch_bounds__(256) k_psi_digits(const float *__restrict__ ps
 
 // ------------------------------------------------------------- state helpers
 __global__ void k_copy_state(const float *__restrict__ src, float *__restrict__ dst,
-                             __nv_bfloat16 *__restrict__ dst16, int64_t n) {
+                             __nv_bfloat16 *__restrict__ dst16, uint8_t *__restrict__ dst8,
+                             int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float v = src[i];
         dst[i] = v;
-        if (dst16) dst16[i] = __float2bfloat16_rn(v);
+        if (dst16) dst16[i] = Low<false>::from(v);
+        if (dst8) dst8[i] = Low<true>::from(v);
     }
 }
 
@@ -515,7 +552,9 @@ __global__ void __launch_bounds__(256) k_dense_prepare(const double *__restrict_
                                                        uint16_t *__restrict__ dig,
                                                        int *__restrict__ row_exp,
                                                        float *__restrict__ Jhi,
-                                                       float *__restrict__ Jlo) {
+                                                       float *__restrict__ Jlo,
+                                                       uint8_t *__restrict__ J8,
+                                                       float *__restrict__ sJ8) {
     __shared__ double red[8];
     const int64_t i = blockIdx.x;
     const double *row = J + i * N;
@@ -528,11 +567,16 @@ __global__ void __launch_bounds__(256) k_dense_prepare(const double *__restrict_
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
     const int e = mx > 0.0 ? ilogb(mx) + 2 : 0;
     if (threadIdx.x == 0 && row_exp) row_exp[i] = e;
+    // FP8 row scale: the row's largest |J| maps to 448, the largest E4M3 value
+    const float s8 = mx > 0.0 ? (float)(mx / 448.0) : 1.0f;
+    if (threadIdx.x == 0 && sJ8) sJ8[i] = s8;
     constexpr int FRAC = ACT_BITS * ACT_DIGITS;   // 42 fraction bits
     const int64_t nn = N * N;
     for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
         const double x = row[j];
-        J16[i * N + j] = bf16_bits((float)x);
+        if (J16) J16[i * N + j] = bf16_bits((float)x);
+        if (J8)
+            J8[i * N + j] = (uint8_t)__nv_cvt_float_to_fp8((float)x / s8, __NV_SATFINITE, __NV_E4M3);
         if (dig) {
             const unsigned long long b = (unsigned long long)__double_as_longlong(x);
             const int be = (int)((b >> 52) & 0x7FF);
@@ -610,8 +654,8 @@ cudaError_t launch_gemm(void (*kern)(KArgs...), int cn, int nclu, int units, cud
 
 // Tensor map of a row-major BF16 matrix (rows x cols, cols contiguous) read in
 // boxes of box_rows x 64 with 128-byte swizzling.
-cudaError_t make_tmap_bf16(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
-                           int box_rows) {
+cudaError_t make_tmap_2d(CUtensorMap *map, const void *base, int64_t rows, int64_t cols,
+                         int box_rows, int elem_bytes) {
     // the driver entry point is looked up through the runtime, so the library
     // does not link the driver library itself
     using encode_fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -628,10 +672,11 @@ cudaError_t make_tmap_bf16(CUtensorMap *map, const void *base, int64_t rows, int
         encode = reinterpret_cast<encode_fn>(fn);
     }
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * (cuuint64_t)elem_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};   // 128-byte rows
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+    CUresult r = encode(map, elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        2, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -652,8 +697,8 @@ static cudaError_t gemm_store_mode(const CUtensorMap &ta, const CUtensorMap &tb,
 cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int N, int K, int *err,
                               cudaStream_t s) {
     CUtensorMap ta, tb;
-    cudaError_t e = make_tmap_bf16(&ta, A, M, K, tc::BM);
-    if (e == cudaSuccess) e = make_tmap_bf16(&tb, B, N, K, tc::BR);
+    cudaError_t e = make_tmap_2d(&ta, A, M, K, tc::BM, 2);
+    if (e == cudaSuccess) e = make_tmap_2d(&tb, B, N, K, tc::BR, 2);
     if (e != cudaSuccess) return e;
     return use_pair(M, N) ? gemm_store_mode<true>(ta, tb, D, M, N, K, err, s)
                           : gemm_store_mode<false>(ta, tb, D, M, N, K, err, s);
@@ -662,24 +707,34 @@ cudaError_t launch_gemm_store(const void *A, const void *B, float *D, int M, int
 template <bool PAIR>
 static cudaError_t force_clusters(int *nclu) {
     const int cs = PAIR ? 2 : 1;
-    int a = 0, b = 0, c = 0;
-    cudaError_t e = max_clusters(force1_kernel<PAIR>, cs, &a);
-    if (e == cudaSuccess) e = max_clusters(force2_kernel<PAIR>, cs, &b);
+    int a = 0, b = 0, c = 0, a8 = 0, b8 = 0;
+    cudaError_t e = max_clusters(force1_kernel<PAIR, false>, cs, &a);
+    if (e == cudaSuccess) e = max_clusters(force2_kernel<PAIR, false>, cs, &b);
+    if (e == cudaSuccess) e = max_clusters(force1_kernel<PAIR, true>, cs, &a8);
+    if (e == cudaSuccess) e = max_clusters(force2_kernel<PAIR, true>, cs, &b8);
     if (e == cudaSuccess) e = max_clusters(action_kernel<PAIR>, cs, &c);
-    *nclu = a < b ? (a < c ? a : c) : (b < c ? b : c);
+    int m = a;
+    for (int x : {b, c, a8, b8}) m = x < m ? x : m;
+    *nclu = m;
     return e;
 }
 
 cudaError_t dense_setup(DenseArgs &d) {
     d.pair = use_pair(d.N, d.b_pad) ? 1 : 0;
     cudaError_t e = d.pair ? force_clusters<true>(&d.nclu) : force_clusters<false>(&d.nclu);
-    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_J, d.J16, d.N, d.N, tc::BM);
-    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_psi, d.psi16, d.b_pad, d.N, tc::BR);
-    if (e == cudaSuccess) e = make_tmap_bf16(&d.tm_u, d.u16, d.b_pad, d.N, tc::BR);
+    const int eb = d.fp8 ? 1 : 2;
+    if (e == cudaSuccess)
+        e = make_tmap_2d(&d.tm_J, d.fp8 ? (const void *)d.J8 : (const void *)d.J16, d.N, d.N, tc::BM, eb);
+    if (e == cudaSuccess)
+        e = make_tmap_2d(&d.tm_psi, d.fp8 ? (const void *)d.psi8 : (const void *)d.psi16, d.b_pad,
+                         d.N, tc::BR, eb);
+    if (e == cudaSuccess)
+        e = make_tmap_2d(&d.tm_u, d.fp8 ? (const void *)d.u8 : (const void *)d.u16, d.b_pad, d.N,
+                         tc::BR, eb);
     if (e == cudaSuccess && d.action_tc) {
-        e = make_tmap_bf16(&d.tm_Jdig, d.Jdig, (int64_t)ACT_DIGITS * d.N, d.N, tc::BM);
+        e = make_tmap_2d(&d.tm_Jdig, d.Jdig, (int64_t)ACT_DIGITS * d.N, d.N, tc::BM, 2);
         if (e == cudaSuccess)
-            e = make_tmap_bf16(&d.tm_psidig, d.psidig, (int64_t)ACT_DIGITS * d.b_pad, d.N, tc::BR);
+            e = make_tmap_2d(&d.tm_psidig, d.psidig, (int64_t)ACT_DIGITS * d.b_pad, d.N, tc::BR, 2);
     }
     return e;
 }
@@ -707,18 +762,24 @@ static cudaError_t launch_action_product(DenseArgs &d, const float *psi, cudaStr
 
 // G = J Psi^T with the pass-1 epilogue (u), then G = J U^T with the pass-2
 // epilogue (kick, drift).
+template <bool PAIR, bool FP8>
+static cudaError_t launch_force_t(const DenseArgs &d, int pass, float kick, float drift,
+                                  int do_drift, cudaStream_t s) {
+    const int t = PAIR ? 256 : 128;
+    const int units = (d.N / t) * (d.b_pad / t);
+    const int cs = PAIR ? 2 : 1;
+    return pass == 0 ? launch_gemm(force1_kernel<PAIR, FP8>, cs, d.nclu, units, s, d.tm_J, d.tm_psi, d)
+                     : launch_gemm(force2_kernel<PAIR, FP8>, cs, d.nclu, units, s, d.tm_J, d.tm_u, d,
+                                   kick, drift, do_drift);
+}
+
 static cudaError_t launch_force(const DenseArgs &d, int pass, float kick, float drift, int do_drift,
                                 cudaStream_t s) {
-    if (d.pair) {
-        const int units = (d.N / 256) * (d.b_pad / 256);
-        return pass == 0 ? launch_gemm(force1_kernel<true>, 2, d.nclu, units, s, d.tm_J, d.tm_psi, d)
-                         : launch_gemm(force2_kernel<true>, 2, d.nclu, units, s, d.tm_J, d.tm_u, d,
-                                       kick, drift, do_drift);
-    }
-    const int units = (d.N / 128) * (d.b_pad / 128);
-    return pass == 0 ? launch_gemm(force1_kernel<false>, 1, d.nclu, units, s, d.tm_J, d.tm_psi, d)
-                     : launch_gemm(force2_kernel<false>, 1, d.nclu, units, s, d.tm_J, d.tm_u, d, kick,
-                                   drift, do_drift);
+    if (d.pair)
+        return d.fp8 ? launch_force_t<true, true>(d, pass, kick, drift, do_drift, s)
+                     : launch_force_t<true, false>(d, pass, kick, drift, do_drift, s);
+    return d.fp8 ? launch_force_t<false, true>(d, pass, kick, drift, do_drift, s)
+                 : launch_force_t<false, false>(d, pass, kick, drift, do_drift, s);
 }
 
 static int grid_elems(int64_t n) {
@@ -730,7 +791,9 @@ cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed,
                              int measure, cudaStream_t s, int64_t *launches) {
     const int64_t nel = (int64_t)d.b_pad * d.N;
     int64_t n = 0;
-    k_copy_state<<<grid_elems(nel), 256, 0, s>>>(d.psi_cur, d.psi, d.psi16, nel); ++n;
+    k_copy_state<<<grid_elems(nel), 256, 0, s>>>(d.psi_cur, d.psi, d.fp8 ? nullptr : d.psi16,
+                                                  d.fp8 ? d.psi8 : nullptr, nel);
+    ++n;
     k_dense_momenta<<<grid_elems(nel / 4), 256, 0, s>>>(d.p, d.N, d.n_chains, d.b_pad, seed, traj); ++n;
     for (int j = 0; j < sched.n_pass; ++j) {
         cudaError_t e = launch_force(d, 0, 0.f, 0.f, 0, s); ++n;
@@ -781,8 +844,8 @@ cudaError_t dense_matvec_f64(const double *J, const double *x, double *y, int64_
 }
 
 cudaError_t dense_prepare(const double *J, int64_t N, uint16_t *J16, uint16_t *dig, int *row_exp,
-                          float *Jhi, float *Jlo, cudaStream_t s) {
-    k_dense_prepare<<<(unsigned)N, 256, 0, s>>>(J, N, J16, dig, row_exp, Jhi, Jlo);
+                          float *Jhi, float *Jlo, uint8_t *J8, float *sJ8, cudaStream_t s) {
+    k_dense_prepare<<<(unsigned)N, 256, 0, s>>>(J, N, J16, dig, row_exp, Jhi, Jlo, J8, sJ8);
     return cudaGetLastError();
 }
 

@@ -106,6 +106,11 @@ constexpr int LOG1PEXP_NODES = 36 * 32 + 1;
 // ACT_DIGITS - 1), exact in the FP32 accumulator up to ACT_MAX_N sites.
 constexpr int ACT_BITS = 7, ACT_DIGITS = 6, ACT_PAIRS = 21, ACT_MAX_N = 4096;
 
+// FP8 force operands psi and u are stored as x / FP8_OP_SCALE in E4M3 (largest
+// value 448): a fixed scale, values beyond +-FP8_OP_RANGE saturate.
+constexpr float FP8_OP_RANGE = 32.0f;
+constexpr float FP8_OP_SCALE = FP8_OP_RANGE / 448.0f;
+
 struct DenseArgs {
     const __nv_bfloat16 *J16;   // N x N BF16 couplings
     const float *Jhi, *Jlo;     // N x N couplings as a double-float pair
@@ -130,6 +135,12 @@ struct DenseArgs {
     ChainState *state;
     int N, n_chains, b_pad;
     int pair, nclu;             // CTA-pair GEMM tiles (1) or single-CTA (0); clusters resident at once
+    // FP8 force variant: E4M3 J with per-row scales sJ8, E4M3 psi and u holding
+    // x / FP8_OP_SCALE
+    int fp8;
+    const uint8_t *J8;
+    const float *sJ8;
+    uint8_t *psi8, *u8;
     int *err;
     CUtensorMap tm_J, tm_psi, tm_u, tm_Jdig, tm_psidig;
 };
@@ -142,7 +153,7 @@ cudaError_t dense_matvec_f64(const double *J, const double *x, double *y, int64_
 // and row exponents (dig, row_exp) or its double-float pair (Jhi, Jlo); null
 // outputs are skipped.
 cudaError_t dense_prepare(const double *J, int64_t N, uint16_t *J16, uint16_t *dig, int *row_exp,
-                          float *Jhi, float *Jlo, cudaStream_t s);
+                          float *Jhi, float *Jlo, uint8_t *J8, float *sJ8, cudaStream_t s);
 cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
                              int measure, cudaStream_t s, int64_t *launches);
 cudaError_t dense_eval(DenseArgs &d, cudaStream_t s, int64_t *launches);

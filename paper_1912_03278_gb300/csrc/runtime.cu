@@ -47,6 +47,7 @@ struct ising_hmc {
     DenseArgs dense{};
     void *dJ16 = nullptr, *dJhi = nullptr, *dJlo = nullptr, *dpsi16 = nullptr, *du32 = nullptr,
          *du16 = nullptr, *dGhi = nullptr, *dGlo = nullptr;
+    void *dsJ8 = nullptr;   // FP8 form: per-row scales of J
     void *dJdig = nullptr, *dpsidig = nullptr, *drow_exp = nullptr, *dchain_exp = nullptr,
          *dGint = nullptr;
     // counters
@@ -76,7 +77,8 @@ static ising_status fail(ising_hmc *h, ising_status st, const char *fmt, ...) {
     } while (0)
 
 static bool is_dense_tc(const ising_hmc *h) {
-    return h->kind == ISING_KIND_DENSE && h->prec == ISING_PREC_BF16;
+    return h->kind == ISING_KIND_DENSE &&
+           (h->prec == ISING_PREC_BF16 || h->prec == ISING_PREC_FP8);
 }
 
 static bool is_fp32_lattice(const ising_hmc *h) {
@@ -225,7 +227,7 @@ static void free_all(ising_hmc *h) {
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
                     h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err, h->dJ16,
                     h->dJhi, h->dJlo, h->dpsi16, h->du32, h->du16, h->dGhi, h->dGlo,
-                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dGint};
+                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dGint, h->dsJ8};
     for (void *b : bufs)
         if (b) cudaFree(b);
     h->p = nullptr;
@@ -236,10 +238,11 @@ static void free_all(ising_hmc *h) {
 static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_h) {
     const int64_t C = n_chains;
     int64_t b = 0;
-    if (kind == ISING_KIND_DENSE && prec == ISING_PREC_BF16) {
+    if (kind == ISING_KIND_DENSE && (prec == ISING_PREC_BF16 || prec == ISING_PREC_FP8)) {
         const int64_t Bp = (C + 127) / 128 * 128;
-        b += Bp * N * (3 * 4 + 2 + 4 + 2);              // psi x2, p, psi16, u32, u16
-        b += N * N * 2;                                  // J in BF16
+        const int64_t lb = prec == ISING_PREC_FP8 ? 1 : 2;   // bytes of the low-precision copies
+        b += Bp * N * (3 * 4 + lb + 4 + lb);            // psi x2, p, psi low, u32, u low
+        b += N * N * lb + (prec == ISING_PREC_FP8 ? N * 4 : 0);   // J low (+ FP8 row scales)
         if (N <= ACT_MAX_N) {                            // digit planes, exponents, G as int64
             b += (int64_t)ACT_DIGITS * (N * N + Bp * N) * 2 + Bp * N * 8 + (N + Bp) * 4;
         } else {                                         // J as two FP32, G hi/lo
@@ -414,11 +417,13 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         h->g.dim = 0;
         h->g.X = (int)h->N; h->g.Y = 1; h->g.Z = 1; h->g.P = (int)h->N; h->g.nplanes = 1;
         h->g.N = h->N;
-        if (h->prec == ISING_PREC_BF16) {
+        if (h->prec == ISING_PREC_BF16 || h->prec == ISING_PREC_FP8) {
             if (h->N % 128)
-                return bail(fail(h, ISING_EINVAL, "BF16 dense form needs n_sites a multiple of 128"));
+                return bail(fail(h, ISING_EINVAL,
+                                 "tensor-core dense form needs n_sites a multiple of 128"));
             if (h->flip_every)
-                return bail(fail(h, ISING_EINVAL, "sign flip not available in the BF16 dense form"));
+                return bail(fail(h, ISING_EINVAL,
+                                 "sign flip not available in the tensor-core dense form"));
             h->dense_tc = true;
             h->b_pad = (h->n_chains + 127) / 128 * 128;
         } else if (h->prec != ISING_PREC_PLAIN_FP64) {
@@ -544,14 +549,17 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     }
     if (is_dense_tc(h)) {
         const size_t bn = (size_t)h->b_pad * N;
-        if ((st = dalloc(h, &h->dpsi16, bn * 2)) != ISING_OK) return bail(st);
+        const bool fp8 = h->prec == ISING_PREC_FP8;
+        const size_t lb = fp8 ? 1 : 2;   // low-precision copies of psi, u, J: E4M3 or BF16
+        if ((st = dalloc(h, &h->dpsi16, bn * lb)) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->du32, bn * 4)) != ISING_OK) return bail(st);
-        if ((st = dalloc(h, &h->du16, bn * 2)) != ISING_OK) return bail(st);
+        if ((st = dalloc(h, &h->du16, bn * lb)) != ISING_OK) return bail(st);
         const bool act_tc = N <= ACT_MAX_N;
         if (!h->d_J) return bail(fail(h, ISING_ECUDA, "coupling upload failed"));
-        if ((st = dalloc(h, &h->dJ16, (size_t)N * N * 2)) != ISING_OK) return bail(st);
-        if (cudaMemset(h->dpsi16, 0, bn * 2) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
-            cudaMemset(h->du16, 0, bn * 2) != cudaSuccess || cudaMemset(h->psi[1], 0, bn * 4) != cudaSuccess)
+        if ((st = dalloc(h, &h->dJ16, (size_t)N * N * lb)) != ISING_OK) return bail(st);
+        if (fp8 && (st = dalloc(h, &h->dsJ8, (size_t)N * sizeof(float))) != ISING_OK) return bail(st);
+        if (cudaMemset(h->dpsi16, 0, bn * lb) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
+            cudaMemset(h->du16, 0, bn * lb) != cudaSuccess || cudaMemset(h->psi[1], 0, bn * 4) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "dense upload failed"));
         if (act_tc) {
             // J in ACT_DIGITS base-2^ACT_BITS digit planes of row-scaled J (exact)
@@ -572,8 +580,10 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         }
         // BF16 copy and the action's operands, derived on the device; the FP64
         // couplings are not needed afterwards
-        if (dense_prepare(h->d_J, N, (uint16_t *)h->dJ16, (uint16_t *)h->dJdig, (int *)h->drow_exp,
-                          (float *)h->dJhi, (float *)h->dJlo, h->stream) != cudaSuccess ||
+        if (dense_prepare(h->d_J, N, fp8 ? nullptr : (uint16_t *)h->dJ16, (uint16_t *)h->dJdig,
+                          (int *)h->drow_exp, (float *)h->dJhi, (float *)h->dJlo,
+                          fp8 ? (uint8_t *)h->dJ16 : nullptr, (float *)h->dsJ8,
+                          h->stream) != cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "dense set-up failed: %s",
                              cudaGetErrorString(cudaGetLastError())));
@@ -581,15 +591,20 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         h->d_J = nullptr;
         h->bytes -= (int64_t)N * N * (int64_t)sizeof(double);
         DenseArgs &d = h->dense;
-        d.J16 = (const __nv_bfloat16 *)h->dJ16;
+        d.fp8 = fp8 ? 1 : 0;
+        d.J16 = fp8 ? nullptr : (const __nv_bfloat16 *)h->dJ16;
+        d.J8 = fp8 ? (const uint8_t *)h->dJ16 : nullptr;
+        d.sJ8 = (const float *)h->dsJ8;
+        d.psi8 = fp8 ? (uint8_t *)h->dpsi16 : nullptr;
+        d.u8 = fp8 ? (uint8_t *)h->du16 : nullptr;
         d.Jhi = (const float *)h->dJhi;
         d.Jlo = (const float *)h->dJlo;
         d.psi_cur = (float *)h->psi[0];
         d.psi = (float *)h->psi[1];
-        d.psi16 = (__nv_bfloat16 *)h->dpsi16;
+        d.psi16 = fp8 ? nullptr : (__nv_bfloat16 *)h->dpsi16;
         d.p = (float *)h->p;
         d.u32 = (float *)h->du32;
-        d.u16 = (__nv_bfloat16 *)h->du16;
+        d.u16 = fp8 ? nullptr : (__nv_bfloat16 *)h->du16;
         d.Ghi = (float *)h->dGhi;
         d.Glo = (float *)h->dGlo;
         d.action_tc = act_tc ? 1 : 0;

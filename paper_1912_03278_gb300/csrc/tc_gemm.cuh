@@ -104,8 +104,8 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulate,
-// both K-major, M = 128, N = BN.
+// Instruction descriptor, FP32 accumulate, both operands K-major:
+// kind::f16 with BF16 A and B, or kind::f8f6f4 with E4M3 A and B.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4)                      // D format F32
            | (1u << 7)                    // A format BF16
@@ -113,11 +113,35 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
            | ((uint32_t)(n >> 3) << 17)   // N / 8
            | ((uint32_t)(m >> 4) << 24);  // M / 16
 }
+__host__ __device__ constexpr uint32_t idesc_e4m3(int m, int n) {
+    return (1u << 4)                      // D format F32
+           | (0u << 7)                    // A format E4M3
+           | (0u << 10)                   // B format E4M3
+           | ((uint32_t)(n >> 3) << 17)   // N / 8
+           | ((uint32_t)(m >> 4) << 24);  // M / 16
+}
+// Elements of K in one 128-byte stage row, and per MMA (32 bytes).
+template <bool FP8>
+struct Elem {
+    static constexpr int BK_ELEMS = FP8 ? 128 : 64;
+};
 
-template <bool PAIR>
+template <bool PAIR, bool FP8 = false>
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                        uint32_t idesc, uint32_t accumulate) {
-    if (PAIR)
+    if (PAIR && FP8)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else if (FP8)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else if (PAIR)
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
@@ -317,7 +341,8 @@ struct Smem {
 constexpr int SMEM_BYTES = (int)sizeof(Smem) + 1024;
 
 // Persistent GEMM D = A B^T over m_units x n_units tiles of the mode's
-// TILE_M x TILE_N (K = nk * BK), each computed reps times: repetition r reads
+// TILE_M x TILE_N (K = nk * 128 bytes: 64 BF16 or, with FP8, 128 E4M3 elements per
+// stage row), each computed reps times: repetition r reads
 // A from row epi.a_off(r) on and B from row epi.b_off(r) on (stacked operand
 // planes) and hands r to the epilogue.  Single mode: CTA b takes tiles b, b +
 // gridDim.x, ..., each with all its repetitions in order.  Pair mode:
@@ -339,12 +364,13 @@ constexpr int SMEM_BYTES = (int)sizeof(Smem) + 1024;
 // TMEM is freed or the CTA exits.  The set-up (barriers, TMEM, cluster) runs
 // before the wait on the previous grid, so under programmatic dependent
 // launch it overlaps that grid's tail.
-template <bool PAIR, class Epi>
+template <bool PAIR, class Epi, bool FP8 = false>
 __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUtensorMap *tb,
                                                 int m_units, int n_units, int nk, int reps,
                                                 Epi &epi, int *err) {
     using Md = Mode<PAIR>;
     constexpr int TN = Md::TILE_N;
+    constexpr int KE = Elem<FP8>::BK_ELEMS;   // K elements per stage (128 bytes per row)
     extern __shared__ uint8_t smem_raw[];
     Smem &s = *reinterpret_cast<Smem *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -391,12 +417,12 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
                     if (PAIR) {
                         if (leader) mbar_expect_tx(&s.full[st], 2 * STAGE_BYTES);
                         const uint32_t fb = peer_addr(smem_u32(&s.full[st]), 0);
-                        tma_load_2d_pair(s.stage[st], ta, kb * BK, a_row, fb);
-                        tma_load_2d_pair(s.stage[st] + A_BYTES, tb, kb * BK, b_row, fb);
+                        tma_load_2d_pair(s.stage[st], ta, kb * KE, a_row, fb);
+                        tma_load_2d_pair(s.stage[st] + A_BYTES, tb, kb * KE, b_row, fb);
                     } else {
                         mbar_expect_tx(&s.full[st], STAGE_BYTES);
-                        tma_load_2d(s.stage[st], ta, kb * BK, a_row, &s.full[st]);
-                        tma_load_2d(s.stage[st] + A_BYTES, tb, kb * BK, b_row, &s.full[st]);
+                        tma_load_2d(s.stage[st], ta, kb * KE, a_row, &s.full[st]);
+                        tma_load_2d(s.stage[st] + A_BYTES, tb, kb * KE, b_row, &s.full[st]);
                     }
                 }
             }
@@ -407,7 +433,7 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
-            constexpr uint32_t idesc = idesc_bf16(Md::TILE_M, TN);
+            constexpr uint32_t idesc = FP8 ? idesc_e4m3(Md::TILE_M, TN) : idesc_bf16(Md::TILE_M, TN);
             uint32_t it = 0, lt = 0;
             for (int u = c0; u < tiles && ok; u += nclu)
             for (int r = 0; r < reps && ok; ++r, ++lt) {
@@ -426,10 +452,10 @@ __device__ __forceinline__ void gemm_persistent(const CUtensorMap *ta, const CUt
                     const uint32_t a_addr = smem_u32(s.stage[st]);
                     const uint32_t b_addr = a_addr + A_BYTES;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        tc_mma<PAIR>(acc, smem_desc_sw128(a_addr + k * 32),
-                                     smem_desc_sw128(b_addr + k * 32), idesc,
-                                     (kb > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k)   // four MMAs of 32 bytes of K each
+                        tc_mma<PAIR, FP8>(acc, smem_desc_sw128(a_addr + k * 32),
+                                          smem_desc_sw128(b_addr + k * 32), idesc,
+                                          (kb > 0 || k > 0) ? 1u : 0u);
                     tc_commit<PAIR>(&s.empty[st]);
                 }
                 if (!ok) break;

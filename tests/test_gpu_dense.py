@@ -49,14 +49,14 @@ BF16 = pkg.ISING_PREC_BF16
 
 
 def _dense_parity(N, n_chains, samples, beta=0.5, n_md=8, eps=0.06, traj=2, seed=5, h=True,
-                  psi_scale=0.4):
+                  psi_scale=0.4, prec=BF16, tol=2e-2):
     J = workloads.dense_couplings(N, seed=1)
     hv = workloads.dense_fields(N, 0.1) if h else 0.0
     lam = np.linalg.eigvalsh(J)[0]
     C = beta * abs(lam) + 0.1
     psi0 = workloads.start_psi(n_chains, N, scale=psi_scale, seed=23).astype(np.float32).astype(np.float64)
     sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=eps, n_md=n_md,
-                       n_chains=n_chains, precision=BF16)
+                       n_chains=n_chains, precision=prec)
     try:
         sim.set_state(psi0, next_traj=traj)
         sim.trajectories(1, seed)
@@ -74,7 +74,7 @@ def _dense_parity(N, n_chains, samples, beta=0.5, n_md=8, eps=0.06, traj=2, seed
         ch.traj = traj
         r = ch.trajectory(eps, n_md)
         rel = np.abs(prop - r["psi_prop"]).max() / np.abs(r["psi_prop"]).max()
-        assert rel <= 2e-2, (c, rel)          # BF16 force
+        assert rel <= tol, (c, rel)           # low-precision force
         H0 = oracle.kinetic(p0) + oracle.action(model, psi0[c])
         H1 = oracle.kinetic(pend) + oracle.action(model, prop)
         assert abs(rec[c, 0] - (H1 - H0)) <= 1e-6, (c, rec[c, 0], H1 - H0)   # FP64-accurate dH
@@ -89,6 +89,21 @@ def test_dense_bf16_parity_small_ragged_chains():
 def test_dense_bf16_parity_config_size():
     """N = 4096 SK couplings, 1024 chains (the dense workload), sampled chains."""
     _dense_parity(4096, 1024, samples=(0, 1023), n_md=8, eps=0.05)
+
+
+# FP8 E4M3 operands round to 3 mantissa bits (unit roundoff 2^-4): the force
+# carries errors of a few per cent, so the proposal after a trajectory may sit
+# up to ~10% (of max |psi|) from the exact one; dH is still exact to 1e-6.
+FP8_TOL = 0.1
+
+
+def test_dense_fp8_parity_small_ragged_chains():
+    _dense_parity(256, 130, samples=(0, 77, 129), prec=pkg.ISING_PREC_FP8, tol=FP8_TOL)
+
+
+def test_dense_fp8_parity_config_size():
+    _dense_parity(4096, 1024, samples=(0, 1023), n_md=8, eps=0.05, prec=pkg.ISING_PREC_FP8,
+                  tol=FP8_TOL)
 
 
 def test_dense_bf16_statistics_small_against_brute_force():
@@ -109,6 +124,30 @@ def test_dense_bf16_statistics_small_against_brute_force():
             sim.close()
     a, b = res[BF16], res[pkg.ISING_PREC_PLAIN_FP64]
     assert a["acceptance"] > 0.5
+    for key in ("E", "m"):
+        err = np.hypot(a[key + "_err"], b[key + "_err"])
+        assert abs(a[key] - b[key]) <= 4 * err + 1e-3, (key, a[key], b[key], err)
+
+
+def test_dense_fp8_statistics_against_plain_fp64():
+    """The FP8 force only lowers the acceptance: the chain still samples the
+    exact distribution (the action and dH are exact), so E and m agree with
+    the plain FP64 form within the statistical errors."""
+    N, beta = 128, 0.5
+    J = workloads.dense_couplings(N, seed=3)
+    hv = workloads.dense_fields(N, 0.1, seed=4)
+    C = beta * abs(np.linalg.eigvalsh(J)[0]) + 0.1
+    res = {}
+    for prec, chains, eps in ((pkg.ISING_PREC_FP8, 256, 0.06), (pkg.ISING_PREC_PLAIN_FP64, 8, 0.1)):
+        sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=eps, n_md=6,
+                           n_chains=chains, precision=prec, n_therm=50)
+        try:
+            sim.trajectories(350 if prec == pkg.ISING_PREC_FP8 else 300, 9)
+            res[prec] = sim.observables()
+        finally:
+            sim.close()
+    a, b = res[pkg.ISING_PREC_FP8], res[pkg.ISING_PREC_PLAIN_FP64]
+    assert a["acceptance"] > 0.3
     for key in ("E", "m"):
         err = np.hypot(a[key + "_err"], b[key + "_err"])
         assert abs(a[key] - b[key]) <= 4 * err + 1e-3, (key, a[key], b[key], err)
