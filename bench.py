@@ -695,10 +695,42 @@ def request_sites(r):
     return r["J"].shape[0] if r.get("kind") == "dense" else int(np.prod(r["L"]))
 
 
-def serve_run(pkg, seconds, rate=200.0, rho=0.8, seed=2, budget_gb=120.0):
+def _serve_window(pkg, reqs, arrivals, budget_gb, drain=True):
+    """Submit `reqs` at `arrivals` (s) to a fresh server; with drain, wait for
+    all of them and return latencies; without, stop at the last arrival and
+    report the queue."""
+    srv = pkg.IsingServer(int(budget_gb * 1e9), 4)
+    try:
+        ids = []
+        t0 = time.perf_counter()
+        for ta, r in zip(arrivals, reqs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(**r))
+        t_sub = time.perf_counter() - t0
+        st_sub = srv.stats()
+        if not drain:
+            return {"submitted": len(ids), "seconds": t_sub, "admitted": int(st_sub["admitted"]),
+                    "completed": int(st_sub["completed"]), "queued": int(st_sub["queued"]),
+                    "active": int(st_sub["active"]), "rejected": int(st_sub["rejected"])}
+        srv.drain(600.0)
+        t_all = time.perf_counter() - t0
+        res = [srv.poll(i) for i in ids]
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"res": res, "t_sub": t_sub, "t_all": t_all, "st": st,
+            "peak_queue": int(st_sub["queued"])}
+
+
+def serve_run(pkg, seconds, rate=200.0, rhos=(0.5, 0.8, 0.95), seed=2, budget_gb=120.0):
     """Serving: measure the server's capacity on a saturating batch, then
-    Poisson arrivals at `rate` requests/s for `seconds`, with trajectory counts
-    scaled so the offered load is `rho` of that capacity; p50/p99 latency."""
+    Poisson arrivals at `rate` requests/s for `seconds` (half as long for the
+    other loads), with trajectory counts scaled so the offered load is rho of
+    that capacity, for each rho; p50/p99 latency.  Last, the literal workload
+    (unscaled trajectory counts, far beyond any GPU) for a short window:
+    queue growth and admissions."""
     rng = np.random.default_rng(seed)
     work = lambda r: (request_sites(r) * r["n_chains"] * r["n_traj"] * r["n_md"])
     # mean work of an unscaled request, from a large sample
@@ -713,37 +745,40 @@ def serve_run(pkg, seconds, rate=200.0, rho=0.8, seed=2, budget_gb=120.0):
         cap = sum(work(r) for r in cal) / (time.perf_counter() - t0)
     finally:
         srv.close()
-    scale = rho * cap / (rate * mean_w)
-    n = int(rng.poisson(rate * seconds))
-    arrivals = np.sort(rng.uniform(0, seconds, n))
-    reqs = serve_requests(rng, n, scale)
-    srv = pkg.IsingServer(int(budget_gb * 1e9), 4)
-    try:
-        ids = []
-        t0 = time.perf_counter()
-        for ta, r in zip(arrivals, reqs):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            ids.append(srv.submit(**r))
-        t_sub = time.perf_counter() - t0
-        peak_queue = srv.stats()["queued"]
-        srv.drain(600.0)
-        t_all = time.perf_counter() - t0
-        res = [srv.poll(i) for i in ids]
-        st = srv.stats()
-    finally:
-        srv.close()
-    lat = np.array([r["latency"] for r in res if r["state"] == 2])
-    done_work = sum(work(r) for r, x in zip(reqs, res) if x["state"] == 2)
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "requests": n, "completed": int(st["completed"]),
-            "rejected": int(st["rejected"]), "rho": rho, "arrival_rate": rate,
-            "arrival_seconds": seconds, "submit_seconds": t_sub, "total_seconds": t_all,
-            "site_steps_per_s": done_work / t_all, "capacity_site_steps_per_s": cap,
-            "trajectory_scale": scale, "queued_at_end_of_arrivals": int(peak_queue),
-            "shared_graph_launches": int(st["group_launches"]), "quanta": int(st["quanta"]),
-            "dense_requests": int(sum(1 for r in reqs if r.get("kind") == "dense"))}
+    by_rho = {}
+    main = None
+    for rho in rhos:
+        secs = seconds if rho == 0.8 else seconds / 2
+        scale = rho * cap / (rate * mean_w)
+        n = int(rng.poisson(rate * secs))
+        arrivals = np.sort(rng.uniform(0, secs, n))
+        reqs = serve_requests(rng, n, scale)
+        w = _serve_window(pkg, reqs, arrivals, budget_gb)
+        res, st = w["res"], w["st"]
+        lat = np.array([r["latency"] for r in res if r["state"] == 2])
+        done_work = sum(work(r) for r, x in zip(reqs, res) if x["state"] == 2)
+        row = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+               "mean_s": float(lat.mean()), "requests": n, "completed": int(st["completed"]),
+               "rejected": int(st["rejected"]), "arrival_seconds": secs,
+               "total_seconds": w["t_all"], "site_steps_per_s": done_work / w["t_all"],
+               "trajectory_scale": scale, "queued_at_end_of_arrivals": w["peak_queue"],
+               "dense_requests": int(sum(1 for r in reqs if r.get("kind") == "dense"))}
+        by_rho[str(rho)] = row
+        if rho == 0.8:
+            main = dict(row, rho=rho, arrival_rate=rate, submit_seconds=w["t_sub"],
+                        capacity_site_steps_per_s=cap,
+                        shared_graph_launches=int(st["group_launches"]), quanta=int(st["quanta"]))
+    out = main if main is not None else {}
+    out["by_rho"] = by_rho
+    lit_secs = 2.0
+    n = int(rng.poisson(rate * lit_secs))
+    arrivals = np.sort(rng.uniform(0, lit_secs, n))
+    reqs = serve_requests(rng, n, 1.0)
+    out["literal"] = dict(_serve_window(pkg, reqs, arrivals, budget_gb, drain=False),
+                          offered_site_steps=float(sum(work(r) for r in reqs)),
+                          note="unscaled trajectory counts; the window ends at the last arrival, "
+                               "queued work is dropped with the server")
+    return out
 
 
 def e2e_rate(pkg, sims, Ls, n_chains, seed, stream, steps=3):
