@@ -402,6 +402,11 @@ class IsingGroup:
     def launches(self):
         return ising_group_launch_count(self.g)
 
+    @property
+    def stream(self):
+        """cudaStream_t (as an integer) the group's graph launches run on."""
+        return ising_group_stream(self.g) or 0
+
     def close(self):
         if self.g:
             ising_group_destroy(self.g)
