@@ -207,7 +207,7 @@ __device__ __forceinline__ float *sel3(const FusedArgs &A, int i) {
 // Per-chain constants of the action in double-float form.
 struct ActConst {
     f2 C2, bJ2, hp2, beta2;
-    float Cf, bJf;
+    float Cf, bJf, betaf, hpf;
     bool hzero;
 };
 
@@ -219,6 +219,8 @@ __device__ __forceinline__ ActConst act_const(const ChainParams &prm) {
     k.beta2 = df_from_double(prm.beta);
     k.Cf = prm.Cf;
     k.bJf = prm.bJf;
+    k.betaf = prm.betaf;
+    k.hpf = prm.hpf;
     k.hzero = prm.hp == 0.0;
     return k;
 }
@@ -226,12 +228,15 @@ __device__ __forceinline__ ActConst act_const(const ChainParams &prm) {
 // Action terms of the VEC sites site0.. of S(sign*psi), whose neighbourhood n
 // has been gathered:  S_i = 1/2 psi_i a_i - |x_i| - log(1 + exp(-2|x_i|)),
 // x = a + h', a = A psi, in double-float arithmetic; the Sec. 4 estimators
-// (tanh(x) sums) and one conditional spin draw per site.
+// (tanh(x) sums, x in FP32 exactly as the force pass forms it, so a force
+// pass may hand over its tanh values in tpre) and one conditional spin draw
+// per site.
 template <int DIM, int VEC>
 __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst &kc,
                                               const Nbr<DIM, VEC> &n, int64_t site0, float sign,
                                               uint32_t spin_traj, uint64_t seed, int chain,
-                                              const float4 *tab, Acc &acc) {
+                                              const float4 *tab, Acc &acc,
+                                              const Vec<VEC> *tpre = nullptr) {
     float su[4];
     if constexpr (VEC == 4) {
         const float4 w = spin_u4_f32((uint32_t)(site0 >> 2), spin_traj, (uint32_t)chain, seed);
@@ -246,25 +251,24 @@ __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst
         const f2 nbd = exact_nb<DIM, VEC>(n, q);
         const f2 a = df_add_q(df_mul_f(kc.C2, ps), df_mul(kc.bJ2, f2{sign * nbd.hi, sign * nbd.lo}));
         f2 x = a;
-        float hq = 0.0f;
         if (A.hdf) {
             const float2 hh = A.hdf[site0 + q];
             const f2 hp = df_mul(kc.beta2, f2{hh.x, hh.y});
             x = df_add_q(a, hp);
-            hq = hp.hi;
         } else if (!kc.hzero) {
             x = df_add_q(a, kc.hp2);
-            hq = kc.hp2.hi;
         }
         const f2 ax = x.hi < 0.0f ? df_neg(x) : x;
         const f2 gl = log1pexp_neg(f2{2.0f * ax.hi, 2.0f * ax.lo}, tab);
         // S_i for this site, summed over the vector first (short chains)
         const f2 si = df_add_q(df_mul_f(a, 0.5f * ps), df_neg(df_add_q(ax, gl)));
         sv = df_add_q(sv, si);
-        const float tq = tanh_f(fmaf(kc.Cf, ps, sign * kc.bJf * n.nb.v[q]) + hq);
+        const float hf = A.hdf ? kc.betaf * A.hdf[site0 + q].x : kc.hpf;
+        const float tq = tpre ? tpre->v[q]
+                              : tanh_f(fmaf(kc.Cf, ps, sign * kc.bJf * n.nb.v[q]) + hf);
         vT += tq;
         vAT = fmaf(a.hi, tq, vAT);
-        if (has_h) vHT = fmaf(hq, tq, vHT);
+        if (has_h) vHT = fmaf(hf, tq, vHT);
         float uu;
         if constexpr (VEC == 4) {
             uu = su[q];
@@ -395,7 +399,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     if constexpr (LAST) {
                         if (it >= 0 && it < nz)
                             vector_action<DIM, VEC>(A, kc, n, (int64_t)it * P + e0, 1.0f, pc.traj,
-                                                    A.seed, chain, tab, acc);
+                                                    A.seed, chain, tab, acc, &t);
                     }
                 }
             }
