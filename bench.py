@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -361,6 +362,13 @@ def run_ours(args):
                                n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
                                stream=stream.cuda_stream)
     seed = replica_seed(rank)
+    # launch shape (threads per CTA, ring depth) per lattice size from the
+    # library's autotuner (a temporary handle, before any state is set)
+    tuned_launch = {}
+    if not args.no_autotune:
+        for L in Ls:
+            ms = sims[L].autotune(reps=2)
+            tuned_launch[str(L)] = dict(zip(("threads", "depth"), sims[L].launch), ms=ms)
     hot_start(pkg, sims, seed, betas, C)
     tune_trace = tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
@@ -427,6 +435,7 @@ def run_ours(args):
                              % (16 * sum(L * L for L in Ls) * n_chains / 1e9)},
             "acceptance": {str(L): obs[L]["acceptance"] for L in Ls},
             "tuning": tune_trace,
+            "launch_shape": tuned_launch or {str(L): sims[L].launch for L in Ls},
             "roofline": roofline,
             "gpu_launches": int(launches)}
 
