@@ -86,6 +86,13 @@ def test_dense_bf16_parity_small_ragged_chains():
     _dense_parity(256, 130, samples=(0, 77, 129))
 
 
+@pytest.mark.parametrize("prec,tol", [(BF16, 2e-2), (pkg.ISING_PREC_FP8, 0.1)])
+def test_dense_parity_single_cta_tiles(prec, tol):
+    """N = 384 and 100 chains are not multiples of 256: the forces and the
+    action run on single-CTA 128 x 128 tiles instead of CTA pairs."""
+    _dense_parity(384, 100, samples=(0, 57, 99), prec=prec, tol=tol)
+
+
 def test_dense_bf16_parity_config_size():
     """N = 4096 SK couplings, 1024 chains (the dense workload), sampled chains."""
     _dense_parity(4096, 1024, samples=(0, 1023), n_md=8, eps=0.05)
