@@ -469,19 +469,25 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def plain_rate(pkg, L, betas, C, tuned, stream):
-    """Plain FP64 form (one chain per launch, unfused kernels) on a sample of chains
-    with the tuned step sizes."""
+def plain_rate(pkg, L, betas, C, tuned, stream, k=8, n=4):
+    """Plain FP64 form (one chain per launch, unfused kernels) on k chains spread
+    over the betas, started from the batched handle's own current
+    configurations with its tuned step sizes, so both forms run the same
+    Markov chains at the same point of equilibration; acceptance of both on
+    these chains is reported (the plain form's from n trajectories, the
+    batched form's from its timed steps)."""
     import torch
-    idx = np.array([0, len(betas) // 2, len(betas) - 1])
+    idx = np.linspace(0, len(betas) - 1, k).round().astype(int)
     eps = tuned._eps[idx]
     sim = pkg.IsingHMC(dim=2, L=(L, L), beta=betas[idx], C=C[idx], eps=eps, n_md=N_MD,
                        n_chains=len(idx), precision=pkg.ISING_PREC_PLAIN_FP64,
                        stream=stream.cuda_stream)
     try:
+        psi = np.stack([tuned.chains(pkg.binding.ISING_STATE_PSI, int(c), 1)[0] for c in idx])
+        sim.set_state(psi, next_traj=10 ** 6)
         sim.trajectories(1, 77)
         sim.sync()
-        n = 2
+        sim.reset_sums()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         l0 = sim.launches
@@ -491,9 +497,12 @@ def plain_rate(pkg, L, betas, C, tuned, stream):
         torch.cuda.synchronize()
         dt = t0.elapsed_time(t1) / 1e3
         acc = sim.observables()["acceptance"]
+        sums = tuned.chain_sums()[idx]
+        acc_b = float(sums[:, 1].sum() / max(1.0, sums[:, 0].sum()))
         return {"value": len(idx) * L * L * N_MD * n / dt, "unit": UNIT, "chains": len(idx),
                 "L": L, "trajectories": n, "launches": sim.launches - l0, "dtype": "f64",
-                "acceptance_sample": acc}
+                "acceptance_sample": acc, "acceptance_batched_same_chains": acc_b,
+                "start": "the batched handle's current configurations of the same chains"}
     finally:
         sim.close()
 

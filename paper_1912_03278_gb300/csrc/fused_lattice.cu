@@ -769,9 +769,9 @@ int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec) {
 
 // Launch shape: VEC = 4 when rows split into float4s; threads = one per vector
 // up to 256, each thread owning at most NVMAX vectors per plane; prefetch
-// depth 4 planes when the rings fit in 200 KB, else 2 (or 1 for the largest
-// planes).  Returns VEC, or -1 if
-// the plane does not fit on chip.
+// depth 1 plane (with the force plane trailing, the resident CTAs cover the
+// copy latency: the autotuner picks depth 1 for 2D L = 256 and 1024 as well).
+// Returns VEC, or -1 if the plane does not fit on chip.
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
     const int vec = (g.X % 4 == 0 && g.P % 4 == 0) ? 4 : 1;
     const int nvec = g.P / vec;
@@ -780,11 +780,8 @@ int fused_lattice_pick(const Geometry &g, int *threads, int *depth) {
     if (t < 32) t = 32;
     if ((nvec + t - 1) / t > NVMAX) return -1;
     *threads = t;
-    int d = 4;
-    if (fused_lattice_smem_bytes(g, d, vec) > 200 * 1024) d = 2;
-    if (fused_lattice_smem_bytes(g, d, vec) > 220 * 1024) d = 1;
-    if (fused_lattice_smem_bytes(g, d, vec) > 227 * 1024) return -1;
-    *depth = d;
+    if (fused_lattice_smem_bytes(g, 1, vec) > 227 * 1024) return -1;
+    *depth = 1;
     return vec;
 }
 
