@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-integrators", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -446,6 +447,8 @@ def run_ours(args):
             line["speedup_vs_plain"] = value / ws / line["plain_form"]["value"]
         if not args.no_e2e:
             line["e2e"] = e2e_rate(pkg, sims, Ls, n_chains, seed, stream)
+        if not args.no_integrators:
+            line["integrators"] = integrator_compare(pkg, sims[big], betas, stream, L=big)
     for s in sims.values():
         s.close()
     sims = {}
@@ -616,6 +619,45 @@ def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10
         out["speedup_vs_plain"] = out["value"] / rate
     except Exception as e:   # report, do not hide
         out["plain_form"] = {"error": str(e)}
+    return out
+
+
+def integrator_compare(pkg, tuned, betas, stream, L=1024, per_beta=19, therm=8, steps=4, seed=55):
+    """Omelyan's second-order minimum-norm integrator against KDK leapfrog at
+    equal cost and equal trajectory length: 21 force evaluations each
+    (leapfrog N_md = 20 at the tuned eps, Omelyan N_md = 10 at twice it), on
+    the same chains started from the same states; acceptance and time per
+    trajectory (CUDA events)."""
+    import torch
+    ub = np.unique(betas)
+    eps_b = {b: float(np.median(tuned._eps[betas == b])) for b in ub}
+    bsub = np.repeat(ub, per_beta)
+    C = workloads.lattice_C(bsub, 2)
+    eps = np.array([eps_b[b] for b in bsub])
+    out = {}
+    for name, integ, n_md, e in (("leapfrog", pkg.ISING_INTEGRATOR_LEAPFROG, N_MD, eps),
+                                 ("omelyan", pkg.ISING_INTEGRATOR_OMELYAN, N_MD // 2, 2 * eps)):
+        sim = pkg.IsingHMC(dim=2, L=(L, L), beta=bsub, C=C, eps=e, n_md=n_md, n_chains=len(bsub),
+                           precision=pkg.ISING_PREC_FP32, integrator=integ,
+                           stream=stream.cuda_stream)
+        try:
+            hot_start(pkg, {L: sim}, seed, bsub, C)
+            sim.trajectories(therm, seed)
+            sim.reset_sums()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.trajectories(steps, seed)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            obs = sim.observables()
+            out[name] = {"n_md": n_md, "force_evaluations": n_md + 1 if integ == 0 else 2 * n_md + 1,
+                         "ms_per_trajectory": e0.elapsed_time(e1) / steps,
+                         "acceptance": obs["acceptance"], "mean_dH": obs["mean_dH"]}
+        finally:
+            sim.close()
+    out["chains"] = int(len(bsub))
+    out["L"] = L
     return out
 
 
