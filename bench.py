@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-integrators", action="store_true")
+    ap.add_argument("--no-infinite", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -457,6 +458,8 @@ def run_ours(args):
             line["mixed_3d"] = mixed_3d_rate(pkg)
         if not args.no_dense:
             line["dense"] = dense_rate(pkg, stream)
+        if not args.no_infinite:
+            line["infinite"] = infinite_rate(pkg, stream)
         if not args.no_serve:
             line["serve"] = serve_run(pkg, args.serve_seconds)
         if not args.no_cpu:
@@ -659,6 +662,48 @@ def integrator_compare(pkg, tuned, betas, stream, L=1024, per_beta=19, therm=8, 
     out["chains"] = int(len(bsub))
     out["L"] = L
     return out
+
+
+def infinite_rate(pkg, stream, N=4096, n_chains=152 * 32, steps=4, therm=20, seed=41):
+    """Infinite-range (all-to-all) model of the appendix at the critical
+    coupling beta*J = 1, h = 0, C = 1 (A's spectrum in [1, 2]), N_md =
+    floor(ln N), eps = 1/N_md: site-steps/s of the O(N) kernel, time per
+    trajectory (CUDA events, one launch per trajectory) and its HBM roofline
+    at 16 algorithmic bytes per site-step (psi and p read, p and psi' written)."""
+    import torch
+    n_md = workloads.n_md_default(N)
+    sim = pkg.IsingHMC(kind="infinite", n_sites=N, beta=1.0, C=1.0, eps=1.0 / n_md, n_md=n_md,
+                       n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
+                       stream=stream.cuda_stream)
+    try:
+        sim.trajectories(therm, seed)
+        sim.reset_sums()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        l0 = sim.launches
+        for k in range(steps):
+            ev[k][0].record(stream)
+            sim.trajectories(1, seed)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        obs = sim.observables()
+        dur = float(np.mean(ms)) / 1e3
+        site_steps = float(N) * n_chains * n_md
+        peak, peak_kind = measured_peaks()
+        achieved = 16.0 * site_steps / dur / 1e9
+        return {"workload": "all-to-all N=%d, %d chains, beta*J=1, h=0, C=1, N_md=%d, eps=1/N_md"
+                            % (N, n_chains, n_md),
+                "value": site_steps / dur, "unit": UNIT, "ms_per_trajectory": dur * 1e3,
+                "launches": int(sim.launches - l0), "acceptance": obs["acceptance"],
+                "E": obs["E"], "E_err": obs["E_err"],
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_kind,
+                             "kernel": "infinite_kernel",
+                             "algorithmic_bytes_per_launch": 16.0 * site_steps}}
+    finally:
+        sim.close()
 
 
 def mixed_3d_rate(pkg, steps=4, seed=31):

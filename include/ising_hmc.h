@@ -52,7 +52,13 @@ typedef enum {
     ISING_EBUSY = 6     /* resource in use (e.g. a group already running)    */
 } ising_status;
 
-enum { ISING_KIND_LATTICE = 0, ISING_KIND_DENSE = 1 };
+/* Kinds of coupling (Sec. 2: the Hamiltonian with connectivity K):
+ *  LATTICE   periodic hypercubic lattice, nearest neighbours, coupling Jnn;
+ *  DENSE     arbitrary symmetric N x N couplings J (K absorbed into J);
+ *  INFINITE  the all-to-all ("infinite-range") model of the appendix:
+ *            K_ij = 1/N for i != j, coupling Jnn, N = n_sites; no matrix is
+ *            stored, every product with A costs O(N).  FP32 form only. */
+enum { ISING_KIND_LATTICE = 0, ISING_KIND_DENSE = 1, ISING_KIND_INFINITE = 2 };
 
 enum {
     ISING_PREC_PLAIN_FP64 = 0, /* FP64 state and force, one chain per launch, unfused */
@@ -64,12 +70,13 @@ enum {
 enum { ISING_INTEGRATOR_LEAPFROG = 0, ISING_INTEGRATOR_OMELYAN = 1 };
 
 typedef struct {
-    int kind;             /* ISING_KIND_LATTICE or ISING_KIND_DENSE                    */
+    int kind;             /* ISING_KIND_LATTICE, ISING_KIND_DENSE or ISING_KIND_INFINITE */
     int dim;              /* lattice: 1..3                                              */
     int L[3];             /* lattice extents, each >= 3 (L = 2 would double the bonds)  */
-    int64_t n_sites;      /* dense: N (ignored for lattices)                            */
+    int64_t n_sites;      /* dense, infinite: N (ignored for lattices)                  */
     const double *J;      /* dense: host N*N row-major, symmetric, J_ii = 0; copied     */
-    double Jnn;           /* lattice nearest-neighbour coupling J (Sec. 2)              */
+    double Jnn;           /* lattice nearest-neighbour coupling J (Sec. 2); infinite:
+                             the all-to-all coupling J (each pair couples with J/N)    */
     const double *h;      /* host per-site field h_i (N values) or NULL; copied         */
     double h0;            /* uniform field when h == NULL                               */
     double beta, C, eps;  /* defaults for every chain; C in the units of A above        */
@@ -116,7 +123,9 @@ typedef struct ising_hmc ising_hmc_t;
  * action S(0) computed on the device.
  * Validation (Sec. 2, spectrum bound and shift): lattice requires
  * C > beta*|J|*2*dim for every chain; dense requires C > beta*|lambda_min(J)|,
- * with lambda_min from a Lanczos estimate on the host (ENOTPD otherwise).
+ * with lambda_min from a Lanczos estimate on the host (ENOTPD otherwise);
+ * infinite requires C > beta*J/N for J >= 0 and C > beta*|J|*(N-1)/N for
+ * J < 0 (the exact extreme eigenvalues of beta*J*K), and 2 <= N <= 2^31.
  * Errors: EINVAL (bad sizes/kinds/precision for the kind), ENOTPD, ENOMEM, ECUDA. */
 ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out);
 

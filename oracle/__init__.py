@@ -11,6 +11,7 @@ Parity status: every C function is pinned by a CPU test (see the header
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 from ctypes import POINTER, c_double, c_int, c_int64, c_uint32, c_uint64, c_void_p
@@ -29,7 +30,8 @@ PURPOSE_MOM, PURPOSE_ACC, PURPOSE_SPIN, PURPOSE_FLIP, PURPOSE_MH = 1, 2, 3, 4, 5
 def build(force: bool = False, extra_flags=()) -> str:
     """Compile the oracle into a shared library next to its source."""
     out = _LIB_PATH if not extra_flags else os.path.join(
-        _HERE, "libising_oracle_%x.so" % (abs(hash(tuple(extra_flags))) & 0xffffff))
+        _HERE, "libising_oracle_%s.so"
+        % hashlib.sha1(" ".join(extra_flags).encode()).hexdigest()[:8])
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", *extra_flags,
                _SRC, "-o", out, "-lm", "-lpthread"]

@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(HERE, "lib", "libising_hmc.so")
 # status codes
 ISING_OK, ISING_EINVAL, ISING_ENOTPD, ISING_ENOMEM, ISING_ECUDA, ISING_ETIMEOUT, ISING_EBUSY = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOTPD", "ENOMEM", "ECUDA", "ETIMEOUT", "EBUSY"]
-ISING_KIND_LATTICE, ISING_KIND_DENSE = 0, 1
+ISING_KIND_LATTICE, ISING_KIND_DENSE, ISING_KIND_INFINITE = 0, 1, 2
+_KINDS = {"lattice": ISING_KIND_LATTICE, "dense": ISING_KIND_DENSE,
+          "infinite": ISING_KIND_INFINITE}
 ISING_PREC_PLAIN_FP64, ISING_PREC_FP32, ISING_PREC_BF16, ISING_PREC_FP8 = 0, 1, 2, 3
 ISING_INTEGRATOR_LEAPFROG, ISING_INTEGRATOR_OMELYAN = 0, 1
 ISING_STATE_PSI, ISING_STATE_PSI_PROPOSAL, ISING_STATE_P_END = 0, 1, 2
@@ -145,7 +147,9 @@ def make_config(kind="lattice", dim=2, L=(4, 4), n_sites=0, J=None, Jnn=1.0, h=0
     create call returns."""
     cfg = ising_hmc_config()
     keep = []
-    cfg.kind = ISING_KIND_DENSE if kind == "dense" else ISING_KIND_LATTICE
+    if kind not in _KINDS:
+        raise ValueError("kind must be one of %s" % sorted(_KINDS))
+    cfg.kind = _KINDS[kind]
     cfg.dim = dim
     Lt = tuple(L) + (1,) * (3 - len(L))
     for i in range(3):
@@ -155,6 +159,8 @@ def make_config(kind="lattice", dim=2, L=(4, 4), n_sites=0, J=None, Jnn=1.0, h=0
         keep.append(Jm)
         cfg.J = Jm.ctypes.data
         cfg.n_sites = Jm.shape[0]
+    elif kind == "infinite":
+        cfg.n_sites = int(n_sites)
     cfg.Jnn = Jnn
     if np.isscalar(h):
         cfg.h = None
@@ -183,6 +189,12 @@ def make_config(kind="lattice", dim=2, L=(4, 4), n_sites=0, J=None, Jnn=1.0, h=0
         bmax = float(np.max(beta))
         if kind == "dense":
             C = bmax * abs(np.linalg.eigvalsh(_f64(J))[0]) + 0.1
+        elif kind == "infinite":
+            # beta*J*K has eigenvalues -beta*J/N and beta*J*(N-1)/N
+            lam = -Jnn / n_sites if Jnn >= 0 else Jnn * (n_sites - 1) / n_sites
+            C = np.asarray(beta) * abs(lam) + 0.1
+            if np.ndim(C) == 0:
+                C = float(C)
         else:
             C = np.asarray(beta) * abs(Jnn) * 2 * dim + 0.1
             if np.ndim(C) == 0:

@@ -86,6 +86,13 @@ cudaError_t fused_lattice_node(const FusedArgs &a, int threads, int depth,
 int fused_lattice_valid_launch(const Geometry &g, int threads, int depth);
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
 
+// Infinite-range (all-to-all) model, FP32 form: the same arguments, modes and
+// per-chain state as the lattice kernel (g.N sites, one CTA per chain);
+// ChainParams::bJ holds kappa = beta*J/N.
+cudaError_t launch_infinite(const FusedArgs &a, const Schedule &sched, cudaStream_t s);
+cudaError_t infinite_node(const FusedArgs &a, cudaKernelNodeParams *np, void **args);
+int infinite_threads(int64_t N);
+
 cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s);
 // BF16 tensor-core GEMM D[n*M + m] = sum_k A[m][k] B[n][k]; M, N multiples of
 // 128, K a multiple of 64; *err gets bit 0 if a bounded wait ran out.

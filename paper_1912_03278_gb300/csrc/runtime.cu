@@ -85,6 +85,12 @@ static bool is_fp32_lattice(const ising_hmc *h) {
     return h->kind == ISING_KIND_LATTICE && h->prec == ISING_PREC_FP32;
 }
 
+// Forms run by one fused whole-trajectory kernel over three state buffers:
+// the FP32 lattice and the infinite-range model.
+static bool is_fused(const ising_hmc *h) {
+    return is_fp32_lattice(h) || h->kind == ISING_KIND_INFINITE;
+}
+
 static size_t state_elem(const ising_hmc *h) {
     return h->prec == ISING_PREC_PLAIN_FP64 ? sizeof(double) : sizeof(float);
 }
@@ -296,6 +302,11 @@ static PlainArgs plain_args(ising_hmc *h, int c) {
     return a;
 }
 
+static cudaError_t launch_fused(ising_hmc *h, const FusedArgs &a) {
+    if (h->kind == ISING_KIND_INFINITE) return launch_infinite(a, h->sched, h->stream);
+    return launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream);
+}
+
 static FusedArgs fused_args(ising_hmc *h) {
     FusedArgs a{};
     for (int i = 0; i < 3; ++i) a.psi[i] = (float *)h->psi[i];
@@ -319,13 +330,13 @@ static ising_status eval_current(ising_hmc *h) {
         CUDA_OR_FAIL(h, dense_eval(h->dense, h->stream, &h->launches));
         return ISING_OK;
     }
-    if (is_fp32_lattice(h)) {
+    if (is_fused(h)) {
         FusedArgs a = fused_args(h);
         a.mode = MODE_EVAL;
         a.seed = 0;
         a.traj0 = TRAJ_INIT_INDEX;
         a.n_traj = 0;
-        CUDA_OR_FAIL(h, launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream));
+        CUDA_OR_FAIL(h, launch_fused(h, a));
         h->launches += 1;
     } else {
         for (int c = 0; c < h->n_chains; ++c) {
@@ -352,7 +363,7 @@ const char *ising_hmc_last_create_error(void) { return g_create_err; }
 int64_t ising_hmc_estimate_bytes(const ising_hmc_config *cfg) {
     if (!cfg) return -1;
     int64_t N = 0;
-    if (cfg->kind == ISING_KIND_DENSE) N = cfg->n_sites;
+    if (cfg->kind == ISING_KIND_DENSE || cfg->kind == ISING_KIND_INFINITE) N = cfg->n_sites;
     else {
         N = 1;
         for (int d = 0; d < cfg->dim && d < 3; ++d) N *= cfg->L[d];
@@ -430,6 +441,17 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             return bail(fail(h, ISING_EINVAL, "precision %d not available for dense couplings in this build",
                              h->prec));
         }
+    } else if (cfg->kind == ISING_KIND_INFINITE) {
+        if (cfg->n_sites < 2 || cfg->n_sites > ((int64_t)1 << 31))
+            return bail(fail(h, ISING_EINVAL, "infinite-range model needs 2 <= n_sites <= 2^31"));
+        if (h->prec != ISING_PREC_FP32)
+            return bail(fail(h, ISING_EINVAL,
+                             "precision %d not available for the infinite-range model", h->prec));
+        h->dim = 0;
+        h->N = cfg->n_sites;
+        h->g.dim = 0;
+        h->g.X = 1; h->g.Y = 1; h->g.Z = 1; h->g.P = 1; h->g.nplanes = 1;
+        h->g.N = h->N;
     } else {
         return bail(fail(h, ISING_EINVAL, "unknown kind %d", cfg->kind));
     }
@@ -471,6 +493,15 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             if (!(C > bound))
                 return bail(fail(h, ISING_ENOTPD,
                                  "chain %d: C=%g must exceed beta*|J|*2*dim=%g (Sec. 2)", c, C, bound));
+        } else if (h->kind == ISING_KIND_INFINITE) {
+            // eigenvalues of beta*J*K: -beta*J/N (N-1 times), beta*J*(N-1)/N
+            const double Nd = (double)N;
+            const double bound = cfg->Jnn >= 0 ? beta * cfg->Jnn / Nd
+                                               : beta * -cfg->Jnn * (Nd - 1.0) / Nd;
+            if (!(C > bound))
+                return bail(fail(h, ISING_ENOTPD,
+                                 "chain %d: C=%g must exceed %g, the largest -eigenvalue of beta*J*K "
+                                 "(Sec. 2)", c, C, bound));
         } else {
             const double bound = beta * std::fabs(lam_min);
             if (!(C > bound * (1.0 + 1e-9) + 1e-12))
@@ -479,7 +510,11 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
                                  bound));
         }
         p.beta = beta;
-        p.bJ = beta * (h->kind == ISING_KIND_LATTICE ? cfg->Jnn : 1.0);
+        // lattice: beta*J; dense: beta (J carries the couplings); infinite:
+        // kappa = beta*J/N, the coupling of every pair
+        p.bJ = h->kind == ISING_KIND_LATTICE    ? beta * cfg->Jnn
+               : h->kind == ISING_KIND_INFINITE ? beta * cfg->Jnn / (double)N
+                                                : beta;
         p.C = C;
         p.eps = eps;
         p.hp = beta * h0;
@@ -509,7 +544,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     const size_t elem = state_elem(h);
     const size_t sbytes = (size_t)(h->dense_tc ? h->b_pad : h->n_chains) * N * elem;
     ising_status st;
-    const int nbuf = is_fp32_lattice(h) ? 3 : 2;
+    const int nbuf = is_fused(h) ? 3 : 2;
     for (int i = 0; i < nbuf; ++i)
         if ((st = dalloc(h, &h->psi[i], sbytes)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->p, sbytes)) != ISING_OK) return bail(st);
@@ -526,7 +561,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     if ((st = dalloc(h, &h->d_params, sizeof(ChainParams) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_state, sizeof(ChainState) * h->n_chains)) != ISING_OK) return bail(st);
     if ((st = dalloc(h, &h->d_err, sizeof(int))) != ISING_OK) return bail(st);
-    if (is_fp32_lattice(h) || is_dense_tc(h)) {
+    if (is_fused(h) || is_dense_tc(h)) {
         std::vector<float> tab(4 * LOG1PEXP_NODES);
         build_log1pexp_table(tab.data());
         if ((st = dalloc(h, &h->d_lpe, tab.size() * sizeof(float))) != ISING_OK) return bail(st);
@@ -661,7 +696,7 @@ ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
         h->traj += n;
         return ISING_OK;
     }
-    if (is_fp32_lattice(h)) {
+    if (is_fused(h)) {
         // trajectories per launch: keep each launch to a bounded amount of work
         const double work = (double)h->N * h->n_chains * h->sched.n_pass;
         int64_t per = (int64_t)std::max(1.0, std::floor(4.0e9 / std::max(work, 1.0)));
@@ -674,7 +709,7 @@ ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
             a.seed = seed;
             a.traj0 = (uint32_t)(h->traj + done);
             a.n_traj = (int)k;
-            CUDA_OR_FAIL(h, launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream));
+            CUDA_OR_FAIL(h, launch_fused(h, a));
             h->launches += 1;
             done += k;
         }
@@ -831,7 +866,7 @@ ising_status ising_hmc_get_chains(ising_hmc_t *h, int which, int chain0, int cou
         const int c = chain0 + k;
         const void *src;
         if (which == ISING_STATE_P_END) src = (const char *)h->p + (size_t)c * N * state_elem(h);
-        else if (is_fp32_lattice(h)) {
+        else if (is_fused(h)) {
             const int b = which == ISING_STATE_PSI ? hs[c].start : hs[c].prop;
             src = (const char *)h->psi[b] + (size_t)c * N * sizeof(float);
         } else {
@@ -900,14 +935,14 @@ ising_status ising_hmc_momenta(ising_hmc_t *h, uint64_t seed, int64_t traj, int 
         return fail(h, ISING_EINVAL, "chain range out of bounds");
     if (is_dense_tc(h)) {
         CUDA_OR_FAIL(h, dense_momenta(h->dense, seed, (uint32_t)traj, h->stream, &h->launches));
-    } else if (is_fp32_lattice(h)) {
+    } else if (is_fused(h)) {
         FusedArgs a = fused_args(h);
         a.mode = MODE_MOMENTA;
         a.seed = seed;
         a.traj0 = (uint32_t)traj;
         a.chain0 = chain0;
         a.n_chains = chain0 + count;
-        CUDA_OR_FAIL(h, launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream));
+        CUDA_OR_FAIL(h, launch_fused(h, a));
         h->launches += 1;
     } else {
         for (int c = chain0; c < chain0 + count; ++c) {
@@ -937,7 +972,7 @@ ising_status ising_hmc_get_state_native(ising_hmc_t *h, void *out) {
     if (st != ISING_OK) return st;
     const size_t cb = (size_t)h->N * state_elem(h);
     for (int c = 0; c < h->n_chains; ++c) {
-        const int b = is_fp32_lattice(h) ? hs[c].start : 0;
+        const int b = is_fused(h) ? hs[c].start : 0;
         CUDA_OR_FAIL(h, cudaMemcpyAsync((char *)out + c * cb, (const char *)h->psi[b] + c * cb, cb,
                                         cudaMemcpyDefault, h->stream));
     }

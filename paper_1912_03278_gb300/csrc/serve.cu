@@ -86,9 +86,9 @@ static ising_status sfail(ising_server *s, ising_status st, const char *fmt, ...
 static void copy_cfg(Request &r, const ising_hmc_config *c) {
     r.cfg = *c;
     r.cfg.stream = nullptr;
-    const int64_t N = c->kind == ISING_KIND_DENSE ? c->n_sites
-                                                  : (int64_t)c->L[0] * (c->dim > 1 ? c->L[1] : 1) *
-                                                        (c->dim > 2 ? c->L[2] : 1);
+    const int64_t N = c->kind != ISING_KIND_LATTICE
+                          ? c->n_sites
+                          : (int64_t)c->L[0] * (c->dim > 1 ? c->L[1] : 1) * (c->dim > 2 ? c->L[2] : 1);
     auto cp = [&](std::vector<double> &dst, const double *src, int64_t n) -> const double * {
         if (!src) return nullptr;
         dst.assign(src, src + n);

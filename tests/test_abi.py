@@ -90,8 +90,19 @@ def test_ctypes_structs_match_header():
     (dict(dim=2, L=(4, 4), beta=0.44, C=4 * 0.44), binding.ISING_ENOTPD),  # C must exceed 2d beta J
     (dict(dim=2, L=(4, 4), eps=-0.1), binding.ISING_EINVAL),
     (dict(dim=2, L=(4, 4), precision=binding.ISING_PREC_BF16), binding.ISING_EINVAL),
+    # infinite-range model: N >= 2, FP32 form only, C above the exact spectrum bound
+    (dict(kind="infinite", n_sites=1), binding.ISING_EINVAL),
+    (dict(kind="infinite", n_sites=64, precision=binding.ISING_PREC_PLAIN_FP64),
+     binding.ISING_EINVAL),
+    (dict(kind="infinite", n_sites=64, beta=1.0, C=0.99 / 64), binding.ISING_ENOTPD),
+    (dict(kind="infinite", n_sites=64, Jnn=-1.0, beta=1.0, C=0.98), binding.ISING_ENOTPD),
+    (dict(kind="crystal", n_sites=64), binding.ISING_EINVAL),
 ])
 def test_invalid_configurations_rejected(lib, kw, status):
+    if kw.get("kind") not in (None, "lattice", "dense", "infinite"):
+        with pytest.raises(ValueError):
+            binding.make_config(**kw)
+        return
     cfg, keep = binding.make_config(**kw)
     with pytest.raises(binding.IsingError) as ei:
         binding.ising_hmc_create(cfg)

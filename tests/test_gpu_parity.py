@@ -37,7 +37,7 @@ def _built():
 
 
 def _oracle_model(kind, dim, L, J, h, beta, C, Jnn=1.0):
-    if kind == "dense":
+    if kind in ("dense", "infinite"):   # infinite: J is the all-to-all matrix
         return oracle.Model(kind="dense", J=J, h=h, beta=beta, C=C)
     return oracle.Model(dim=dim, L=L, Jnn=Jnn, h=h, beta=beta, C=C)
 
@@ -51,12 +51,16 @@ def _count_near_ties(model, psi, form, seed, chain, traj):
 
 def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,), C=None,
                           eps=0.1, n_md=5, prec=FP32, integrator=0, flip_every=0, traj=3, seed=11,
-                          psi_scale=0.5, n_traj=1):
+                          psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0):
     n_chains = len(betas)
     betas = np.asarray(betas, dtype=np.float64)
-    N = int(np.prod(L[:dim])) if kind != "dense" else J.shape[0]
+    if kind == "infinite":   # the oracle sees the same model as a dense matrix
+        N = n_sites
+        J = workloads.infinite_range_couplings(N, Jnn)
+    else:
+        N = int(np.prod(L[:dim])) if kind != "dense" else J.shape[0]
     if C is None:
-        if kind == "dense":
+        if kind in ("dense", "infinite"):
             C = betas * abs(np.linalg.eigvalsh(J)[0]) + 0.1
         else:
             C = betas * 2 * dim + 0.1
@@ -66,9 +70,10 @@ def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=
     if prec == FP32:
         psi0 = psi0.astype(np.float32).astype(np.float64)
     form = oracle.FORM_FP32 if prec == FP32 else oracle.FORM_FP64
-    sim = pkg.IsingHMC(kind=kind, dim=dim, L=L, J=J, h=h, beta=betas, C=C, eps=eps_c, n_md=n_md,
-                       n_chains=n_chains, precision=prec, integrator=integrator,
-                       flip_every=flip_every)
+    sim = pkg.IsingHMC(kind=kind, dim=dim, L=L, J=None if kind == "infinite" else J,
+                       n_sites=N if kind == "infinite" else 0, Jnn=Jnn, h=h, beta=betas, C=C,
+                       eps=eps_c, n_md=n_md, n_chains=n_chains, precision=prec,
+                       integrator=integrator, flip_every=flip_every)
     try:
         sim.set_state(psi0, next_traj=traj)
         for k in range(n_traj - 1):
@@ -85,7 +90,7 @@ def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=
     finally:
         sim.close()
     for c in range(n_chains):
-        model = _oracle_model(kind, dim, L, J, h, betas[c], C[c])
+        model = _oracle_model(kind, dim, L, J, h, betas[c], C[c], Jnn)
         ch = oracle.Chain(model, form=form, seed=seed, chain=c, psi0=psi0[c])
         ch.traj = traj
         for k in range(n_traj):
