@@ -625,18 +625,25 @@ def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10
     return out
 
 
-def integrator_compare(pkg, tuned, betas, stream, L=1024, per_beta=19, therm=8, steps=4, seed=55):
+def integrator_compare(pkg, tuned, betas, stream, L=1024, per_beta=19, therm=4, steps=6, seed=55):
     """Omelyan's second-order minimum-norm integrator against KDK leapfrog at
     equal cost and equal trajectory length: 21 force evaluations each
-    (leapfrog N_md = 20 at the tuned eps, Omelyan N_md = 10 at twice it), on
-    the same chains started from the same states; acceptance and time per
-    trajectory (CUDA events)."""
+    (leapfrog N_md = 20 at each chain's tuned eps, Omelyan N_md = 10 at twice
+    it), both started from the same equilibrated configurations (the first
+    per_beta chains of every beta of the tuned handle, copied on the device);
+    acceptance, <dH> and time per trajectory (CUDA events)."""
     import torch
-    ub = np.unique(betas)
-    eps_b = {b: float(np.median(tuned._eps[betas == b])) for b in ub}
-    bsub = np.repeat(ub, per_beta)
+    n_all = pkg.binding.load().ising_hmc_n_chains(tuned.h)
+    per_block = n_all // len(np.unique(betas))
+    idx = np.concatenate([np.arange(b * per_block, b * per_block + per_beta)
+                          for b in range(n_all // per_block)])
+    full = torch.empty(n_all, L * L, device="cuda", dtype=torch.float32)
+    pkg.ising_hmc_get_state_native(tuned.h, full.data_ptr())
+    start = full[torch.as_tensor(idx, device="cuda")].contiguous()
+    del full
+    bsub = betas[idx]
     C = workloads.lattice_C(bsub, 2)
-    eps = np.array([eps_b[b] for b in bsub])
+    eps = np.asarray(tuned._eps, dtype=np.float64)[idx]
     out = {}
     for name, integ, n_md, e in (("leapfrog", pkg.ISING_INTEGRATOR_LEAPFROG, N_MD, eps),
                                  ("omelyan", pkg.ISING_INTEGRATOR_OMELYAN, N_MD // 2, 2 * eps)):
@@ -644,7 +651,8 @@ def integrator_compare(pkg, tuned, betas, stream, L=1024, per_beta=19, therm=8, 
                            precision=pkg.ISING_PREC_FP32, integrator=integ,
                            stream=stream.cuda_stream)
         try:
-            hot_start(pkg, {L: sim}, seed, bsub, C)
+            torch.cuda.synchronize()
+            pkg.ising_hmc_set_state_native(sim.h, start.data_ptr(), 0)
             sim.trajectories(therm, seed)
             sim.reset_sums()
             torch.cuda.synchronize()
@@ -656,54 +664,80 @@ def integrator_compare(pkg, tuned, betas, stream, L=1024, per_beta=19, therm=8, 
             obs = sim.observables()
             out[name] = {"n_md": n_md, "force_evaluations": n_md + 1 if integ == 0 else 2 * n_md + 1,
                          "ms_per_trajectory": e0.elapsed_time(e1) / steps,
-                         "acceptance": obs["acceptance"], "mean_dH": obs["mean_dH"]}
+                         "acceptance": obs["acceptance"], "mean_dH": obs["mean_dH"],
+                         "mean_exp_mdH": obs["mean_exp_mdH"]}
         finally:
             sim.close()
+    del start
     out["chains"] = int(len(bsub))
     out["L"] = L
+    out["start"] = "equilibrated configurations of the tuned handle; %d trajectories before " \
+                   "measuring, %d measured" % (therm, steps)
     return out
 
 
-def infinite_rate(pkg, stream, N=4096, n_chains=152 * 32, steps=4, therm=20, seed=41):
+# FP32-pipe operations per site and force evaluation of the resident
+# infinite-range kernel, counted from its source: tanh argument and tanh 12,
+# u 1, F 3, kick 1, drift 1, quad sums and double-float accumulation 4.5
+INF_OPS_PER_SITE_PASS = 22.5
+
+
+def infinite_rate(pkg, stream, steps=4, therm=20, seed=41):
     """Infinite-range (all-to-all) model of the appendix at the critical
     coupling beta*J = 1, h = 0, C = 1 (A's spectrum in [1, 2]), N_md =
-    floor(ln N), eps = 1/N_md: site-steps/s of the O(N) kernel, time per
-    trajectory (CUDA events, one launch per trajectory) and its HBM roofline
-    at 16 algorithmic bytes per site-step (psi and p read, p and psi' written)."""
+    floor(ln N), eps = 1/N_md, in both kernel variants: N = 4096 (chain
+    resident in registers; bound by the FP32 pipe) and N = 65536 (streaming;
+    bound by HBM at 16 algorithmic bytes per site-step: psi and p read, p and
+    psi' written).  Site-steps/s and time per trajectory from CUDA events,
+    one launch per trajectory."""
     import torch
-    n_md = workloads.n_md_default(N)
-    sim = pkg.IsingHMC(kind="infinite", n_sites=N, beta=1.0, C=1.0, eps=1.0 / n_md, n_md=n_md,
-                       n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
-                       stream=stream.cuda_stream)
-    try:
-        sim.trajectories(therm, seed)
-        sim.reset_sums()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        l0 = sim.launches
-        for k in range(steps):
-            ev[k][0].record(stream)
-            sim.trajectories(1, seed)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        obs = sim.observables()
+    out = {}
+    for name, N, n_chains in (("resident", 4096, 152 * 32), ("streaming", 65536, 152 * 4)):
+        n_md = workloads.n_md_default(N)
+        sim = pkg.IsingHMC(kind="infinite", n_sites=N, beta=1.0, C=1.0, eps=1.0 / n_md,
+                           n_md=n_md, n_chains=n_chains, precision=pkg.ISING_PREC_FP32,
+                           stream=stream.cuda_stream)
+        try:
+            sim.trajectories(therm, seed)
+            sim.reset_sums()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            l0 = sim.launches
+            for k in range(steps):
+                ev[k][0].record(stream)
+                sim.trajectories(1, seed)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(b) for a, b in ev]
+            obs = sim.observables()
+            launches = int(sim.launches - l0)
+        finally:
+            sim.close()
         dur = float(np.mean(ms)) / 1e3
         site_steps = float(N) * n_chains * n_md
-        peak, peak_kind = measured_peaks()
-        achieved = 16.0 * site_steps / dur / 1e9
-        return {"workload": "all-to-all N=%d, %d chains, beta*J=1, h=0, C=1, N_md=%d, eps=1/N_md"
-                            % (N, n_chains, n_md),
-                "value": site_steps / dur, "unit": UNIT, "ms_per_trajectory": dur * 1e3,
-                "launches": int(sim.launches - l0), "acceptance": obs["acceptance"],
-                "E": obs["E"], "E_err": obs["E_err"],
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        r = {"workload": "all-to-all N=%d, %d chains, beta*J=1, h=0, C=1, N_md=%d, eps=1/N_md"
+                         % (N, n_chains, n_md),
+             "value": site_steps / dur, "unit": UNIT, "ms_per_trajectory": dur * 1e3,
+             "launches": launches, "acceptance": obs["acceptance"],
+             "E": obs["E"], "E_err": obs["E_err"]}
+        if name == "resident":
+            # FP32 lanes x SM clock: 152 SMs x 128 lanes x 2.07 GHz
+            ops = INF_OPS_PER_SITE_PASS * float(N) * n_chains * (n_md + 1) / dur / 1e9
+            peak = 152 * 128 * 2.07
+            r["roofline"] = {"bound": "alu", "achieved": ops, "peak": peak, "unit": "Gop/s",
+                             "frac": ops / peak, "peak_source": "derived (FP32 lanes x max clock)",
+                             "kernel": "infinite_kernel<resident>",
+                             "ops_per_site_pass": INF_OPS_PER_SITE_PASS}
+        else:
+            peak, peak_kind = measured_peaks()
+            achieved = 16.0 * site_steps / dur / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_kind,
-                             "kernel": "infinite_kernel",
-                             "algorithmic_bytes_per_launch": 16.0 * site_steps}}
-    finally:
-        sim.close()
+                             "kernel": "infinite_kernel<streaming>",
+                             "algorithmic_bytes_per_launch": 16.0 * site_steps}
+        out[name] = r
+    return out
 
 
 def mixed_3d_rate(pkg, steps=4, seed=31):

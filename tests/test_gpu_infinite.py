@@ -29,10 +29,16 @@ def _built():
     oracle.build()
 
 
+# Variant by N (threads = min(256, quads rounded up to 32)): resident with 1,
+# 2, 4 or 8 quads per thread up to N = 8192, streaming above.
 @pytest.mark.parametrize("N", [
-    1024,   # float4 quads, four per thread
-    1001,   # scalar path, ragged last quad
-    4000,   # several quads per thread, N a multiple of 4 but not of 1024
+    1024,   # resident, 1 quad per thread, float4 quads
+    1001,   # resident, scalar loads, ragged last quad
+    2000,   # resident, 2 quads per thread, ragged thread tail
+    4000,   # resident, 4 quads per thread
+    8190,   # resident, 8 quads per thread, scalar loads
+    8193,   # streaming, scalar loads, one site in the last quad
+    9000,   # streaming, float4 quads
     2,      # smallest model
     5,      # one full quad plus a single site
 ])
@@ -70,8 +76,15 @@ def test_several_trajectories():
                           n_traj=3, traj=0)
 
 
-def test_trajectory_split_is_bitwise_invariant():
-    kw = dict(kind="infinite", n_sites=777, beta=np.array([1.0, 0.9]), h=0.02, eps=0.1, n_md=5,
+def test_sign_flip_streaming_and_several_quads_per_thread():
+    for N in (3001, 8500):
+        one_trajectory_parity(kind="infinite", n_sites=N, betas=(1.1,), h=0.02, eps=0.1, n_md=3,
+                              flip_every=1, traj=0, n_traj=2)
+
+
+@pytest.mark.parametrize("N", [777, 3001, 8500])
+def test_trajectory_split_is_bitwise_invariant(N):
+    kw = dict(kind="infinite", n_sites=N, beta=np.array([1.0, 0.9]), h=0.02, eps=0.1, n_md=5,
               n_chains=2, flip_every=2)
     a = pkg.IsingHMC(**kw)
     b = pkg.IsingHMC(**kw)
