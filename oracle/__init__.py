@@ -93,6 +93,8 @@ def _load(path=None):
         "or_brute_force": (None, [P, P]),
         "or_ring_logZ": (c_double, [c_double, c_double, c_double, c_int64]),
         "or_infinite_range_energy": (c_double, [c_double, c_double, c_double, c_int64]),
+        "or_mh_accept_prob": (ctypes.c_float, [c_double, c_double, c_double, c_int, c_int]),
+        "or_mh_checkerboard": (None, [P, c_uint64, c_uint32, c_int64, c_int64, c_int64, P, P]),
         "or_mh_run": (None, [P, c_uint64, c_int64, c_int64, P, P]),
         "or_pform_action": (c_double, [P, c_double, P]),
         "or_pform_force": (None, [P, c_double, P, P]),
@@ -391,6 +393,22 @@ def mh_run(model: Model, seed, n, n_therm=0, series=False):
     if series:
         res["abs_m"] = ser
     return res
+
+
+def mh_checkerboard(model: Model, seed, chain=0, n=1, n_therm=0, spins=None, sweep0=0):
+    """Checkerboard local Metropolis-Hastings (Sec. 4 comparator).  Returns the
+    spins (int8, starting from `spins` or all +1) and the ISING_SUM_* sums."""
+    N = model.N
+    s = np.ones(N, dtype=np.int8) if spins is None else np.ascontiguousarray(spins, dtype=np.int8).copy()
+    sums = np.zeros(10)
+    m = model.struct()
+    lib().or_mh_checkerboard(ctypes.byref(m), seed, chain, sweep0, n, n_therm, s.ctypes.data,
+                             _ptr(sums))
+    return s, sums
+
+
+def mh_accept_prob(beta, J, h, s, nb):
+    return lib().or_mh_accept_prob(beta, J, h, s, nb)
 
 
 def pform_action(model: Model, Cp, psip):

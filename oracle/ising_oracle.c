@@ -651,6 +651,76 @@ void or_mh_run(const or_model *m, uint64_t seed, int64_t n, int64_t n_therm, dou
 }
 
 /* ------------------------------------------------------------------------ */
+/* Checkerboard local Metropolis-Hastings (Sec. 4 comparator; the paper does  */
+/* not fix the order of the N single-spin proposals of a sweep).  On a        */
+/* lattice whose extents are all even, colour c = (x + y + z) mod 2 splits    */
+/* the sites so that every bond joins the two colours: proposals of one       */
+/* colour do not see each other, so one colour may be updated in any order.  */
+/* A sweep updates colour 0, then colour 1, each in site order.  Site i of    */
+/* colour c in sweep k draws u = u23(word (j mod 4) of Philox(j div 4,        */
+/* 2k + c, chain, MH)) with j = i div 2 (the two sites 2j, 2j+1 have          */
+/* different colours), and flips iff u < p in FP32, where p =                 */
+/* min(1, exp(-2 beta s_i (J nb_i + h))) is formed in FP64 (nb_i the          */
+/* neighbour spin sum, no contraction) and rounded to FP32.                   */
+/* After each sweep k >= n_therm, with M = sum_i s_i and B = sum over bonds   */
+/* s_i s_j: m = M/N, E = beta (-J B - h M) / N, and the fraction of flipped   */
+/* sites, summed in the order of ising_hmc.h's ISING_SUM_* (10 values).       */
+/* ------------------------------------------------------------------------ */
+float or_mh_accept_prob(double beta, double J, double h, int s, int nb) {
+    double f = J * (double)nb + h;
+    double x = -2.0 * beta * (double)s * f;
+    double p = x >= 0.0 ? 1.0 : exp(x);
+    return (float)p;
+}
+
+void or_mh_checkerboard(const or_model *m, uint64_t seed, uint32_t chain, int64_t sweep0,
+                        int64_t n, int64_t n_therm, int8_t *s, double *sums) {
+    int64_t N = or_num_sites(m);
+    int nn = 2 * m->dim;
+    int64_t *nbr = (int64_t *)malloc(sizeof(int64_t) * N * nn);
+    or_neighbors(m, nbr);
+    int L0 = m->L[0], L1 = m->dim > 1 ? m->L[1] : 1;
+    for (int64_t k = sweep0; k < sweep0 + n; ++k) {
+        int64_t flips = 0;
+        for (int c = 0; c < 2; ++c) {
+            for (int64_t i = 0; i < N; ++i) {
+                int64_t x = i % L0, y = (i / L0) % L1, z = i / ((int64_t)L0 * L1);
+                if ((int)((x + y + z) & 1) != c) continue;
+                int nb = 0;
+                for (int d = 0; d < nn; ++d) nb += s[nbr[i * nn + d]];
+                int64_t j = i / 2;
+                uint32_t w[4];
+                draw(seed, (uint32_t)(j / 4), (uint32_t)(2 * k + c), chain, OR_PURPOSE_MH, w);
+                float u = (float)or_u23(w[j % 4]);
+                if (u < or_mh_accept_prob(m->beta, m->Jnn, m->h0, s[i], nb)) {
+                    s[i] = (int8_t)(-s[i]);
+                    flips += 1;
+                }
+            }
+        }
+        if (k >= n_therm) {
+            int64_t M = 0, B = 0;
+            for (int64_t i = 0; i < N; ++i) {
+                M += s[i];
+                /* forward neighbours (+x, +y, +z): every bond once */
+                for (int d = 0; d < m->dim; ++d) B += s[i] * s[nbr[i * nn + 2 * d]];
+            }
+            double mm = (double)M / (double)N;
+            double E = m->beta * (-m->Jnn * (double)B - m->h0 * (double)M) / (double)N;
+            sums[0] += 1.0;
+            sums[1] += (double)flips / (double)N;
+            sums[2] += mm;
+            sums[3] += mm * mm;
+            sums[4] += E;
+            sums[5] += E * E;
+            sums[6] += fabs(mm);
+            sums[7] += mm * mm;
+        }
+    }
+    free(nbr);
+}
+
+/* ------------------------------------------------------------------------ */
 /* The paper's own parametrisation (P form).  K~ = K + C_p 1, J' = beta J,   */
 /* h' = beta h (Sec. 2); action and forces as printed in Sec. 3:             */
 /*  S_p = 1/2 psi.K~ psi - psi.h'/sqrt(J') - sum log cosh(sqrt(J') (K~ psi)_i)   */

@@ -142,6 +142,14 @@ double or_infinite_range_energy(double beta, double J, double h, int64_t N);
  * out: n_meas, sum|m|, sum|m|^2, sum E, sum E^2, acceptance. */
 void or_mh_run(const or_model *m, uint64_t seed, int64_t n, int64_t n_therm, double *out,
                double *series_absm);
+/* Checkerboard form (every lattice extent even): colour 0 then colour 1 per
+ * sweep, Philox draws per (site pair, half-sweep, chain), the decision
+ * u < p in FP32.  s: N spins (+-1), updated in place; sweeps sweep0 ..
+ * sweep0+n-1; sums (10 values, ising_hmc.h ISING_SUM_* order) accumulate the
+ * sweeps >= n_therm.  Pinned by brute force, beta = 0 and field limits. */
+float or_mh_accept_prob(double beta, double J, double h, int s, int nb);
+void or_mh_checkerboard(const or_model *m, uint64_t seed, uint32_t chain, int64_t sweep0,
+                        int64_t n, int64_t n_therm, int8_t *s, double *sums);
 
 /* ---- the paper's own parametrisation (P form, Sec. 2-3) ---- */
 /* A_p = J'*(K + C_p*1) with J' = beta*J; S_p and its force as printed in

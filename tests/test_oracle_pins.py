@@ -365,6 +365,73 @@ def test_metropolis_hastings_matches_brute_force():
     assert within(E, bf["E"], 4 * math.sqrt(varE / n))  # loose: tau_E small
 
 
+# --------------------------------------- checkerboard Metropolis-Hastings ----
+def test_checkerboard_mh_beta_zero_flips_every_spin():
+    """beta = 0: every proposal has p = 1, so one sweep negates every spin."""
+    model = oracle.Model(dim=2, L=(6, 4), beta=0.0, C=1.0)
+    s0 = np.where(workloads.rng(4).random(24) < 0.5, 1, -1).astype(np.int8)
+    s, sums = oracle.mh_checkerboard(model, seed=3, n=1, spins=s0)
+    assert np.array_equal(s, -s0)
+    assert sums[1] == 1.0   # flipped fraction
+
+
+def test_checkerboard_mh_strong_field_aligns_in_one_sweep():
+    """h = 50: from all -1 colour 0 flips (its neighbours are all -1), then colour 1
+    (its neighbours now all +1); from all +1 nothing flips."""
+    model = oracle.Model(dim=3, L=(4, 4, 4), beta=1.0, h=50.0, C=7.0)
+    s, _ = oracle.mh_checkerboard(model, seed=1, n=1, spins=-np.ones(64, np.int8))
+    assert np.all(s == 1)
+    s, sums = oracle.mh_checkerboard(model, seed=1, n=3, spins=np.ones(64, np.int8))
+    assert np.all(s == 1) and sums[1] == 0.0
+
+
+def test_checkerboard_mh_colour_order_does_not_matter():
+    """The same sweep with each colour's sites visited in reverse order (a plain
+    loop here, from the oracle's Philox and acceptance probability) gives the
+    same spins: the property that lets a GPU update a colour in parallel."""
+    L0, L1, beta, J, h, seed = 6, 4, 0.5, 1.0, 0.1, 9
+    model = oracle.Model(dim=2, L=(L0, L1), beta=beta, h=h)
+    nbr = oracle.neighbors(model)
+    s0 = np.where(workloads.rng(8).random(L0 * L1) < 0.5, 1, -1).astype(np.int8)
+    s = s0.copy()
+    for k in range(3):
+        for c in (0, 1):
+            for i in reversed(range(L0 * L1)):
+                if ((i % L0) + (i // L0)) % 2 != c:
+                    continue
+                nb = int(sum(s[j] for j in nbr[i]))
+                j = i // 2
+                w = oracle.philox((j // 4, 2 * k + c, 0, oracle.PURPOSE_MH),
+                                  (seed & 0xffffffff, seed >> 32))
+                u = np.float32(oracle.u23(w[j % 4]))
+                if u < np.float32(oracle.mh_accept_prob(beta, J, h, int(s[i]), nb)):
+                    s[i] = -s[i]
+    ref, _ = oracle.mh_checkerboard(model, seed=seed, n=3, spins=s0)
+    assert np.array_equal(s, ref)
+
+
+@pytest.mark.parametrize("dim,L,beta,h", [(2, (4, 4), 0.44, 0.05), (2, (4, 4), 0.3, 0.0),
+                                         (1, (12,), 0.7, 0.1)])
+def test_checkerboard_mh_matches_brute_force(dim, L, beta, h):
+    """64 independent chains (chain index in the Philox counter), 2500 sweeps
+    each after 200 of thermalisation: m, |m| and E within 3 standard errors of
+    the exact sums over all spin states.  (On a ring at h = 0 local Metropolis
+    is not ergodic -- a flip between unlike neighbours costs nothing and is
+    always taken -- in site order as in checkerboard order, so 1D runs with a
+    field.)"""
+    model = oracle.Model(dim=dim, L=L, beta=beta, h=h)
+    bf = oracle.brute_force(model)
+    per = {k: [] for k in ("m", "abs_m", "E")}
+    for c in range(64):
+        _, sums = oracle.mh_checkerboard(model, seed=11, chain=c, n=2700, n_therm=200)
+        per["m"].append(sums[2] / sums[0])
+        per["E"].append(sums[4] / sums[0])
+        per["abs_m"].append(sums[6] / sums[0])
+    for key, v in per.items():
+        v = np.asarray(v)
+        assert within(v.mean(), bf[key], v.std(ddof=1) / math.sqrt(len(v))), (key, v.mean(), bf[key])
+
+
 # ---------------------------------------- the paper's own parametrisation ----
 def test_pform_is_the_ns_form_under_the_map():
     """P form (Sec. 2-3 as printed) vs NS form: with C = J' C_p, eps_ns = eps_p/sqrt(J'),
