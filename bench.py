@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-integrators", action="store_true")
     ap.add_argument("--no-infinite", action="store_true")
+    ap.add_argument("--no-mh", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -460,6 +461,8 @@ def run_ours(args):
             line["dense"] = dense_rate(pkg, stream)
         if not args.no_infinite:
             line["infinite"] = infinite_rate(pkg, stream)
+        if not args.no_mh:
+            line["mh"] = mh_rate(pkg, stream, big, betas, float(np.mean(big_ms)))
         if not args.no_serve:
             line["serve"] = serve_run(pkg, args.serve_seconds)
         if not args.no_cpu:
@@ -738,6 +741,42 @@ def infinite_rate(pkg, stream, steps=4, therm=20, seed=41):
                              "algorithmic_bytes_per_launch": 16.0 * site_steps}
         out[name] = r
     return out
+
+
+def mh_rate(pkg, stream, L, betas, hmc_ms, steps=4, warm=2, seed=61):
+    """The Sec. 4 comparator on the same batch as the headline step (2D L x L,
+    the same chains and betas, h = 0): checkerboard Metropolis-Hastings sweeps
+    timed with CUDA events, and the cost ratio T_HMC / T_MH (the paper reports
+    ~4 N_step for its implementation).  HBM roofline at 2 algorithmic bytes
+    per site and sweep (each int8 spin read and written once)."""
+    import torch
+    n = len(betas)
+    sim = pkg.IsingMH(dim=2, L=(L, L), beta=betas, n_chains=n, stream=stream.cuda_stream)
+    try:
+        sim.sweeps(warm, seed)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = sim.launches
+        e0.record(stream)
+        sim.sweeps(steps, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        launches = int(sim.launches - l0)
+        acc = sim.observables()["acceptance"]
+    finally:
+        sim.close()
+    sites = float(L) * L * n
+    peak, peak_kind = measured_peaks()
+    achieved = 2.0 * sites / (ms / 1e3) / 1e9
+    return {"workload": "2D L=%d, %d chains (16 betas in [0.38, 0.50]), J=1, h=0, checkerboard, "
+                        "spins start +1, %d warm-up sweeps" % (L, n, warm),
+            "value": sites / (ms / 1e3), "unit": "site-updates/s", "ms_per_sweep": ms,
+            "launches_per_sweep": launches / steps, "flip_fraction": acc,
+            "t_hmc_over_t_mh": hmc_ms / ms, "n_step": N_MD, "paper_4_n_step": 4 * N_MD,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "kernel": "mh_colour_kernel", "algorithmic_bytes_per_sweep": 2.0 * sites}}
 
 
 def mixed_3d_rate(pkg, steps=4, seed=31):

@@ -341,6 +341,47 @@ void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);
 
+/* ---- Local Metropolis-Hastings comparator (Sec. 4) ----------------------
+ * The paper's reference algorithm (single-spin-flip Metropolis sweeps on the
+ * spins), run on the GPU so that the cost of an HMC trajectory can be set
+ * against the cost of a sweep.  A sweep updates colour 0, then colour 1
+ * (c = (x + y + z) mod 2; every extent must be even so that each bond joins
+ * the two colours and a colour's sites can be updated in parallel).  Site i of
+ * colour c in sweep k draws u = u23(word (j mod 4) of Philox(j / 4, 2k + c,
+ * chain, 5)), j = i / 2, and flips iff u < p in FP32, where
+ * p = min(1, exp(-2 beta s_i (J nb_i + h))) (nb_i the neighbour spin sum) is
+ * formed in FP64 on the host and rounded to FP32.  Spins start all +1 (int8,
+ * chain-major).  After each sweep with index >= n_therm the per-chain sums
+ * (ISING_SUM_* order) take m = M/N, |m|, beta*eps = beta (-J B - h M) / N
+ * (M the spin sum, B the bond sum) and, under ISING_SUM_NACC, the fraction of
+ * spins flipped in the sweep; ISING_SUM_DH and ISING_SUM_EXPMDH stay 0.  The
+ * same conventions as the HMC calls apply (status codes, stream, ownership). */
+typedef struct ising_mh ising_mh_t;
+
+/* cfg: kind LATTICE, dim 1..3, L (each even and >= 4), Jnn, h0 or h0_chain (a
+ * per-site h must be NULL), beta or beta_chain (>= 0), n_chains (1..65535),
+ * n_therm, stream; every other field is ignored.  Errors: EINVAL, ENOMEM,
+ * ECUDA (message from ising_mh_last_error(NULL)). */
+ising_status ising_mh_create(const ising_hmc_config *cfg, ising_mh_t **out);
+/* n sweeps of every chain (asynchronous); the sweep counter persists, so
+ * sweeps(a) then sweeps(b) equals sweeps(a + b) bit for bit.  Errors: EINVAL, ECUDA. */
+ising_status ising_mh_sweeps(ising_mh_t *h, int64_t n, uint64_t seed);
+/* Chain-averaged m, |m|, E and the flipped fraction (as acceptance), errors
+ * as in ising_hmc_observables.  Synchronises. */
+ising_status ising_mh_observables(ising_mh_t *h, ising_obs *out);
+/* Per-chain sums, ISING_NSUMS doubles per chain.  Synchronises. */
+ising_status ising_mh_chain_sums(ising_mh_t *h, double *out);
+/* Spins of every chain to host memory (n_chains * N int8 values, +-1). */
+ising_status ising_mh_get_spins(ising_mh_t *h, int8_t *out);
+/* Spins from host memory (+-1 each, else EINVAL); the next sweep has index next_sweep. */
+ising_status ising_mh_set_spins(ising_mh_t *h, const int8_t *in, int64_t next_sweep);
+ising_status ising_mh_sync(ising_mh_t *h);
+int64_t ising_mh_sweep_index(const ising_mh_t *h);
+int64_t ising_mh_launch_count(const ising_mh_t *h);
+/* Last error message of h, or of the failed ising_mh_create of this thread when h is NULL. */
+const char *ising_mh_last_error(const ising_mh_t *h);
+void ising_mh_destroy(ising_mh_t *h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,6 +117,17 @@ def load(path: str | None = None):
                                              c_int, P, P, P, P]),
         "ising_hmc_energy_noalloc_error": (c_char_p, []),
         "ising_hmc_destroy": (None, [P]),
+        "ising_mh_create": (c_int, [P, P]),
+        "ising_mh_sweeps": (c_int, [P, c_int64, c_uint64]),
+        "ising_mh_observables": (c_int, [P, P]),
+        "ising_mh_chain_sums": (c_int, [P, P]),
+        "ising_mh_get_spins": (c_int, [P, P]),
+        "ising_mh_set_spins": (c_int, [P, P, c_int64]),
+        "ising_mh_sync": (c_int, [P]),
+        "ising_mh_sweep_index": (c_int64, [P]),
+        "ising_mh_launch_count": (c_int64, [P]),
+        "ising_mh_last_error": (c_char_p, [P]),
+        "ising_mh_destroy": (None, [P]),
         "ising_hmc_last_error": (c_char_p, [P]),
         "ising_hmc_last_create_error": (c_char_p, []),
     }
@@ -395,6 +406,126 @@ def ising_group_last_error(g) -> str:
 def ising_group_destroy(g):
     if g:
         load().ising_group_destroy(g)
+
+
+# ------------------------------------------ local Metropolis-Hastings ----
+def _check_mh(h, st):
+    if st != ISING_OK:
+        msg = load().ising_mh_last_error(h)
+        raise IsingError(st, (msg or b"").decode())
+
+
+def ising_mh_create(cfg: ising_hmc_config) -> int:
+    out = c_void_p()
+    _check_mh(None, load().ising_mh_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def ising_mh_sweeps(h, n, seed):
+    _check_mh(h, load().ising_mh_sweeps(h, int(n), int(seed)))
+
+
+def ising_mh_observables(h) -> dict:
+    o = ising_obs()
+    _check_mh(h, load().ising_mh_observables(h, ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in ising_obs._fields_}
+
+
+def ising_mh_chain_sums(h, n_chains) -> np.ndarray:
+    out = np.zeros((n_chains, ISING_NSUMS))
+    _check_mh(h, load().ising_mh_chain_sums(h, out.ctypes.data))
+    return out
+
+
+def ising_mh_get_spins(h, n_chains, N) -> np.ndarray:
+    out = np.zeros((n_chains, N), dtype=np.int8)
+    _check_mh(h, load().ising_mh_get_spins(h, out.ctypes.data))
+    return out
+
+
+def ising_mh_set_spins(h, spins, next_sweep=0):
+    a = np.ascontiguousarray(spins, dtype=np.int8)
+    _check_mh(h, load().ising_mh_set_spins(h, a.ctypes.data, int(next_sweep)))
+
+
+def ising_mh_sync(h):
+    _check_mh(h, load().ising_mh_sync(h))
+
+
+def ising_mh_sweep_index(h) -> int:
+    return load().ising_mh_sweep_index(h)
+
+
+def ising_mh_launch_count(h) -> int:
+    return load().ising_mh_launch_count(h)
+
+
+def ising_mh_last_error(h) -> str:
+    return (load().ising_mh_last_error(h) or b"").decode()
+
+
+def ising_mh_destroy(h):
+    load().ising_mh_destroy(h)
+
+
+class IsingMH:
+    """The local Metropolis-Hastings comparator (Sec. 4) on the GPU: checkerboard
+    sweeps of many lattice chains.  IsingMH(**make_config kwargs); the lattice
+    kind, dim, L (even extents), Jnn, scalar h, beta (per chain allowed),
+    n_chains, n_therm and stream are used."""
+
+    def __init__(self, **kw):
+        cfg, keep = make_config(**kw)
+        self.h = ising_mh_create(cfg)
+        del keep
+        self.n_chains = int(kw.get("n_chains", 1))
+        L = tuple(kw.get("L", (4, 4)))[: kw.get("dim", 2)]
+        self.N = int(np.prod(L))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def close(self):
+        if self.h:
+            ising_mh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweeps(self, n, seed):
+        ising_mh_sweeps(self.h, n, seed)
+
+    def observables(self) -> dict:
+        return ising_mh_observables(self.h)
+
+    def chain_sums(self) -> np.ndarray:
+        return ising_mh_chain_sums(self.h, self.n_chains)
+
+    def spins(self) -> np.ndarray:
+        return ising_mh_get_spins(self.h, self.n_chains, self.N)
+
+    def set_spins(self, spins, next_sweep=0):
+        if np.size(spins) != self.n_chains * self.N:
+            raise ValueError("need n_chains * N spins")
+        ising_mh_set_spins(self.h, spins, next_sweep)
+
+    def sync(self):
+        ising_mh_sync(self.h)
+
+    @property
+    def sweep_index(self):
+        return ising_mh_sweep_index(self.h)
+
+    @property
+    def launches(self):
+        return ising_mh_launch_count(self.h)
 
 
 class IsingGroup:

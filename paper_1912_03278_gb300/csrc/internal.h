@@ -93,6 +93,9 @@ cudaError_t launch_infinite(const FusedArgs &a, const Schedule &sched, cudaStrea
 cudaError_t infinite_node(const FusedArgs &a, cudaKernelNodeParams *np, void **args);
 int infinite_threads(int64_t N);
 
+// Chain-averaged observables from per-chain sums (ISING_NSUMS per chain).
+void obs_from_sums(const double *sums, int n_chains, int64_t n_traj, ising_obs *out);
+
 cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s);
 // BF16 tensor-core GEMM D[n*M + m] = sum_k A[m][k] B[n][k]; M, N multiples of
 // 128, K a multiple of 64; *err gets bit 0 if a bounded wait ran out.

@@ -356,6 +356,63 @@ static ising_status upload_params(ising_hmc *h) {
                : fail(h, ISING_ECUDA, "parameter upload failed");
 }
 
+// Chain-averaged observables from per-chain sums (ISING_NSUMS per chain):
+// standard errors of the per-chain means for several chains, the naive
+// sigma/sqrt(n) of the single chain otherwise.
+void ihmc::obs_from_sums(const double *sums, int C, int64_t n_traj, ising_obs *out) {
+    std::memset(out, 0, sizeof(*out));
+    double nmeas = 0, nacc = 0, sdh = 0, sexp = 0;
+    std::vector<double> cm(C), ca(C), ce(C), cx(C);
+    double vm = 0, va = 0, ve = 0;
+    for (int c = 0; c < C; ++c) {
+        const double *s = sums + (size_t)c * ISING_NSUMS;
+        const double n = s[ISING_SUM_NMEAS];
+        nmeas += n;
+        nacc += s[ISING_SUM_NACC];
+        sdh += s[ISING_SUM_DH];
+        sexp += s[ISING_SUM_EXPMDH];
+        const double inv = n > 0 ? 1.0 / n : 0.0;
+        cm[c] = s[ISING_SUM_M] * inv;
+        ca[c] = s[ISING_SUM_ABSM] * inv;
+        ce[c] = s[ISING_SUM_E] * inv;
+        cx[c] = s[ISING_SUM_EXPMDH] * inv;
+        if (C == 1 && n > 1) {
+            vm = (s[ISING_SUM_M2] * inv - cm[c] * cm[c]) / (n - 1);
+            va = (s[ISING_SUM_ABSM2] * inv - ca[c] * ca[c]) / (n - 1);
+            ve = (s[ISING_SUM_E2] * inv - ce[c] * ce[c]) / (n - 1);
+        }
+    }
+    auto mean = [&](const std::vector<double> &v) {
+        double s = 0;
+        for (double x : v) s += x;
+        return s / (double)v.size();
+    };
+    auto sem = [&](const std::vector<double> &v, double mu) {
+        if (v.size() < 2) return 0.0;
+        double s = 0;
+        for (double x : v) s += (x - mu) * (x - mu);
+        return std::sqrt(s / ((double)v.size() - 1) / (double)v.size());
+    };
+    out->m = mean(cm);
+    out->abs_m = mean(ca);
+    out->E = mean(ce);
+    out->mean_exp_mdH = nmeas > 0 ? sexp / nmeas : 0;
+    if (C > 1) {
+        out->m_err = sem(cm, out->m);
+        out->abs_m_err = sem(ca, out->abs_m);
+        out->E_err = sem(ce, out->E);
+        out->exp_mdH_err = sem(cx, mean(cx));
+    } else {
+        out->m_err = std::sqrt(std::max(vm, 0.0));
+        out->abs_m_err = std::sqrt(std::max(va, 0.0));
+        out->E_err = std::sqrt(std::max(ve, 0.0));
+    }
+    out->acceptance = nmeas > 0 ? nacc / nmeas : 0;
+    out->mean_dH = nmeas > 0 ? sdh / nmeas : 0;
+    out->n_traj = n_traj;
+    out->n_meas = (int64_t)nmeas;
+}
+
 extern "C" {
 
 const char *ising_hmc_last_create_error(void) { return g_create_err; }
@@ -796,58 +853,10 @@ ising_status ising_hmc_observables(ising_hmc_t *h, ising_obs *out) {
     std::vector<ChainState> hs;
     ising_status st = fetch_states(h, hs);
     if (st != ISING_OK) return st;
-    std::memset(out, 0, sizeof(*out));
-    const int C = h->n_chains;
-    double nmeas = 0, nacc = 0, sdh = 0, sexp = 0;
-    std::vector<double> cm(C), ca(C), ce(C), cx(C);
-    double vm = 0, va = 0, ve = 0;
-    for (int c = 0; c < C; ++c) {
-        const double *s = hs[c].sums;
-        const double n = s[ISING_SUM_NMEAS];
-        nmeas += n;
-        nacc += s[ISING_SUM_NACC];
-        sdh += s[ISING_SUM_DH];
-        sexp += s[ISING_SUM_EXPMDH];
-        const double inv = n > 0 ? 1.0 / n : 0.0;
-        cm[c] = s[ISING_SUM_M] * inv;
-        ca[c] = s[ISING_SUM_ABSM] * inv;
-        ce[c] = s[ISING_SUM_E] * inv;
-        cx[c] = s[ISING_SUM_EXPMDH] * inv;
-        if (C == 1 && n > 1) {
-            vm = (s[ISING_SUM_M2] * inv - cm[c] * cm[c]) / (n - 1);
-            va = (s[ISING_SUM_ABSM2] * inv - ca[c] * ca[c]) / (n - 1);
-            ve = (s[ISING_SUM_E2] * inv - ce[c] * ce[c]) / (n - 1);
-        }
-    }
-    auto mean = [&](const std::vector<double> &v) {
-        double s = 0;
-        for (double x : v) s += x;
-        return s / (double)v.size();
-    };
-    auto sem = [&](const std::vector<double> &v, double mu) {
-        if (v.size() < 2) return 0.0;
-        double s = 0;
-        for (double x : v) s += (x - mu) * (x - mu);
-        return std::sqrt(s / ((double)v.size() - 1) / (double)v.size());
-    };
-    out->m = mean(cm);
-    out->abs_m = mean(ca);
-    out->E = mean(ce);
-    out->mean_exp_mdH = nmeas > 0 ? sexp / nmeas : 0;
-    if (C > 1) {
-        out->m_err = sem(cm, out->m);
-        out->abs_m_err = sem(ca, out->abs_m);
-        out->E_err = sem(ce, out->E);
-        out->exp_mdH_err = sem(cx, mean(cx));
-    } else {
-        out->m_err = std::sqrt(std::max(vm, 0.0));
-        out->abs_m_err = std::sqrt(std::max(va, 0.0));
-        out->E_err = std::sqrt(std::max(ve, 0.0));
-    }
-    out->acceptance = nmeas > 0 ? nacc / nmeas : 0;
-    out->mean_dH = nmeas > 0 ? sdh / nmeas : 0;
-    out->n_traj = h->traj;
-    out->n_meas = (int64_t)nmeas;
+    std::vector<double> sums((size_t)h->n_chains * ISING_NSUMS);
+    for (int c = 0; c < h->n_chains; ++c)
+        std::memcpy(&sums[(size_t)c * ISING_NSUMS], hs[c].sums, sizeof(double) * ISING_NSUMS);
+    obs_from_sums(sums.data(), h->n_chains, h->traj, out);
     return ISING_OK;
 }
 

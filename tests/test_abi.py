@@ -110,6 +110,23 @@ def test_invalid_configurations_rejected(lib, kw, status):
     assert len(binding.load().ising_hmc_last_create_error()) > 0
 
 
+@pytest.mark.parametrize("kw", [
+    dict(dim=2, L=(5, 4)),                   # odd extent: no checkerboard
+    dict(dim=2, L=(2, 4)),                   # extent below 4
+    dict(dim=4, L=(4, 4)),
+    dict(dim=2, L=(4, 4), n_chains=0),
+    dict(dim=2, L=(4, 4), n_chains=70000),
+    dict(dim=2, L=(4, 4), h=np.zeros(16)),    # per-site field
+    dict(dim=2, L=(4, 4), beta=-0.1),
+])
+def test_mh_invalid_configurations_rejected(lib, kw):
+    cfg, keep = binding.make_config(**kw)
+    out = ctypes.c_void_p()
+    st = binding.load().ising_mh_create(ctypes.byref(cfg), ctypes.byref(out))
+    assert st == binding.ISING_EINVAL and not out.value
+    assert len(binding.load().ising_mh_last_error(None)) > 0
+
+
 def test_dense_not_positive_definite_rejected(lib):
     import workloads
     J = workloads.dense_couplings(40, seed=3)
