@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-integrators", action="store_true")
     ap.add_argument("--no-infinite", action="store_true")
     ap.add_argument("--no-mh", action="store_true")
+    ap.add_argument("--no-autocorr", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
@@ -463,6 +464,8 @@ def run_ours(args):
             line["infinite"] = infinite_rate(pkg, stream)
         if not args.no_mh:
             line["mh"] = mh_rate(pkg, stream, big, betas, float(np.mean(big_ms)))
+        if not args.no_autocorr:
+            line["autocorr"] = autocorr_run(pkg, stream)
         if not args.no_serve:
             line["serve"] = serve_run(pkg, args.serve_seconds)
         if not args.no_cpu:
@@ -777,6 +780,51 @@ def mh_rate(pkg, stream, L, betas, hmc_ms, steps=4, warm=2, seed=61):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "kernel": "mh_colour_kernel", "algorithmic_bytes_per_sweep": 2.0 * sites}}
+
+
+def _tau_abs_m(pkg, stream, L, C_over_beta, n_chains, therm, n, seed):
+    """tau_int of |m| (Gamma method over the chains' device-recorded series) of
+    the 2D lattice at the critical coupling, N_md = floor(ln N), unit
+    trajectory length in the paper's units (eps = 1 / (N_md sqrt(beta)))."""
+    beta = math.log(1 + math.sqrt(2)) / 2
+    n_md = workloads.n_md_default(L * L)
+    sim = pkg.IsingHMC(dim=2, L=(L, L), beta=beta, C=C_over_beta * beta,
+                       eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md, n_chains=n_chains,
+                       stream=stream.cuda_stream)
+    try:
+        sim.trajectories(therm, seed)
+        sim.series_enable(n)
+        sim.trajectories(n, seed)
+        ser = sim.series()
+        acc = sim.observables()["acceptance"]
+    finally:
+        sim.close()
+    r = pkg.binding.ising_gamma_method(ser[:, :, 2])
+    return {"tau_int": r["tau_int"], "tau_err": r["tau_err"], "abs_m": r["mean"],
+            "abs_m_err": r["err"], "acceptance": acc, "n_md": n_md}
+
+
+def autocorr_run(pkg, stream, n_chains=128, therm=200, n=1500, seed=71):
+    """Sec. 4, Fig. 2 and Fig. 3 on synthetic chains: tau_int of |m| at beta_c
+    for L = 8, 16, 32 (C = 5 beta, i.e. the paper's C_p = n + 1 with n = 4
+    neighbours) and the dynamic exponent from a log-log fit; and a scan of the
+    shift at L = 15, C_p - n in {0.1, 0.5, 1, 2, 4}."""
+    import time as _t
+    t0 = _t.perf_counter()
+    sizes = {}
+    for L in (8, 16, 32):
+        sizes[str(L)] = _tau_abs_m(pkg, stream, L, 5.0, n_chains, therm, n, seed)
+    Ls = np.array([8.0, 16.0, 32.0])
+    taus = np.array([sizes[str(int(L))]["tau_int"] for L in Ls])
+    z = float(np.polyfit(np.log(Ls), np.log(taus), 1)[0])
+    scan = {}
+    for dc in (0.1, 0.5, 1.0, 2.0, 4.0):
+        scan[str(dc)] = _tau_abs_m(pkg, stream, 15, 4.0 + dc, n_chains, therm, n, seed)
+    best = min(scan, key=lambda k: scan[k]["tau_int"])
+    return {"workload": "2D periodic lattice at beta_c, h = 0, %d chains, %d trajectories "
+                        "recorded after %d" % (n_chains, n, therm),
+            "tau_abs_m_by_L": sizes, "z_fit": z, "c_scan_L15": scan, "c_p_minus_n_best": float(best),
+            "seconds": _t.perf_counter() - t0}
 
 
 def mixed_3d_rate(pkg, steps=4, seed=31):

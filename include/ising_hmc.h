@@ -341,6 +341,28 @@ void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);
 
+/* ---- Per-trajectory series and autocorrelation (Sec. 4) -----------------
+ * From the next trajectory on, record each chain's m, beta*eps and |m| (the
+ * values the measurement step adds to the sums; recorded for every
+ * trajectory, thermalisation included) for up to `capacity` trajectories
+ * (3 doubles per chain and trajectory in device memory).  While recording,
+ * ising_hmc_trajectories runs one trajectory per launch followed by a record
+ * launch (results are unchanged); groups and servers do not record.
+ * capacity 0 frees the buffer.  Synchronises.  Errors: EINVAL, ENOMEM. */
+ising_status ising_hmc_series_enable(ising_hmc_t *h, int64_t capacity);
+/* The recorded series into out[(c * n + t) * 3 + k] (k = 0 m, 1 beta*eps,
+ * 2 |m|), n = *n_out recorded trajectories; with out NULL only *n_out is
+ * set.  Synchronises.  Errors: EINVAL, ECUDA. */
+ising_status ising_hmc_series_get(ising_hmc_t *h, double *out, int64_t *n_out);
+/* Gamma method (U. Wolff, Comput. Phys. Commun. 156 (2004) 143) on n_rep
+ * replicas of length n (x[r * n + t], host memory): the autocorrelation
+ * function about the global mean, tau_int with automatic windowing (factor
+ * S, 1.5 is customary) and the bias correction of the mean.  out[0] mean,
+ * out[1] its error, out[2] tau_int, out[3] the error of tau_int, out[4] the
+ * window W.  Host-only (no device work).  Errors: EINVAL (n < 2, n_rep < 1,
+ * S <= 0; message from ising_hmc_last_create_error()). */
+ising_status ising_gamma_method(const double *x, int64_t n, int n_rep, double S, double *out);
+
 /* ---- Local Metropolis-Hastings comparator (Sec. 4) ----------------------
  * The paper's reference algorithm (single-spin-flip Metropolis sweeps on the
  * spins), run on the GPU so that the cost of an HMC trajectory can be set

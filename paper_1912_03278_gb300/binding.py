@@ -117,6 +117,9 @@ def load(path: str | None = None):
                                              c_int, P, P, P, P]),
         "ising_hmc_energy_noalloc_error": (c_char_p, []),
         "ising_hmc_destroy": (None, [P]),
+        "ising_hmc_series_enable": (c_int, [P, c_int64]),
+        "ising_hmc_series_get": (c_int, [P, P, P]),
+        "ising_gamma_method": (c_int, [P, c_int64, c_int, c_double, P]),
         "ising_mh_create": (c_int, [P, P]),
         "ising_mh_sweeps": (c_int, [P, c_int64, c_uint64]),
         "ising_mh_observables": (c_int, [P, P]),
@@ -406,6 +409,31 @@ def ising_group_last_error(g) -> str:
 def ising_group_destroy(g):
     if g:
         load().ising_group_destroy(g)
+
+
+# --------------------------------------- series and autocorrelation ----
+def ising_hmc_series_enable(h, capacity):
+    _check(h, load().ising_hmc_series_enable(h, int(capacity)))
+
+
+def ising_hmc_series_get(h) -> np.ndarray:
+    """Recorded series as an array (n_chains, n, 3): m, beta*eps, |m|."""
+    n = ctypes.c_int64(0)
+    _check(h, load().ising_hmc_series_get(h, None, ctypes.byref(n)))
+    nc = load().ising_hmc_n_chains(h)
+    out = np.zeros((nc, n.value, 3))
+    if n.value:
+        _check(h, load().ising_hmc_series_get(h, out.ctypes.data, ctypes.byref(n)))
+    return out
+
+
+def ising_gamma_method(x, S=1.5) -> dict:
+    """Gamma method on a series (1D) or replicas (2D array, one row per replica)."""
+    a = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    out = np.zeros(5)
+    _check(None, load().ising_gamma_method(a.ctypes.data, a.shape[1], a.shape[0], float(S),
+                                           out.ctypes.data))
+    return dict(mean=out[0], err=out[1], tau_int=out[2], tau_err=out[3], window=int(out[4]))
 
 
 # ------------------------------------------ local Metropolis-Hastings ----
@@ -773,6 +801,12 @@ class IsingHMC:
 
     def sync(self):
         ising_hmc_sync(self.h)
+
+    def series_enable(self, capacity):
+        ising_hmc_series_enable(self.h, capacity)
+
+    def series(self) -> np.ndarray:
+        return ising_hmc_series_get(self.h)
 
     @property
     def traj_index(self):

@@ -50,6 +50,9 @@ struct ising_hmc {
     void *dsJ8 = nullptr;   // FP8 form: per-row scales of J
     void *dJdig = nullptr, *dpsidig = nullptr, *drow_exp = nullptr, *dchain_exp = nullptr,
          *dGint = nullptr;
+    // per-trajectory series (m, E, |m| per chain and trajectory)
+    double *series = nullptr;
+    int64_t series_cap = 0, series_n = 0;
     // counters
     int64_t traj = 0;
     int64_t launches = 0;
@@ -233,7 +236,8 @@ static void free_all(ising_hmc *h) {
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
                     h->d_state, h->d_h32, h->d_h64, h->d_J, h->d_lpe, h->d_err, h->dJ16,
                     h->dJhi, h->dJlo, h->dpsi16, h->du32, h->du16, h->dGhi, h->dGlo,
-                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dGint, h->dsJ8};
+                    h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dGint, h->dsJ8,
+                    h->series};
     for (void *b : bufs)
         if (b) cudaFree(b);
     h->p = nullptr;
@@ -354,6 +358,24 @@ static ising_status upload_params(ising_hmc *h) {
     return cudaStreamSynchronize(h->stream) == cudaSuccess
                ? ISING_OK
                : fail(h, ISING_ECUDA, "parameter upload failed");
+}
+
+// Series record of trajectory k: each chain's m, E, |m| (the values the
+// measurement step adds to its sums) into series[(c * cap + k) * 3 + j].
+__global__ void k_series_record(const ChainState *st, double *series, int n_chains, int64_t cap,
+                                int64_t k) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    double *r = series + ((size_t)c * cap + k) * 3;
+    r[0] = st[c].obs[0];
+    r[1] = st[c].obs[1];
+    r[2] = st[c].obs[2];
+}
+
+static cudaError_t launch_series_record(const ChainState *st, double *series, int n_chains,
+                                        int64_t cap, int64_t k, cudaStream_t s) {
+    k_series_record<<<(n_chains + 127) / 128, 128, 0, s>>>(st, series, n_chains, cap, k);
+    return cudaGetLastError();
 }
 
 // Chain-averaged observables from per-chain sums (ISING_NSUMS per chain):
@@ -738,10 +760,112 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     return ISING_OK;
 }
 
+static ising_status run_trajectories(ising_hmc *h, int64_t n, uint64_t seed);
+
 ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
     if (!h) return ISING_EINVAL;
     if (n < 0) return fail(h, ISING_EINVAL, "n must be >= 0");
     if (n == 0) return ISING_OK;
+    // while a series is recorded: one trajectory per launch, then its record
+    while (n > 0 && h->series && h->series_n < h->series_cap) {
+        ising_status st = run_trajectories(h, 1, seed);
+        if (st != ISING_OK) return st;
+        CUDA_OR_FAIL(h, launch_series_record(h->d_state, h->series, h->n_chains, h->series_cap,
+                                             h->series_n, h->stream));
+        h->launches += 1;
+        h->series_n += 1;
+        --n;
+    }
+    return n > 0 ? run_trajectories(h, n, seed) : ISING_OK;
+}
+
+ising_status ising_hmc_series_enable(ising_hmc_t *h, int64_t capacity) {
+    if (!h) return ISING_EINVAL;
+    if (capacity < 0) return fail(h, ISING_EINVAL, "capacity must be >= 0");
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    if (h->series) {
+        cudaFree(h->series);
+        h->bytes -= h->series_cap * h->n_chains * 3 * (int64_t)sizeof(double);
+        h->series = nullptr;
+    }
+    h->series_cap = 0;
+    h->series_n = 0;
+    if (capacity == 0) return ISING_OK;
+    st = dalloc(h, &h->series, (size_t)capacity * h->n_chains * 3 * sizeof(double));
+    if (st != ISING_OK) return st;
+    h->series_cap = capacity;
+    return ISING_OK;
+}
+
+ising_status ising_hmc_series_get(ising_hmc_t *h, double *out, int64_t *n_out) {
+    if (!h || !n_out) return ISING_EINVAL;
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    *n_out = h->series_n;
+    if (!h->series || h->series_n == 0 || !out) return ISING_OK;   // NULL out: query n only
+    // device layout [chain][capacity][3] -> host [chain][n][3]
+    for (int c = 0; c < h->n_chains; ++c)
+        CUDA_OR_FAIL(h, cudaMemcpy(out + (size_t)c * h->series_n * 3,
+                                   h->series + (size_t)c * h->series_cap * 3,
+                                   (size_t)h->series_n * 3 * sizeof(double), cudaMemcpyDeviceToHost));
+    return ISING_OK;
+}
+
+// Gamma method with automatic windowing (Wolff, Comput. Phys. Commun. 156
+// (2004) 143): R replicas of length n; Gamma(t) from all replicas about the
+// global mean, tau_int(W) = 1/2 + sum_{t<=W} Gamma(t)/Gamma(0), W the first
+// window with exp(-W/tau_W) - tau_W/sqrt(W N) < 0 where tau_W =
+// S / ln((2 tau_int + 1)/(2 tau_int - 1)); the bias of Gamma from the
+// estimated mean is corrected by C_W / N (his Eq. 31).
+ising_status ising_gamma_method(const double *x, int64_t n, int n_rep, double S, double *out) {
+    if (!x || !out || n < 2 || n_rep < 1 || !(S > 0))
+        return fail(nullptr, ISING_EINVAL, "gamma method: need n >= 2, n_rep >= 1, S > 0");
+    const double Ntot = (double)n * n_rep;
+    double mean = 0;
+    for (int64_t i = 0; i < n * n_rep; ++i) mean += x[i];
+    mean /= Ntot;
+    auto gamma = [&](int64_t t) {
+        double g = 0;
+        for (int r = 0; r < n_rep; ++r) {
+            const double *xr = x + (size_t)r * n;
+            for (int64_t i = 0; i + t < n; ++i) g += (xr[i] - mean) * (xr[i + t] - mean);
+        }
+        return g / ((double)(n - t) * n_rep);
+    };
+    std::vector<double> G;
+    G.push_back(gamma(0));
+    for (int k = 0; k < 5; ++k) out[k] = 0;
+    out[0] = mean;
+    if (G[0] <= 0) {
+        out[2] = 0.5;
+        return ISING_OK;
+    }
+    int64_t W = 0;
+    double csum = G[0];   // G(0) + 2 sum_{t<=W} G(t)
+    const int64_t Wmax = n / 2;
+    for (int64_t t = 1; t <= Wmax; ++t) {
+        G.push_back(gamma(t));
+        csum += 2 * G[t];
+        const double tau = csum / (2 * G[0]);
+        if (tau <= 0.5) { W = t; break; }
+        const double tw = S / std::log((2 * tau + 1) / (2 * tau - 1));
+        if (std::exp(-(double)t / tw) - tw / std::sqrt((double)t * Ntot) < 0) { W = t; break; }
+        W = t;
+    }
+    // bias correction, then tau_int and the errors at the chosen window
+    const double CW = csum;
+    double g0 = G[0] + CW / Ntot, cs = g0;
+    for (int64_t t = 1; t <= W; ++t) cs += 2 * (G[t] + CW / Ntot);
+    double tau = std::max(cs / (2 * g0), 0.5);
+    out[1] = std::sqrt(std::max(cs, 0.0) / Ntot);
+    out[2] = tau;
+    out[3] = tau * std::sqrt(std::max(4.0 / Ntot * ((double)W + 0.5 - tau), 0.0));
+    out[4] = (double)W;
+    return ISING_OK;
+}
+
+static ising_status run_trajectories(ising_hmc *h, int64_t n, uint64_t seed) {
     if (h->traj + n > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "trajectory counter overflow");
     if (is_dense_tc(h)) {
         for (int64_t t = 0; t < n; ++t) {
