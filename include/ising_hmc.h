@@ -341,6 +341,18 @@ void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);
 const char *ising_hmc_last_create_error(void);
 
+/* A x = b for chain `chain`'s A = beta*J*K + C*1 (Sec. 2) by conjugate
+ * gradients in FP64 on the device (one CTA; a set-up computation).  Serves the
+ * paper's own parametrisation: its field is psi_p = sqrt(J') (psi + A^-1 h')
+ * with J' = beta*J, and its observables carry h'^T Kt^-1 h' = J' h'^T A^-1 h'
+ * (Kt = K + C_p*1 = A/J').  b, x: host arrays of N doubles.  Stops when the
+ * recursive residual satisfies ||r|| <= tol ||b|| or after max_iter
+ * iterations; *iters (may be NULL) gets the count, *resid (may be NULL)
+ * ||r||/||b||.  Lattice and infinite-range models.  Synchronises.
+ * Errors: EINVAL (kind, chain, tol <= 0, max_iter < 1), ENOMEM, ECUDA. */
+ising_status ising_hmc_solve_A(ising_hmc_t *h, int chain, const double *b, double *x, double tol,
+                               int max_iter, int *iters, double *resid);
+
 /* ---- Per-trajectory series and autocorrelation (Sec. 4) -----------------
  * From the next trajectory on, record each chain's m, beta*eps and |m| (the
  * values the measurement step adds to the sums; recorded for every

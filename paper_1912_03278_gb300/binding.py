@@ -117,6 +117,7 @@ def load(path: str | None = None):
                                              c_int, P, P, P, P]),
         "ising_hmc_energy_noalloc_error": (c_char_p, []),
         "ising_hmc_destroy": (None, [P]),
+        "ising_hmc_solve_A": (c_int, [P, c_int, P, P, c_double, c_int, P, P]),
         "ising_hmc_series_enable": (c_int, [P, c_int64]),
         "ising_hmc_series_get": (c_int, [P, P, P]),
         "ising_gamma_method": (c_int, [P, c_int64, c_int, c_double, P]),
@@ -409,6 +410,18 @@ def ising_group_last_error(g) -> str:
 def ising_group_destroy(g):
     if g:
         load().ising_group_destroy(g)
+
+
+def ising_hmc_solve_A(h, chain, b, tol=1e-13, max_iter=10000):
+    """x with A x = b for one chain (FP64 conjugate gradients on the device);
+    returns (x, iterations, relative residual)."""
+    bv = _f64(b)
+    x = np.zeros_like(bv)
+    it = ctypes.c_int(0)
+    res = c_double(0.0)
+    _check(h, load().ising_hmc_solve_A(h, int(chain), bv.ctypes.data, x.ctypes.data, float(tol),
+                                       int(max_iter), ctypes.byref(it), ctypes.byref(res)))
+    return x, it.value, res.value
 
 
 # --------------------------------------- series and autocorrelation ----
@@ -801,6 +814,9 @@ class IsingHMC:
 
     def sync(self):
         ising_hmc_sync(self.h)
+
+    def solve_A(self, b, chain=0, tol=1e-13, max_iter=10000):
+        return ising_hmc_solve_A(self.h, chain, b, tol, max_iter)
 
     def series_enable(self, capacity):
         ising_hmc_series_enable(self.h, capacity)

@@ -779,6 +779,44 @@ ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
     return n > 0 ? run_trajectories(h, n, seed) : ISING_OK;
 }
 
+ising_status ising_hmc_solve_A(ising_hmc_t *h, int chain, const double *b, double *x, double tol,
+                               int max_iter, int *iters, double *resid) {
+    if (!h || !b || !x) return ISING_EINVAL;
+    if (chain < 0 || chain >= h->n_chains) return fail(h, ISING_EINVAL, "chain %d out of range", chain);
+    if (h->kind != ISING_KIND_LATTICE && h->kind != ISING_KIND_INFINITE)
+        return fail(h, ISING_EINVAL, "solve_A applies to lattice and infinite-range models");
+    if (!(tol > 0) || max_iter < 1) return fail(h, ISING_EINVAL, "need tol > 0 and max_iter >= 1");
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    const int64_t N = h->N;
+    double *buf = nullptr;   // b, x, r, d, Ad, then resid and iters
+    const size_t bytes = (size_t)5 * N * sizeof(double) + 2 * sizeof(double);
+    if (cudaMalloc((void **)&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, ISING_ENOMEM, "solve_A: device allocation of %zu bytes failed", bytes);
+    }
+    double *dres = buf + 5 * N;
+    int *dit = reinterpret_cast<int *>(buf + 5 * N + 1);
+    const ChainParams &p = h->params[chain];
+    cudaError_t e = cudaMemcpyAsync(buf, b, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = solve_A(buf, buf + N, buf + 2 * N, N, h->kind, h->dim, h->L, p.bJ, p.C, tol, max_iter,
+                    dit, dres, h->stream);
+    double res = 0;
+    int it = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(x, buf + N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&res, dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&it, dit, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(h, ISING_ECUDA, "solve_A: %s", cudaGetErrorString(e));
+    h->launches += 1;
+    if (iters) *iters = it;
+    if (resid) *resid = res;
+    return ISING_OK;
+}
+
 ising_status ising_hmc_series_enable(ising_hmc_t *h, int64_t capacity) {
     if (!h) return ISING_EINVAL;
     if (capacity < 0) return fail(h, ISING_EINVAL, "capacity must be >= 0");
