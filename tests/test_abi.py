@@ -151,3 +151,7 @@ def test_dense_asymmetric_rejected(lib):
 def test_estimate_bytes(lib):
     cfg, keep = binding.make_config(dim=2, L=(1024, 1024), n_chains=4096)
     assert binding.ising_hmc_estimate_bytes(cfg) >= 16 * 1024 * 1024 * 4096
+    # infinite range: three psi buffers and p in FP32, no coupling matrix
+    cfg, keep = binding.make_config(kind="infinite", n_sites=4096, n_chains=4864)
+    est = binding.ising_hmc_estimate_bytes(cfg)
+    assert 16 * 4096 * 4864 <= est < 17 * 4096 * 4864
