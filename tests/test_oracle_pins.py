@@ -211,6 +211,15 @@ def test_brute_force_free_spins():
     assert abs(bf["E"] + (0.9 * h * np.tanh(0.9 * h)).mean()) < 1e-13
 
 
+@pytest.mark.parametrize("N,J", [(7, 1.0), (12, -0.5)])
+def test_infinite_range_spectrum(N, J):
+    """K = (11^T - 1)/N: eigenvalues -1/N (N-1 times) and (N-1)/N, the bounds the
+    library's positive-definiteness check for the all-to-all model uses."""
+    lam = np.linalg.eigvalsh(workloads.infinite_range_couplings(N, J))
+    expect = np.sort(np.r_[np.full(N - 1, -J / N), J * (N - 1) / N])
+    np.testing.assert_allclose(lam, expect, atol=1e-12)
+
+
 def test_infinite_range_matches_brute_force():
     N = 12
     for beta, h in ((1.0, 0.0), (0.7, 0.2), (1.5, -0.1)):
