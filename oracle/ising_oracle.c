@@ -368,7 +368,12 @@ void or_trajectory(const or_model *m, or_chain *c, int form, uint64_t seed, uint
     double S0 = or_action(m, c->psi, NULL, NULL);
     /* 2. molecular dynamics, one trajectory */
     memcpy(psi, c->psi, sizeof(double) * N);
-    if (integrator == 1) or_omelyan(m, psi, p, eps, n_md, 0.1931833275037836);
+#ifdef OR_PLANT_OMELYAN
+    const double omelyan_lambda = 0.25; /* planted mistake: not the minimum-norm value */
+#else
+    const double omelyan_lambda = 0.1931833275037836;
+#endif
+    if (integrator == 1) or_omelyan(m, psi, p, eps, n_md, omelyan_lambda);
     else or_leapfrog(m, psi, p, eps, n_md);
     /* 3. energy splitting and Metropolis test */
     double K1 = or_kinetic(N, p);

@@ -4,7 +4,7 @@ None of these compares the oracle with itself: each checks a closed form, an
 identity, a brute-force enumeration, or a published known-answer vector, and
 each is chosen so that a plausible mistake (dropped term, wrong sign, wrong
 index, wrong step coefficient) fails at least one of them.  The planted-
-mistake tests at the end show that for four such mistakes.
+mistake tests at the end show that for five such mistakes.
 """
 import math
 
@@ -170,6 +170,71 @@ def test_energy_violation_scales_as_eps_squared(integ):
         dH.append(abs(oracle.hamiltonian(m, psi, p) - H0))
     r1, r2 = dH[0] / dH[1], dH[1] / dH[2]
     assert 3.5 < r1 < 4.5 and 3.7 < r2 < 4.3, dH
+
+
+def _omelyan_error_coefficients(lam, eps):
+    """Leading error terms of one Omelyan step, read off the oracle's integrator.
+
+    With a field h = 500 (h' = beta h = 100) the tanh in the force is exactly
+    1 in FP64, so F = A(1 - psi) is linear, and on the uniform mode of a ring
+    with C + 2 beta J = 1 the dynamics is a unit harmonic oscillator,
+    q = psi - 1.
+    The one-step map M (2x2, symplectic) is exp(eps J S) with S the quadratic
+    form of the integrator's modified Hamiltonian
+      H~ = p^2/2 + q^2/2 + eps^2 (a p^2 + b q^2) + O(eps^4),
+    where a and b are the coefficients of the two nested Poisson brackets
+    {T,{T,V}} = p^2 and {V,{V,T}} = q^2 (T = p^2/2, V = q^2/2).  Omelyan,
+    Mryglod and Folk define the minimum-norm scheme as the lambda that
+    minimises a^2 + b^2 (the norm of the eps^3 error of one step)."""
+    m = oracle.Model(dim=1, L=(4,), Jnn=1.0, beta=0.2, C=0.6, h=500.0)
+    cols = []
+    for q0, p0 in ((1.0, 0.0), (0.0, 1.0)):
+        psi, p = oracle.omelyan(m, np.ones(4) + q0, np.full(4, p0), eps, 1, lam)
+        assert np.ptp(psi) == 0.0 and np.ptp(p) == 0.0   # stays on the uniform mode
+        cols.append((psi[0] - 1.0, p[0]))
+    M = np.array(cols).T
+    assert abs(np.linalg.det(M) - 1.0) < 1e-13           # symplectic
+    c = 0.5 * np.trace(M)
+    s = math.sqrt(1.0 - c * c)
+    K = (M - c * np.eye(2)) / s                           # M = cos(th) 1 + sin(th) K, K^2 = -1
+    S = -(math.atan2(s, c) / eps) * np.array([[0.0, 1.0], [-1.0, 0.0]]) @ K
+    assert abs(S[0, 1]) < 1e-8                            # time-reversible: no q p term
+    return (S[1, 1] - 1.0) / (2 * eps ** 2), (S[0, 0] - 1.0) / (2 * eps ** 2)
+
+
+def test_omelyan_lambda_is_the_minimum_norm_value():
+    """The lambda of the oracle's Omelyan scheme (and of its HMC trajectory)
+    is the one that minimises the norm of the scheme's leading error terms,
+    measured on the oracle's own integrator, not typed in."""
+    eps = 0.01
+    lams = np.linspace(0.10, 0.30, 9)
+    ab = np.array([_omelyan_error_coefficients(l, eps) for l in lams])
+    # the eps^2 terms are polynomials in lambda of degree <= 2 (a product of
+    # three exponentials with coefficients linear in lambda); fit, then minimise
+    pa = np.polyfit(lams, ab[:, 0], 2)
+    pb = np.polyfit(lams, ab[:, 1], 2)
+    assert np.abs(np.polyval(pa, lams) - ab[:, 0]).max() < 1e-5
+    assert np.abs(np.polyval(pb, lams) - ab[:, 1]).max() < 1e-5
+    grid = np.linspace(0.10, 0.30, 200_001)
+    norm = np.polyval(pa, grid) ** 2 + np.polyval(pb, grid) ** 2
+    lam_star = grid[np.argmin(norm)]
+    lam_oracle = oracle.omelyan.__defaults__[0]
+    assert abs(lam_star - lam_oracle) < 2e-4, (lam_star, lam_oracle)
+    # at lambda* the norm is well below that of neighbouring choices
+    n_star = np.min(norm)
+    for other in (0.15, 1.0 / 6.0, 0.25):
+        assert np.polyval(pa, other) ** 2 + np.polyval(pb, other) ** 2 > 1.3 * n_star
+    # the HMC trajectory's Omelyan path uses that same lambda
+    model = oracle.Model(dim=2, L=(6, 6), beta=0.44, h=0.05)
+    psi0 = workloads.rng(21).standard_normal(model.N) * 0.5
+    ch = oracle.Chain(model, form=oracle.FORM_FP64, seed=4, chain=2, psi0=psi0)
+    ch.traj = 5
+    r = ch.trajectory(0.1, 6, integrator=1)
+    p0 = oracle.momenta(oracle.FORM_FP64, 4, 2, 5, model.N)
+    want, _ = oracle.omelyan(model, psi0, p0, 0.1, 6, lam_oracle)
+    assert np.abs(r["psi_prop"] - want).max() < 1e-13
+    off, _ = oracle.omelyan(model, psi0, p0, 0.1, 6, lam_oracle + 1e-3)
+    assert np.abs(r["psi_prop"] - off).max() > 1e-6
 
 
 def test_leapfrog_single_step_by_hand():
@@ -508,3 +573,9 @@ def test_planted_leapfrog_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "_lib", _planted("OR_PLANT_LEAPFROG"))
     with pytest.raises(AssertionError):
         test_integrator_reversible("leapfrog")
+
+
+def test_planted_omelyan_lambda_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(oracle, "_lib", _planted("OR_PLANT_OMELYAN"))
+    with pytest.raises(AssertionError):
+        test_omelyan_lambda_is_the_minimum_norm_value()
