@@ -79,7 +79,8 @@ typedef struct {
                              the all-to-all coupling J (each pair couples with J/N)    */
     const double *h;      /* host per-site field h_i (N values) or NULL; copied         */
     double h0;            /* uniform field when h == NULL                               */
-    double beta, C, eps;  /* defaults for every chain; C in the units of A above        */
+    double beta, C, eps;  /* defaults for every chain; C in the units of A above;
+                             C <= 0 selects the default shift (see ising_hmc_create)   */
     const double *beta_chain; /* optional host arrays of n_chains values overriding    */
     const double *C_chain;    /*   beta, C, eps and h0 per chain (NULL = use the scalar) */
     const double *eps_chain;
@@ -121,11 +122,15 @@ typedef struct ising_hmc ising_hmc_t;
 /* Create a simulation: validates the model, allocates device state for
  * n_chains chains, uploads couplings and fields, and sets psi = 0 with its
  * action S(0) computed on the device.
- * Validation (Sec. 2, spectrum bound and shift): lattice requires
- * C > beta*|J|*2*dim for every chain; dense requires C > beta*|lambda_min(J)|,
- * with lambda_min from a Lanczos estimate on the host (ENOTPD otherwise);
- * infinite requires C > beta*J/N for J >= 0 and C > beta*|J|*(N-1)/N for
- * J < 0 (the exact extreme eigenvalues of beta*J*K), and 2 <= N <= 2^31.
+ * Validation (Sec. 2, spectrum bound and shift): A is positive definite iff C
+ * exceeds b = -lambda_min(beta*J*K).  Lattice: b = beta*|J|*2*dim (the bound
+ * the paper uses); dense: b = beta*|lambda_min(J)|, lambda_min estimated by
+ * Lanczos with full reorthogonalisation (min(N, 96) steps, FP64, products on
+ * the device); infinite: b = beta*J/N for J >= 0 and beta*|J|*(N-1)/N for
+ * J < 0 (the exact extreme eigenvalues), and 2 <= N <= 2^31.  A chain whose C
+ * is <= 0 gets the default shift C = b + 0.1 (the shift of the paper's
+ * workloads); ising_hmc_chain_params reports the C every chain uses.  A
+ * positive C <= b is rejected with ENOTPD.
  * Errors: EINVAL (bad sizes/kinds/precision for the kind), ENOTPD, ENOMEM, ECUDA. */
 ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out);
 
@@ -193,6 +198,12 @@ ising_status ising_hmc_momenta(ising_hmc_t *h, uint64_t seed, int64_t traj, int 
 /* Replace the per-chain step sizes (host eps[n_chains]); used by the step-size
  * tuner during equilibration only. */
 ising_status ising_hmc_set_eps(ising_hmc_t *h, const double *eps);
+
+/* Per-chain parameters as the handle uses them, host out[n_chains*3]:
+ * (beta, C, eps) for every chain -- C after the default of ising_hmc_create
+ * was applied (Sec. 2, shift), eps after any ising_hmc_set_eps.
+ * Errors: EINVAL (null handle or pointer). */
+ising_status ising_hmc_chain_params(const ising_hmc_t *h, double *out);
 
 /* Index of the next trajectory. */
 int64_t ising_hmc_traj_index(const ising_hmc_t *h);
@@ -294,7 +305,8 @@ ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n)
  * runs inside a memory pool or arena it does not own, hosts that forbid
  * allocation after start-up, or work inside a region where an allocation
  * would stall or break the caller's stream.  For them this entry point
- * computes, in FP64 and with the plain form's kernels, the action
+ * computes, in FP64 with the plain form's per-site arithmetic (in kernels of
+ * its own), the action
  * S(psi) = 1/2 psi.A.psi - sum_i log 2cosh((A psi)_i + beta*h0) and the
  * kinetic energy 1/2 p.p of n_chains periodic-lattice configurations
  * (A = beta*Jnn*K + C*1), without allocating any memory.  The paper has no
@@ -312,8 +324,10 @@ ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n)
  * (other streams, other host threads) share the array and race, so
  * serialise them.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  Errors: EINVAL (arguments; message in
- * ising_hmc_energy_noalloc_error()), ECUDA. */
+ * call before any stream capture.  A CUDA error left pending by earlier work
+ * is not cleared and not taken for this call's own: the call returns ECUDA
+ * without launching, and the message says so.  Errors: EINVAL (arguments;
+ * message in ising_hmc_energy_noalloc_error()), ECUDA. */
 #define ISING_NOALLOC_MAX_CHAINS 64
 ising_status ising_hmc_energy_noalloc(int dim, const int L[3], double beta, double Jnn, double C,
                                       double h0, int n_chains, const double *psi, const double *p,

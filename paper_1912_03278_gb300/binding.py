@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "ising_hmc_momenta": (c_int, [P, c_uint64, c_int64, c_int, c_int, P]),
         "ising_hmc_get_chains": (c_int, [P, c_int, c_int, c_int, P]),
         "ising_hmc_set_eps": (c_int, [P, P]),
+        "ising_hmc_chain_params": (c_int, [P, P]),
         "ising_hmc_traj_index": (c_int64, [P]),
         "ising_hmc_n_sites": (c_int64, [P]),
         "ising_hmc_n_chains": (c_int, [P]),
@@ -201,19 +202,7 @@ def make_config(kind="lattice", dim=2, L=(4, 4), n_sites=0, J=None, Jnn=1.0, h=0
 
     per_chain("beta", beta)
     if C is None:
-        bmax = float(np.max(beta))
-        if kind == "dense":
-            C = bmax * abs(np.linalg.eigvalsh(_f64(J))[0]) + 0.1
-        elif kind == "infinite":
-            # beta*J*K has eigenvalues -beta*J/N and beta*J*(N-1)/N
-            lam = -Jnn / n_sites if Jnn >= 0 else Jnn * (n_sites - 1) / n_sites
-            C = np.asarray(beta) * abs(lam) + 0.1
-            if np.ndim(C) == 0:
-                C = float(C)
-        else:
-            C = np.asarray(beta) * abs(Jnn) * 2 * dim + 0.1
-            if np.ndim(C) == 0:
-                C = float(C)
+        C = 0.0   # the library's default shift (Sec. 2 bound + 0.1)
     per_chain("C", C)
     per_chain("eps", eps)
     cfg.n_md = n_md
@@ -315,6 +304,13 @@ def ising_hmc_get_chains(h, which, chain0, count) -> np.ndarray:
 def ising_hmc_set_eps(h, eps):
     e = _f64(eps)
     _check(h, load().ising_hmc_set_eps(h, e.ctypes.data))
+
+
+def ising_hmc_chain_params(h) -> np.ndarray:
+    """(n_chains, 3) array of (beta, C, eps) as the handle uses them."""
+    out = np.zeros((load().ising_hmc_n_chains(h), 3))
+    _check(h, load().ising_hmc_chain_params(h, out.ctypes.data))
+    return out
 
 
 def ising_hmc_traj_index(h) -> int:
@@ -797,6 +793,11 @@ class IsingHMC:
 
     def reset_sums(self):
         ising_hmc_reset_sums(self.h)
+
+    @property
+    def params(self):
+        """(n_chains, 3) array of (beta, C, eps) per chain."""
+        return ising_hmc_chain_params(self.h)
 
     def autotune(self, reps=2):
         return ising_hmc_autotune(self.h, reps)

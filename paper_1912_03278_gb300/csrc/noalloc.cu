@@ -1,5 +1,5 @@
-// noalloc.cu -- the plain FP64 energy kernels in a form that allocates no
-// memory: S(psi) and 1/2 p.p of periodic-lattice configurations, with the
+// noalloc.cu -- the plain FP64 form's energy arithmetic in kernels that
+// allocate no memory: S(psi) and 1/2 p.p of periodic-lattice configurations, with the
 // per-block partial sums in a fixed, file-scope device array instead of a
 // buffer allocated by a simulation handle.  For callers that cannot call
 // cudaMalloc (see ising_hmc_energy_noalloc in ising_hmc.h).
@@ -123,6 +123,12 @@ extern "C" ising_status ising_hmc_energy_noalloc(int dim, const int L[3], double
     }
     if (N > ((int64_t)1 << 31)) return err(ISING_EINVAL, "energy_noalloc: too many sites");
     g.N = N;
+    // an error pending from earlier work belongs to the caller: leave it in
+    // place and do not launch, so the status below is this call's own
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return err(ISING_ECUDA, "energy_noalloc: a CUDA error from earlier work is pending: ",
+                   cudaGetErrorString(pending));
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return err(ISING_ECUDA, "energy_noalloc: no usable CUDA device");

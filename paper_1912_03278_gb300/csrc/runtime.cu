@@ -98,6 +98,10 @@ static size_t state_elem(const ising_hmc *h) {
     return h->prec == ISING_PREC_PLAIN_FP64 ? sizeof(double) : sizeof(float);
 }
 
+// Default shift: the positive-definiteness bound of Sec. 2 plus this margin
+// (the shift C = bound + 0.1 the paper's workloads use).
+static constexpr double DEFAULT_SHIFT_MARGIN = 0.1;
+
 // Integrator schedules (Sec. 3: symmetric symplectic integrators).
 static void make_schedule(int integrator, int n_md, Schedule &s) {
     if (integrator == ISING_INTEGRATOR_OMELYAN) {
@@ -562,32 +566,32 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     for (int c = 0; c < h->n_chains; ++c) {
         ChainParams &p = h->params[c];
         const double beta = cfg->beta_chain ? cfg->beta_chain[c] : cfg->beta;
-        const double C = cfg->C_chain ? cfg->C_chain[c] : cfg->C;
+        double C = cfg->C_chain ? cfg->C_chain[c] : cfg->C;
         const double eps = cfg->eps_chain ? cfg->eps_chain[c] : cfg->eps;
         const double h0 = cfg->h0_chain ? cfg->h0_chain[c] : cfg->h0;
         if (!(beta > 0) || !(eps > 0) || !std::isfinite(C) || !std::isfinite(h0))
             return bail(fail(h, ISING_EINVAL, "chain %d: need beta > 0, eps > 0, finite C and h0", c));
+        // Sec. 2: A = beta*J*K + C*1 is positive definite iff C exceeds minus
+        // the smallest eigenvalue of beta*J*K; C <= 0 selects that bound + 0.1
+        double bound;
+        const char *what;
         if (h->kind == ISING_KIND_LATTICE) {
-            const double bound = beta * std::fabs(cfg->Jnn) * 2 * h->dim;
-            if (!(C > bound))
-                return bail(fail(h, ISING_ENOTPD,
-                                 "chain %d: C=%g must exceed beta*|J|*2*dim=%g (Sec. 2)", c, C, bound));
+            bound = beta * std::fabs(cfg->Jnn) * 2 * h->dim;
+            what = "beta*|J|*2*dim";
         } else if (h->kind == ISING_KIND_INFINITE) {
             // eigenvalues of beta*J*K: -beta*J/N (N-1 times), beta*J*(N-1)/N
             const double Nd = (double)N;
-            const double bound = cfg->Jnn >= 0 ? beta * cfg->Jnn / Nd
-                                               : beta * -cfg->Jnn * (Nd - 1.0) / Nd;
-            if (!(C > bound))
-                return bail(fail(h, ISING_ENOTPD,
-                                 "chain %d: C=%g must exceed %g, the largest -eigenvalue of beta*J*K "
-                                 "(Sec. 2)", c, C, bound));
+            bound = cfg->Jnn >= 0 ? beta * cfg->Jnn / Nd : beta * -cfg->Jnn * (Nd - 1.0) / Nd;
+            what = "the largest -eigenvalue of beta*J*K";
         } else {
-            const double bound = beta * std::fabs(lam_min);
-            if (!(C > bound * (1.0 + 1e-9) + 1e-12))
-                return bail(fail(h, ISING_ENOTPD,
-                                 "chain %d: C=%g must exceed beta*|lambda_min(J)|=%g (Sec. 2)", c, C,
-                                 bound));
+            bound = beta * std::fabs(lam_min);
+            what = "beta*|lambda_min(J)|";
         }
+        if (C <= 0.0) C = bound + DEFAULT_SHIFT_MARGIN;
+        const bool ok = h->kind == ISING_KIND_DENSE ? C > bound * (1.0 + 1e-9) + 1e-12 : C > bound;
+        if (!ok)
+            return bail(fail(h, ISING_ENOTPD, "chain %d: C=%g must exceed %s=%g (Sec. 2)", c, C,
+                             what, bound));
         p.beta = beta;
         // lattice: beta*J; dense: beta (J carries the couplings); infinite:
         // kappa = beta*J/N, the coupling of every pair
@@ -1134,6 +1138,16 @@ ising_status ising_hmc_set_eps(ising_hmc_t *h, const double *eps) {
     ising_status st = ising_hmc_sync(h);
     if (st != ISING_OK) return st;
     return upload_params(h);
+}
+
+ising_status ising_hmc_chain_params(const ising_hmc_t *h, double *out) {
+    if (!h || !out) return ISING_EINVAL;
+    for (int c = 0; c < h->n_chains; ++c) {
+        out[3 * c + 0] = h->params[c].beta;
+        out[3 * c + 1] = h->params[c].C;
+        out[3 * c + 2] = h->params[c].eps;
+    }
+    return ISING_OK;
 }
 
 ising_status ising_hmc_get_state_native(ising_hmc_t *h, void *out) {

@@ -49,9 +49,11 @@ def _count_near_ties(model, psi, form, seed, chain, traj):
     return int(np.sum(np.abs(u - (1 + t) / 2) < 1e-6))
 
 
-def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,), C=None,
-                          eps=0.1, n_md=5, prec=FP32, integrator=0, flip_every=0, traj=3, seed=11,
-                          psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0):
+def _parity_setup(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,), C=None,
+                  eps=0.1, n_md=5, prec=FP32, integrator=0, flip_every=0, traj=3, seed=11,
+                  psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0, launch=None):
+    """Create a handle at a common start state; returns the context of one
+    parity case (the handle and everything the oracle needs)."""
     n_chains = len(betas)
     betas = np.asarray(betas, dtype=np.float64)
     if kind == "infinite":   # the oracle sees the same model as a dense matrix
@@ -69,27 +71,56 @@ def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=
     psi0 = workloads.start_psi(n_chains, N, scale=psi_scale, seed=17)
     if prec == FP32:
         psi0 = psi0.astype(np.float32).astype(np.float64)
-    form = oracle.FORM_FP32 if prec == FP32 else oracle.FORM_FP64
     sim = pkg.IsingHMC(kind=kind, dim=dim, L=L, J=None if kind == "infinite" else J,
                        n_sites=N if kind == "infinite" else 0, Jnn=Jnn, h=h, beta=betas, C=C,
                        eps=eps_c, n_md=n_md, n_chains=n_chains, precision=prec,
                        integrator=integrator, flip_every=flip_every)
     try:
+        if launch is not None:
+            sim.set_launch(*launch)
+            assert sim.launch == tuple(launch)
         sim.set_state(psi0, next_traj=traj)
         for k in range(n_traj - 1):
             sim.trajectories(1, seed)
-        start_last = sim.state(pkg.ISING_STATE_PSI)
-        sums_before = sim.chain_sums()
-        sim.trajectories(1, seed)
-        rec = sim.records()
-        prop = sim.state(pkg.ISING_STATE_PSI_PROPOSAL)
-        cur = sim.state(pkg.ISING_STATE_PSI)
-        pend = sim.state(pkg.ISING_STATE_P_END)
-        sums = sim.chain_sums() - sums_before
-        p0 = sim.momenta(seed, traj + n_traj - 1)
+    except BaseException:
+        sim.close()
+        raise
+    return dict(sim=sim, kind=kind, dim=dim, L=L, J=J, h=h, betas=betas, C=C, eps=eps_c,
+                n_md=n_md, prec=prec, integrator=integrator, flip_every=flip_every, traj=traj,
+                seed=seed, n_traj=n_traj, Jnn=Jnn, N=N, psi0=psi0, n_chains=n_chains)
+
+
+def _parity_before(ctx):
+    sim = ctx["sim"]
+    ctx["start_last"] = sim.state(pkg.ISING_STATE_PSI)
+    ctx["sums_before"] = sim.chain_sums()
+
+
+def _parity_after(ctx):
+    """Read the GPU's results of the last trajectory, then release the handle."""
+    sim = ctx["sim"]
+    try:
+        ctx["rec"] = sim.records()
+        ctx["prop"] = sim.state(pkg.ISING_STATE_PSI_PROPOSAL)
+        ctx["cur"] = sim.state(pkg.ISING_STATE_PSI)
+        ctx["pend"] = sim.state(pkg.ISING_STATE_P_END)
+        ctx["sums"] = sim.chain_sums() - ctx["sums_before"]
+        ctx["p0"] = sim.momenta(ctx["seed"], ctx["traj"] + ctx["n_traj"] - 1)
     finally:
         sim.close()
-    for c in range(n_chains):
+
+
+def _parity_check(ctx):
+    """Recompute every chain's trajectories with the oracle from the same start
+    and compare element by element (tolerances in the module docstring)."""
+    kind, dim, L, J, h, Jnn = ctx["kind"], ctx["dim"], ctx["L"], ctx["J"], ctx["h"], ctx["Jnn"]
+    betas, C, eps_c, n_md = ctx["betas"], ctx["C"], ctx["eps"], ctx["n_md"]
+    prec, integrator, flip_every = ctx["prec"], ctx["integrator"], ctx["flip_every"]
+    traj, seed, n_traj, N, psi0 = ctx["traj"], ctx["seed"], ctx["n_traj"], ctx["N"], ctx["psi0"]
+    rec, prop, cur, pend, sums, p0 = (ctx[k] for k in ("rec", "prop", "cur", "pend", "sums", "p0"))
+    start_last = ctx["start_last"]
+    form = oracle.FORM_FP32 if prec == FP32 else oracle.FORM_FP64
+    for c in range(ctx["n_chains"]):
         model = _oracle_model(kind, dim, L, J, h, betas[c], C[c], Jnn)
         ch = oracle.Chain(model, form=form, seed=seed, chain=c, psi0=psi0[c])
         ch.traj = traj
@@ -127,6 +158,18 @@ def one_trajectory_parity(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=
                                     last if r["accepted"] else 0xFFFFFFFF)
             assert abs(o_gpu["abs_m"] - o_ref["abs_m"]) <= 2.0 * ties / N + 1e-12, ("|m|", c)
     return rec
+
+
+def one_trajectory_parity(**kw):
+    ctx = _parity_setup(**kw)
+    try:
+        _parity_before(ctx)
+        ctx["sim"].trajectories(1, ctx["seed"])
+    except BaseException:
+        ctx["sim"].close()
+        raise
+    _parity_after(ctx)
+    return _parity_check(ctx)
 
 
 # ------------------------------------------------------------------ FP32 ----
@@ -173,6 +216,67 @@ def test_fp32_sign_flip_with_field():
 def test_fp32_several_trajectories():
     one_trajectory_parity(dim=3, L=(6, 6, 6), betas=(0.22,), h=0.05, eps=0.1, n_md=4, n_traj=3,
                           traj=0)
+
+
+# ------------------------------------ full-size layouts of the fused kernel ----
+# A thread of the fused lattice kernel owns up to 4 vectors of a plane (a
+# vector = 4 sites on rows that split into float4s, else 1 site).  These cases
+# reach 2, 3 and 4 vectors per thread, ragged last vectors (vectors not a
+# multiple of the thread count) and explicit launch shapes below the default
+# thread count, on both the float4 and the scalar path.
+@pytest.mark.parametrize("dim,L,launch", [
+    (3, (48, 48, 4), None),        # 576 vectors / 256 threads: 3 each, the third ragged
+    (3, (32, 32, 4), (64, 1)),     # 256 / 64: 4 each
+    (3, (20, 12, 5), (32, 2)),     # 60 / 32: 2 each, ragged, ring depth 2
+    (2, (1022, 6), None),          # scalar path, 1022 / 256: 4 each, ragged
+    (2, (1001, 8), None),          # scalar path, odd row
+    (2, (256, 8), (32, 1)),        # 64 / 32: 2 each
+    (2, (1024, 6), (64, 1)),       # 256 / 64: 4 each (a row of the L = 1024 workload)
+    (2, (1024, 5), (96, 4)),       # 256 / 96: 3 each, ragged, ring depth 4
+])
+def test_fp32_multi_vector_layouts(dim, L, launch):
+    one_trajectory_parity(dim=dim, L=L, betas=(0.30, 0.44), h=0.05, eps=0.08, n_md=6,
+                          launch=launch)
+
+
+@pytest.mark.parametrize("L", [48, 64])
+def test_fp32_3d_mixed_workload_sizes(L):
+    """The two largest sizes of the mixed 3D workload (h = 0.05, beta = 0.2217,
+    C = 6 beta + 0.1) at the default launch shape: 3 and 4 vectors per thread."""
+    one_trajectory_parity(dim=3, L=(L, L, L), betas=(0.2217, 0.2217), h=0.05, eps=0.08, n_md=6)
+
+
+def test_mixed_size_group_launch_against_oracle():
+    """Members of different sizes and launch shapes advanced by one group
+    launch; every chain of every member is checked against the oracle."""
+    cases = [
+        dict(dim=3, L=(48, 48, 4), betas=(0.2217,), h=0.05),
+        dict(dim=2, L=(1001, 8), betas=(0.3, 0.44), h=0.02),
+        dict(dim=3, L=(6, 5, 7), betas=(0.2,), h=0.0),
+        dict(dim=2, L=(32, 32), betas=(0.4,), h=0.05, launch=(32, 1)),
+        dict(dim=3, L=(16, 16, 16), betas=(0.2217, 0.25), h=0.05),
+    ]
+    ctxs = []
+    try:
+        for c in cases:
+            ctxs.append(_parity_setup(eps=0.08, n_md=6, **c))
+        for c in ctxs:
+            _parity_before(c)
+        grp = pkg.IsingGroup([c["sim"] for c in ctxs])
+        try:
+            grp.trajectories(1, ctxs[0]["seed"])
+            grp.sync()
+            assert grp.launches == 1
+        finally:
+            grp.close()
+    except BaseException:
+        for c in ctxs:
+            c["sim"].close()
+        raise
+    for c in ctxs:
+        _parity_after(c)
+    for c in ctxs:
+        _parity_check(c)
 
 
 # ------------------------------------------------------------ plain FP64 ----

@@ -24,14 +24,27 @@ def torch_cuda():
     return torch
 
 
-def test_energy_noalloc_matches_handle_path(torch_cuda):
+@pytest.mark.parametrize("dim,L,with_p", [
+    (2, (12, 10), True),
+    (2, (12, 10), False),     # p = NULL: K must be exactly 0
+    (3, (6, 5, 7), True),
+    (1, (9,), True),
+])
+def test_energy_noalloc_matches_handle_path(torch_cuda, dim, L, with_p):
+    """Two calls in a row (the second reuses the scratch array the first
+    filled): S and K equal the handle path's S0 and K0 and the oracle's FP64
+    values within 1e-6."""
+    import oracle
+    oracle.build()
     torch = torch_cuda
-    L, beta, C, h0, n, seed, traj = (12, 10), 0.41, 4 * 0.41 + 0.2, 0.07, 3, 21, 4
-    N = L[0] * L[1]
+    beta, h0, n, seed, traj = 0.41, 0.07, 3, 21, 4
+    C = 2 * dim * beta + 0.2
+    N = int(np.prod(L))
+    model = oracle.Model(dim=dim, L=L, beta=beta, C=C, h=h0)
     for call in range(2):
         psi = workloads.start_psi(n, N, scale=0.6 + 0.3 * call, seed=40 + call)
         # existing entry point: S0 and K0 of the trajectory record of a plain FP64 handle
-        sim = pkg.IsingHMC(dim=2, L=L, beta=beta, C=C, h=h0, eps=0.1, n_md=2, n_chains=n,
+        sim = pkg.IsingHMC(dim=dim, L=L, beta=beta, C=C, h=h0, eps=0.1, n_md=2, n_chains=n,
                            precision=pkg.ISING_PREC_PLAIN_FP64)
         try:
             sim.set_state(psi, next_traj=traj)
@@ -41,14 +54,21 @@ def test_energy_noalloc_matches_handle_path(torch_cuda):
         finally:
             sim.close()
         dpsi = torch.tensor(psi, dtype=torch.float64, device="cuda")
-        dp = torch.tensor(p0, dtype=torch.float64, device="cuda")
+        dp = torch.tensor(p0, dtype=torch.float64, device="cuda") if with_p else None
         out = torch.full((2 * n,), float("nan"), dtype=torch.float64, device="cuda")
-        binding.ising_hmc_energy_noalloc(2, L, beta, 1.0, C, h0, n, dpsi.data_ptr(),
-                                         dp.data_ptr(), out.data_ptr())
+        binding.ising_hmc_energy_noalloc(dim, L, beta, 1.0, C, h0, n, dpsi.data_ptr(),
+                                         dp.data_ptr() if with_p else 0, out.data_ptr())
         torch.cuda.synchronize()
         res = out.cpu().numpy().reshape(n, 2)
         np.testing.assert_allclose(res[:, 0], rec[:, 4], rtol=0, atol=1e-6)   # S
-        np.testing.assert_allclose(res[:, 1], rec[:, 3], rtol=0, atol=1e-6)   # K
+        for c in range(n):
+            assert abs(res[c, 0] - oracle.action(model, psi[c])) <= 1e-6
+        if with_p:
+            np.testing.assert_allclose(res[:, 1], rec[:, 3], rtol=0, atol=1e-6)   # K
+            for c in range(n):
+                assert abs(res[c, 1] - oracle.kinetic(p0[c])) <= 1e-6
+        else:
+            assert np.all(res[:, 1] == 0.0)
 
 
 def test_energy_noalloc_rejects_too_many_chains(torch_cuda):
