@@ -233,13 +233,30 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm ----
+BETA_C = 0.5 * math.log(1.0 + math.sqrt(2.0))   # Onsager's critical coupling (J = 1)
+
+
+def onsager_u(beta):
+    """Energy per site of the infinite square lattice (J = 1, h = 0), Onsager's
+    closed form: u = -coth(2b) [1 + (2/pi)(2 tanh^2(2b) - 1) K(k)], k =
+    2 sinh(2b)/cosh^2(2b), K the complete elliptic integral of the first kind."""
+    from scipy.special import ellipk
+    b2 = 2.0 * beta
+    k = 2.0 * math.sinh(b2) / math.cosh(b2) ** 2
+    return -(1.0 / math.tanh(b2)) * (1.0 + (2.0 / math.pi) * (2.0 * math.tanh(b2) ** 2 - 1.0)
+                                     * float(ellipk(k * k)))
+
+
 def hot_start(pkg, sims, seed, betas, C, batch=256):
-    """Start every chain from random spins s = +-1 dressed with the HS field's
-    exact conditional fluctuation: given s, phi = A psi ~ N(A s, A) (Sec. 2,
-    Eq. did_HS_trafo), i.e. psi = s + A^{-1/2} xi with xi ~ N(0, 1).  On the
-    periodic square lattice A = beta J K + C is circulant, so A^{-1/2} is
-    applied in Fourier space (eigenvalues C + 2 beta J (cos kx + cos ky)).
-    Set-up only (torch on the device, before any timed region)."""
+    """Start every chain from spins s = +-1 dressed with the HS field's exact
+    conditional fluctuation: given s, phi = A psi ~ N(A s, A) (Sec. 2,
+    Eq. did_HS_trafo), i.e. psi = s + A^{-1/2} xi with xi ~ N(0, 1).  Spins
+    are drawn at random for beta <= beta_c and all +1 above it (the phase each
+    chain equilibrates to, so off-critical chains become stationary within a
+    few dozen trajectories).  On the periodic square lattice A = beta J K + C
+    is circulant, so A^{-1/2} is applied in Fourier space (eigenvalues
+    C + 2 beta J (cos kx + cos ky)).  Set-up only (torch on the device,
+    before any timed region)."""
     import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
@@ -259,6 +276,8 @@ def hot_start(pkg, sims, seed, betas, C, batch=256):
             f *= (c + b * lam_k[None]).rsqrt().to(torch.float32)
             spins = torch.randint(0, 2, (c1 - c0, L, L), device="cuda", generator=g,
                                   dtype=torch.int8).to(torch.float32).mul_(2.0).sub_(1.0)
+            ordered = torch.tensor(betas[c0:c1] > BETA_C, device="cuda")[:, None, None]
+            spins = torch.where(ordered, torch.ones_like(spins), spins)
             psi[c0:c1] = spins + torch.fft.irfft2(f, s=(L, L))
             del xi, f, spins
         torch.cuda.synchronize()
@@ -445,9 +464,15 @@ def run_ours(args):
 
     if rank == 0:
         line["clocks"] = clk.summary()
+        line["onsager"] = onsager_check(sims, Ls, betas)
         if not args.no_plain:
-            line["plain_form"] = plain_rate(pkg, big, betas, C, sims[big], stream)
-            line["speedup_vs_plain"] = value / ws / line["plain_form"]["value"]
+            cmp = {str(L): acceptance_compare(pkg, L, betas, C, sims[L], stream) for L in Ls}
+            # plain-form time for one step's work (every chain of every size)
+            work = {L: float(L * L) * n_chains * N_MD for L in Ls}
+            plain_rate = sum(work.values()) / sum(work[L] / cmp[str(L)]["plain_rate"] for L in Ls)
+            line["plain_form"] = {"value": plain_rate, "unit": UNIT, "dtype": "f64",
+                                  "by_L": cmp}
+            line["speedup_vs_plain"] = value / ws / plain_rate
         if not args.no_e2e:
             line["e2e"] = e2e_rate(pkg, sims, Ls, n_chains, seed, stream)
         if not args.no_integrators:
@@ -476,54 +501,159 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": "%d chains of L=%d (one per core), 1 trajectory, "
                                               "N_md=%d, %.1f s" % (cores, big, N_MD, dt)}
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
-def plain_rate(pkg, L, betas, C, tuned, stream, k=64, n=8):
-    """Plain FP64 form (one chain per launch, unfused kernels) on k chains spread
-    over the betas, started from the batched handle's own current
-    configurations with its tuned step sizes, so both forms run the same
-    Markov chains at the same point of equilibration; acceptance of both on
-    these chains is reported (the plain form's from n trajectories, the
-    batched form's from its timed steps), each with its binomial standard
-    error: the two forms draw different momenta (FP64 vs FP32 Box-Muller), so
-    their acceptances agree only statistically."""
+def summary(line):
+    """The headline comparisons in a few numbers, emitted as the line's last key
+    (so that a truncated copy of the line still carries them)."""
+    def g(*path):
+        d = line
+        for p in path:
+            if not isinstance(d, dict) or p not in d:
+                return None
+            d = d[p]
+        return round(d, 4) if isinstance(d, float) else d
+    out = {"speedup_vs_plain": g("speedup_vs_plain"), "stencil_frac": g("roofline", "frac")}
+    for L in LS:
+        c = g("plain_form", "by_L", str(L))
+        if c:
+            out["acc_L%d" % L] = {"chosen": g("plain_form", "by_L", str(L), "chosen", "acceptance"),
+                                  "plain": g("plain_form", "by_L", str(L), "plain", "acceptance"),
+                                  "diff": g("plain_form", "by_L", str(L), "acc_diff"),
+                                  "err": g("plain_form", "by_L", str(L), "acc_diff_err"),
+                                  "within_2pct": c.get("within_2pct"),
+                                  "creutz_ok": c.get("stationary_creutz_3sigma")}
+        o = g("onsager", str(L), "max_abs_dev_off_critical")
+        if o is not None:
+            out["onsager_maxdev_L%d" % L] = o
+    out["mixed_3d_frac"] = g("mixed_3d", "roofline", "frac")
+    out["dense_bf16_frac"] = g("dense", "roofline", "frac")
+    for f in ("bf16", "fp8"):
+        d = g("dense", "precision_error", f + "_minus_fp64")
+        if d:
+            out["dense_%s_minus_fp64_sigma" % f] = {k: round(d[k]["sigma"], 2)
+                                                    for k in ("m", "E", "abs_m")}
+    out["mh_frac"] = g("mh", "roofline", "frac")
+    out["t_hmc_over_t_mh"] = g("mh", "t_hmc_over_t_mh")
+    out["infinite_resident_frac"] = g("infinite", "resident", "roofline", "frac")
+    out["serve_p50_p99_s"] = [g("serve", "p50_s"), g("serve", "p99_s")]
+    return out
+
+
+def _pick_stationary(betas, per_group, groups=4):
+    """Chains of the `groups` beta values farthest from beta_c (two on each
+    side), `per_group` of each: chains that become stationary within a few
+    dozen trajectories (correlation lengths of a few sites)."""
+    ub = np.unique(betas)
+    far = list(ub[:groups // 2]) + list(ub[-(groups // 2):])
+    idx = np.concatenate([np.flatnonzero(betas == b)[:per_group] for b in far])
+    return idx, [float(b) for b in far]
+
+
+def _arm_stats(sums, n_traj, k):
+    """Acceptance (binomial error over chain-trajectories) and Creutz's
+    <exp(-dH)> (standard error of the per-chain means) from chain sums."""
+    n_meas = sums[:, 0]
+    acc = float(sums[:, 1].sum() / n_meas.sum())
+    e_chain = sums[:, 9] / n_meas
+    return {"acceptance": acc, "acceptance_err": math.sqrt(acc * (1 - acc) / (k * n_traj)),
+            "mean_exp_mdH": float(e_chain.mean()),
+            "exp_mdH_err": float(e_chain.std(ddof=1) / math.sqrt(k)),
+            "mean_dH": float(sums[:, 8].sum() / n_meas.sum())}
+
+
+def acceptance_compare(pkg, L, betas, C, tuned, stream, per_group=32, therm=100, n=32, seed=77):
+    """The metric's condition: the chosen form (FP32 fused, batched) and the
+    plain form (FP64 state and force, one chain per launch, unfused) at equal
+    acceptance within 2%.  Chains of the four beta values farthest from beta_c
+    (per_group each) are copied from the tuned handle, thermalised for `therm`
+    more trajectories in the chosen form at their tuned eps, and from that
+    common snapshot both forms run `n` trajectories at the same eps and N_md
+    with the same seed and trajectory indices (their momenta come from the
+    same Philox draws, rounded differently).  Per arm: acceptance with its
+    binomial error over all chain-trajectories (>= 4096), Creutz's
+    <exp(-dH)> = 1 as the stationarity check.  The plain arm's n
+    trajectories are timed with CUDA events: its site-steps/s."""
     import torch
-    idx = np.linspace(0, len(betas) - 1, k).round().astype(int)
-    eps = tuned._eps[idx]
-    sim = pkg.IsingHMC(dim=2, L=(L, L), beta=betas[idx], C=C[idx], eps=eps, n_md=N_MD,
-                       n_chains=len(idx), precision=pkg.ISING_PREC_PLAIN_FP64,
-                       stream=stream.cuda_stream)
+    idx, far = _pick_stationary(betas, per_group)
+    k = len(idx)
+    eps = np.asarray(tuned._eps, dtype=np.float64)[idx]
+    n_all = pkg.binding.load().ising_hmc_n_chains(tuned.h)
+    full = torch.empty(n_all, L * L, device="cuda", dtype=torch.float32)
+    pkg.ising_hmc_get_state_native(tuned.h, full.data_ptr())
+    start = full[torch.as_tensor(idx, device="cuda")].contiguous()
+    del full
+    kw = dict(dim=2, L=(L, L), beta=betas[idx], C=C[idx], eps=eps, n_md=N_MD, n_chains=k,
+              stream=stream.cuda_stream)
+    t0_idx = 5 * 10 ** 6
+    chosen = pkg.IsingHMC(precision=pkg.ISING_PREC_FP32, **kw)
     try:
-        psi = np.stack([tuned.chains(pkg.binding.ISING_STATE_PSI, int(c), 1)[0] for c in idx])
-        sim.set_state(psi, next_traj=10 ** 6)
-        sim.trajectories(1, 77)
-        sim.sync()
-        sim.reset_sums()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        l0 = sim.launches
-        t0.record(stream)
-        sim.trajectories(n, 77)
-        t1.record(stream)
         torch.cuda.synchronize()
-        dt = t0.elapsed_time(t1) / 1e3
-        acc = sim.observables()["acceptance"]
-        sums = tuned.chain_sums()[idx]
-        nb = max(1.0, float(sums[:, 0].sum()))
-        acc_b = float(sums[:, 1].sum() / nb)
-        n_p = len(idx) * n
-        return {"value": len(idx) * L * L * N_MD * n / dt, "unit": UNIT, "chains": len(idx),
-                "L": L, "trajectories": n, "launches": sim.launches - l0, "dtype": "f64",
-                "acceptance_sample": acc,
-                "acceptance_sample_err": math.sqrt(max(acc * (1 - acc), 0.0) / n_p),
-                "acceptance_batched_same_chains": acc_b,
-                "acceptance_batched_err": math.sqrt(max(acc_b * (1 - acc_b), 0.0) / nb),
-                "start": "the batched handle's current configurations of the same chains"}
+        pkg.ising_hmc_set_state_native(chosen.h, start.data_ptr(), t0_idx - therm)
+        chosen.trajectories(therm, seed + 1)
+        snap = chosen.state(pkg.ISING_STATE_PSI)
+        chosen.reset_sums()
+        chosen.trajectories(n, seed)
+        a_chosen = _arm_stats(chosen.chain_sums(), n, k)
     finally:
-        sim.close()
+        chosen.close()
+    del start
+    plain = pkg.IsingHMC(precision=pkg.ISING_PREC_PLAIN_FP64, **kw)
+    try:
+        plain.set_state(snap, next_traj=t0_idx)
+        plain.reset_sums()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = plain.launches
+        e0.record(stream)
+        plain.trajectories(n, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        launches = plain.launches - l0
+        a_plain = _arm_stats(plain.chain_sums(), n, k)
+    finally:
+        plain.close()
+    d = a_chosen["acceptance"] - a_plain["acceptance"]
+    d_err = math.hypot(a_chosen["acceptance_err"], a_plain["acceptance_err"])
+    stationary = all(abs(a["mean_exp_mdH"] - 1.0) <= 3.0 * a["exp_mdH_err"]
+                     for a in (a_chosen, a_plain))
+    return {"L": L, "betas": far, "chains": k, "trajectories_per_chain": n,
+            "chain_trajectories_per_arm": k * n, "therm_before": therm,
+            "chosen": a_chosen, "plain": a_plain, "acc_diff": d, "acc_diff_err": d_err,
+            "within_2pct": bool(abs(d) < 0.02), "stationary_creutz_3sigma": bool(stationary),
+            "plain_rate": k * L * L * N_MD * n / dt, "plain_launches": int(launches),
+            "plain_dtype": "f64"}
+
+
+def onsager_check(sims, Ls, betas):
+    """Sec. 4 / Fig. 1: the energy per site E/beta of each beta group (mean over
+    its chains of the timed steps' per-trajectory estimator, error = standard
+    error of the chain means) against Onsager's infinite-lattice u(beta).
+    Groups within 0.02 of beta_c are marked critical: at L >= 256 their chains
+    are far from stationary in a benchmark-length run (tau ~ L^z) and carry
+    O(1/L) finite-size shifts."""
+    out = {}
+    for L in Ls:
+        sums = sims[L].chain_sums()
+        rows = {}
+        worst = 0.0
+        for b in np.unique(betas):
+            sel = betas == b
+            e = sums[sel, 4] / np.maximum(sums[sel, 0], 1) / b
+            m, err = float(e.mean()), float(e.std(ddof=1) / math.sqrt(sel.sum()))
+            u = onsager_u(float(b))
+            crit = abs(b - BETA_C) < 0.02
+            rows["%.4f" % b] = {"E_per_site": m, "err": err, "onsager_u": u,
+                                "dev_sigma": (m - u) / max(err, 1e-300), "critical": bool(crit)}
+            if not crit:
+                worst = max(worst, abs(m - u))
+        out[str(L)] = {"by_beta": rows, "max_abs_dev_off_critical": worst}
+    return out
 
 
 def _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, prec, stream, steps, seed, tune_rounds, n_force):
@@ -533,6 +663,7 @@ def _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, prec, stream, steps, seed, tu
     sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=0.05, n_md=n_md, n_chains=B,
                        precision=prec, stream=stream.cuda_stream)
     try:
+        C_used = float(sim.params[0, 1])   # the library's default shift when C is None
         eps = 0.05
         trace = []
         sim.trajectories(4, seed)
@@ -565,7 +696,7 @@ def _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, prec, stream, steps, seed, tu
     finally:
         sim.close()
     return dict(ms_traj=ms_traj, launches=launches, acc=obs["acceptance"], eps=eps, trace=trace,
-                ms_force=ms_force)
+                ms_force=ms_force, C=C_used)
 
 
 def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10):
@@ -581,14 +712,10 @@ def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10
     N, B, beta = 4096, 1024, 0.5
     J = workloads.dense_couplings(N, seed=1)
     hv = workloads.dense_fields(N, 0.1, seed=2)
-    try:
-        from scipy.sparse.linalg import eigsh
-        lam = float(eigsh(J, k=1, which="SA", return_eigenvectors=False)[0])
-    except Exception:
-        lam = float(np.linalg.eigvalsh(J)[0])
-    C = beta * abs(lam) + 0.1
-    r = _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, pkg.ISING_PREC_BF16, stream, steps, seed,
+    # C = beta |lambda_min(J)| + 0.1, chosen by the library (Lanczos) and reused
+    r = _dense_tuned_run(pkg, J, hv, beta, None, B, n_md, pkg.ISING_PREC_BF16, stream, steps, seed,
                          tune_rounds, n_force)
+    C = r["C"]
     flops_force = 2 * 2.0 * N * N * B
     peaks = measured_peaks_all()
     peak = peaks.get("bf16_tflops") or 1900.0
@@ -617,6 +744,7 @@ def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10
                                "kernel": "force1_kernel + force2_kernel, E4M3 operands",
                                "ms_per_force": r8["ms_force"]}}
     eps = r["eps"]
+    out["precision_error"] = dense_precision(pkg, J, hv, beta, C, eps, n_md, stream)
     # plain one-chain-per-launch FP64 form on a few chains of the same model
     try:
         k = 2
@@ -635,6 +763,51 @@ def dense_rate(pkg, stream, steps=4, n_md=10, seed=77, tune_rounds=6, n_force=10
         out["speedup_vs_plain"] = out["value"] / rate
     except Exception as e:   # report, do not hide
         out["plain_form"] = {"error": str(e)}
+    return out
+
+
+def _chain_means(sums):
+    """Per-observable mean over chains of the per-chain averages, with the
+    standard error of those chain means."""
+    n = np.maximum(sums[:, 0], 1)
+    out = {}
+    for name, col in (("m", 2), ("E", 4), ("abs_m", 6)):
+        v = sums[:, col] / n
+        out[name] = (float(v.mean()), float(v.std(ddof=1) / math.sqrt(len(v))))
+    out["acceptance"] = (float(sums[:, 1].sum() / n.sum()), 0.0)
+    return out
+
+
+def dense_precision(pkg, J, hv, beta, C, eps, n_md, stream, therm=10, n=30, seed=91):
+    """Chosen-precision error against FP64, per observable, on the dense SK
+    workload: the BF16 and FP8 tensor-core forms (256 chains each) and the plain
+    FP64 form (128 chains), all at the same eps and N_md, started at psi = 0,
+    `therm` trajectories discarded, `n` measured.  A deterministic reversible
+    force keeps HMC exact, so each difference should be zero within its
+    combined standard error; the acceptance shows what the precision costs."""
+    forms = (("bf16", pkg.ISING_PREC_BF16, 256), ("fp8", pkg.ISING_PREC_FP8, 256),
+             ("fp64", pkg.ISING_PREC_PLAIN_FP64, 128))
+    res = {}
+    for name, prec, B in forms:
+        sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=eps, n_md=n_md,
+                           n_chains=B, n_therm=therm, precision=prec, stream=stream.cuda_stream)
+        try:
+            sim.trajectories(therm + n, seed)
+            res[name] = _chain_means(sim.chain_sums())
+        finally:
+            sim.close()
+    out = {"eps": eps, "n_md": n_md, "therm": therm, "measured": n,
+           "chains": {name: B for name, _, B in forms}}
+    for name in ("bf16", "fp8", "fp64"):
+        out[name] = {k: {"value": v[0], "err": v[1]} for k, v in res[name].items()}
+    for name in ("bf16", "fp8"):
+        d = {}
+        for k in ("m", "E", "abs_m"):
+            diff = res[name][k][0] - res["fp64"][k][0]
+            err = math.hypot(res[name][k][1], res["fp64"][k][1])
+            d[k] = {"diff": diff, "err": err, "sigma": diff / max(err, 1e-300)}
+        d["acceptance_diff"] = res[name]["acceptance"][0] - res["fp64"]["acceptance"][0]
+        out[name + "_minus_fp64"] = d
     return out
 
 
@@ -854,16 +1027,27 @@ def mixed_3d_rate(pkg, steps=4, seed=31):
     try:
         grp.trajectories(2, seed)
         grp.sync()
+        gs = torch.cuda.ExternalStream(grp.stream)
         l0 = grp.launches
-        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(gs)
         grp.trajectories(steps, seed)
+        e1.record(gs)
         grp.sync()
-        dt = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
         work = sum(s.kw["L"][0] ** 3 * 64 * s.kw["n_md"] for s in sims) * steps
         acc = [s.observables()["acceptance"] for s in sims]
+        peak, peak_kind = measured_peaks()
+        achieved = 16.0 * work / dt / 1e9
         return {"value": work / dt, "unit": UNIT, "graph_launches": grp.launches - l0,
-                "steps": steps, "sites": sum(s.kw["L"][0] ** 3 * 64 for s in sims),
-                "tuned_launch": tuned, "acceptance": acc}
+                "steps": steps, "ms_per_step": dt * 1e3 / steps,
+                "sites": sum(s.kw["L"][0] ** 3 * 64 for s in sims),
+                "tuned_launch": tuned, "acceptance": acc,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_kind,
+                             "kernel": "group graph (fused_lattice_kernel, five sizes)",
+                             "algorithmic_bytes_per_step": 16.0 * work / steps}}
     finally:
         grp.close()
         for s in sims:
@@ -875,15 +1059,9 @@ _DENSE_POOL = {}
 
 def dense_model(n):
     """SK couplings of size n for serving requests (a small pool of models, as
-    a service would host; generated once) and |lambda_min|."""
+    a service would host; generated once)."""
     if n not in _DENSE_POOL:
-        J = workloads.dense_couplings(n, seed=100 + n)
-        try:
-            from scipy.sparse.linalg import eigsh
-            lam = float(eigsh(J, k=1, which="SA", return_eigenvectors=False)[0])
-        except Exception:
-            lam = float(np.linalg.eigvalsh(J)[0])
-        _DENSE_POOL[n] = (J, abs(lam))
+        _DENSE_POOL[n] = workloads.dense_couplings(n, seed=100 + n)
     return _DENSE_POOL[n]
 
 
@@ -906,10 +1084,11 @@ def serve_requests(rng, n, scale, dense_share=0.1):
         seed = int(rng.integers(1, 2 ** 31))
         if rng.random() < dense_share:
             N = int(DENSE_SIZES[int(rng.integers(0, len(DENSE_SIZES)))])
-            J, lam = dense_model(N)
+            J = dense_model(N)
             n_md = workloads.n_md_default(N)
+            # C left to the library: beta |lambda_min(J)| + 0.1 (Lanczos at create)
             out.append(dict(n_traj=traj, seed=seed, kind="dense", J=J, beta=beta, h=h0,
-                            C=beta * lam + 0.1, eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md,
+                            eps=1.0 / (n_md * math.sqrt(beta)), n_md=n_md,
                             n_chains=chains, precision=2))   # ISING_PREC_BF16
             continue
         dim = 2 if rng.random() < 0.5 else 3
