@@ -464,7 +464,6 @@ def run_ours(args):
 
     if rank == 0:
         line["clocks"] = clk.summary()
-        line["onsager"] = onsager_check(sims, Ls, betas)
         if not args.no_plain:
             cmp = {str(L): acceptance_compare(pkg, L, betas, C, sims[L], stream) for L in Ls}
             # plain-form time for one step's work (every chain of every size)
@@ -473,6 +472,8 @@ def run_ours(args):
             line["plain_form"] = {"value": plain_rate, "unit": UNIT, "dtype": "f64",
                                   "by_L": cmp}
             line["speedup_vs_plain"] = value / ws / plain_rate
+        if 256 in sims:
+            line["onsager"] = onsager_sweep(pkg, stream, sims[256], betas)
         if not args.no_e2e:
             line["e2e"] = e2e_rate(pkg, sims, Ls, n_chains, seed, stream)
         if not args.no_integrators:
@@ -527,9 +528,8 @@ def summary(line):
                                   "err": g("plain_form", "by_L", str(L), "acc_diff_err"),
                                   "within_2pct": c.get("within_2pct"),
                                   "creutz_ok": c.get("stationary_creutz_3sigma")}
-        o = g("onsager", str(L), "max_abs_dev_off_critical")
-        if o is not None:
-            out["onsager_maxdev_L%d" % L] = o
+    out["onsager_L256_max_dev_sigma"] = g("onsager", "max_abs_dev_sigma_off_critical")
+    out["onsager_L256_pass"] = g("onsager", "pass_3sigma_off_critical")
     out["mixed_3d_frac"] = g("mixed_3d", "roofline", "frac")
     out["dense_bf16_frac"] = g("dense", "roofline", "frac")
     for f in ("bf16", "fp8"):
@@ -630,30 +630,48 @@ def acceptance_compare(pkg, L, betas, C, tuned, stream, per_group=32, therm=100,
             "plain_dtype": "f64"}
 
 
-def onsager_check(sims, Ls, betas):
-    """Sec. 4 / Fig. 1: the energy per site E/beta of each beta group (mean over
-    its chains of the timed steps' per-trajectory estimator, error = standard
-    error of the chain means) against Onsager's infinite-lattice u(beta).
-    Groups within 0.02 of beta_c are marked critical: at L >= 256 their chains
-    are far from stationary in a benchmark-length run (tau ~ L^z) and carry
-    O(1/L) finite-size shifts."""
-    out = {}
-    for L in Ls:
-        sums = sims[L].chain_sums()
-        rows = {}
-        worst = 0.0
-        for b in np.unique(betas):
-            sel = betas == b
-            e = sums[sel, 4] / np.maximum(sums[sel, 0], 1) / b
-            m, err = float(e.mean()), float(e.std(ddof=1) / math.sqrt(sel.sum()))
-            u = onsager_u(float(b))
-            crit = abs(b - BETA_C) < 0.02
-            rows["%.4f" % b] = {"E_per_site": m, "err": err, "onsager_u": u,
-                                "dev_sigma": (m - u) / max(err, 1e-300), "critical": bool(crit)}
-            if not crit:
-                worst = max(worst, abs(m - u))
-        out[str(L)] = {"by_beta": rows, "max_abs_dev_off_critical": worst}
-    return out
+def onsager_sweep(pkg, stream, tuned, betas_tuned, L=256, per_beta=32, therm=1500, n=1000,
+                  seed=83):
+    """Sec. 4 / Fig. 1 on the headline lattice: E/beta, the energy per site, for
+    the 16 betas of the sweep against Onsager's infinite-lattice u(beta).
+    per_beta chains per beta at that beta's tuned eps (taken from the tuned
+    handle), started in the phase they equilibrate to, `therm` trajectories
+    discarded and `n` measured; the error is the standard error of the chain
+    means.  Betas within 0.02 of beta_c are marked critical: their
+    correlation length and relaxation time grow with L (finite-size shifts,
+    tau ~ L^z) and they are not part of the pass test; elsewhere xi << L and
+    the lattice result equals u(beta) within its error."""
+    ub = np.unique(betas_tuned)
+    eps_t = np.asarray(tuned._eps, dtype=np.float64)
+    eps_b = {b: float(eps_t[betas_tuned == b].mean()) for b in ub}
+    betas = np.repeat(ub, per_beta)
+    C = workloads.lattice_C(betas, 2)
+    sim = pkg.IsingHMC(dim=2, L=(L, L), beta=betas, C=C,
+                       eps=np.array([eps_b[b] for b in betas]), n_md=N_MD,
+                       n_chains=len(betas), n_therm=therm, stream=stream.cuda_stream)
+    try:
+        hot_start(pkg, {L: sim}, seed, betas, C)
+        sim.trajectories(therm + n, seed)
+        sums = sim.chain_sums()
+    finally:
+        sim.close()
+    rows, worst = {}, 0.0
+    for b in ub:
+        sel = betas == b
+        nm = np.maximum(sums[sel, 0], 1)
+        e = sums[sel, 4] / nm / b
+        m, err = float(e.mean()), float(e.std(ddof=1) / math.sqrt(sel.sum()))
+        u = onsager_u(float(b))
+        crit = abs(b - BETA_C) < 0.02
+        dev = (m - u) / max(err, 1e-300)
+        rows["%.4f" % b] = {"E_per_site": m, "err": err, "onsager_u": u, "dev_sigma": dev,
+                            "acceptance": float(sums[sel, 1].sum() / nm.sum()),
+                            "critical": bool(crit)}
+        if not crit:
+            worst = max(worst, abs(dev))
+    return {"L": L, "chains_per_beta": per_beta, "therm": therm, "measured": n,
+            "by_beta": rows, "max_abs_dev_sigma_off_critical": worst,
+            "pass_3sigma_off_critical": bool(worst <= 3.0)}
 
 
 def _dense_tuned_run(pkg, J, hv, beta, C, B, n_md, prec, stream, steps, seed, tune_rounds, n_force):
