@@ -231,11 +231,26 @@ ising_status ising_hmc_sync(ising_hmc_t *h);
 ising_status ising_hmc_set_launch(ising_hmc_t *h, int threads, int depth);
 ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth);
 
+/* CTAs per chain of the fused FP32 lattice kernel (1, 2, 4 or 8; default 1):
+ * with ctas > 1 every chain runs on a thread-block cluster of that many CTAs,
+ * each streaming a slab of the chain's planes (2D rows, 3D xy-slabs; at
+ * least two planes per slab), so a few large chains fill the GPU.  The CTAs
+ * meet at one cluster barrier per force evaluation and add their per-chain
+ * sums in rank order: psi and p are bit for bit those of ctas = 1, the FP64
+ * sums (action, energies, estimators) equal them to rounding; for a given
+ * split, results are reproducible and independent of how trajectories are
+ * split across calls.  EINVAL for other forms, 1D lattices, too few planes,
+ * or a cluster the device cannot hold at the current launch shape. */
+ising_status ising_hmc_set_chain_split(ising_hmc_t *h, int ctas);
+int ising_hmc_get_chain_split(const ising_hmc_t *h);
+
 /* Autotuner: times `reps` trajectories for every valid launch shape on a
  * temporary handle with the same lattice and the first chains' parameters
  * (the handle's own chains are not advanced), keeps the fastest shape, and
- * returns its time per trajectory in *best_ms (may be NULL).  Allocates the
- * temporary handle; synchronises. */
+ * returns its time per trajectory in *best_ms (may be NULL).  The search
+ * covers threads and depth at one CTA per chain, then chain splits of 2, 4
+ * and 8 CTAs at the best thread count.  Allocates the temporary handle;
+ * synchronises. */
 ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms);
 
 /* Groups: FP32 lattice handles of any mix of lattice sizes advanced together
@@ -252,6 +267,17 @@ ising_status ising_group_create(ising_hmc_t *const *members, int n, ising_group_
 ising_status ising_group_trajectories(ising_group_t *g, int64_t n, uint64_t seed);
 /* Same with one seed per member (seeds[i] for the i-th member). */
 ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const uint64_t *seeds);
+
+/* Group autotuner: picks every member's chain split (CTAs per chain, see
+ * ising_hmc_set_chain_split) for the fastest launch of the whole group, by
+ * timing `reps` group trajectories per candidate on temporary copies of the
+ * members (all their chains, their current launch shapes; the members'
+ * chains are not advanced).  Greedy: members in order of work, each split in
+ * {1, 2, 4, 8} that fits, two rounds.  Sets the members' splits; *best_ms
+ * (may be NULL) gets the time per group trajectory.  Allocates the copies
+ * (ENOMEM if they would take more than 80% of the free device memory);
+ * synchronises. */
+ising_status ising_group_autotune(ising_group_t *g, int reps, double *best_ms);
 ising_status ising_group_sync(ising_group_t *g);
 int64_t ising_group_launch_count(const ising_group_t *g);   /* graph launches so far */
 void *ising_group_stream(const ising_group_t *g);           /* cudaStream_t of the launches */

@@ -98,6 +98,9 @@ def load(path: str | None = None):
         "ising_hmc_set_launch": (c_int, [P, c_int, c_int]),
         "ising_hmc_get_launch": (c_int, [P, P, P]),
         "ising_hmc_autotune": (c_int, [P, c_int, P]),
+        "ising_hmc_set_chain_split": (c_int, [P, c_int]),
+        "ising_hmc_get_chain_split": (c_int, [P]),
+        "ising_group_autotune": (c_int, [P, c_int, P]),
         "ising_group_create": (c_int, [P, c_int, P]),
         "ising_group_trajectories": (c_int, [P, c_int64, c_uint64]),
         "ising_group_trajectories_seeds": (c_int, [P, c_int64, P]),
@@ -361,6 +364,20 @@ def ising_hmc_autotune(h, reps=2) -> float:
     return ms.value
 
 
+def ising_hmc_set_chain_split(h, ctas):
+    _check(h, load().ising_hmc_set_chain_split(h, int(ctas)))
+
+
+def ising_hmc_get_chain_split(h) -> int:
+    return load().ising_hmc_get_chain_split(h)
+
+
+def ising_group_autotune(g, reps=2) -> float:
+    ms = c_double()
+    _gcheck(g, load().ising_group_autotune(g, int(reps), ctypes.byref(ms)))
+    return ms.value
+
+
 def ising_hmc_dense_forces(h, n):
     _check(h, load().ising_hmc_dense_forces(h, int(n)))
 
@@ -577,6 +594,10 @@ class IsingGroup:
 
     def sync(self):
         ising_group_sync(self.g)
+
+    def autotune(self, reps=2):
+        """Pick every member's chain split for the fastest group launch."""
+        return ising_group_autotune(self.g, reps)
 
     @property
     def launches(self):
@@ -812,6 +833,13 @@ class IsingHMC:
     @property
     def launch(self):
         return ising_hmc_get_launch(self.h)
+
+    def set_chain_split(self, ctas):
+        ising_hmc_set_chain_split(self.h, ctas)
+
+    @property
+    def chain_split(self):
+        return ising_hmc_get_chain_split(self.h)
 
     def sync(self):
         ising_hmc_sync(self.h)

@@ -18,6 +18,15 @@
 // Work layout inside a plane: a thread owns up to NVMAX vectors of VEC
 // consecutive sites, fixed for the whole launch, so every neighbour offset is
 // computed once.
+//
+// A chain may be split over a thread-block cluster of CS CTAs (launch
+// attribute; CS = 1 is a plain launch): CTA r streams the slab of planes
+// [r*nz/CS, (r+1)*nz/CS) and reads the two planes beyond each end of its slab
+// (the previous pass's psi, in global memory) to form the u values its force
+// needs, so the CTAs of a chain only meet at one cluster barrier after every
+// force pass.  The per-chain sums of a trajectory are exchanged through
+// distributed shared memory and added in rank order by every CTA, so all of
+// them take the same Metropolis decision.
 #include <cuda_runtime.h>
 
 #include "df32.cuh"
@@ -28,7 +37,10 @@ namespace ihmc {
 namespace {
 
 constexpr int NVMAX = 4;
-constexpr int RED_BYTES = 32 * 8 * 8 + 16;   // block reduction + broadcast words
+constexpr int MAX_CS = 8;                    // CTAs per chain (portable cluster size)
+constexpr int XCH_WORDS = 8;                 // per-CTA sums exchanged in a cluster
+// block reduction (32 warps x 8 doubles), broadcast words, two exchange buffers
+constexpr int RED_BYTES = 32 * 8 * 8 + 16 + 2 * XCH_WORDS * 8;
 
 // F(z) trails u by LAG planes: with LAG = 1 a plane's force reads only u
 // planes finished in earlier iterations, so one barrier per plane suffices.
@@ -37,10 +49,72 @@ constexpr int RED_BYTES = 32 * 8 * 8 + 16;   // block reduction + broadcast word
 #endif
 constexpr int LAG = IHMC_FL_LAG;
 
-// Shared memory of a launch: the plane rings (psi D+4+LAG, p D+2+LAG, u
-// 3+LAG slots), optionally the log(1 + e^-y) table, the reduction words.
+// Shared memory of a launch: the plane rings (psi D+4+LAG, u 3+LAG slots),
+// optionally the log(1 + e^-y) table, the reduction words.  The momenta do
+// not pass through shared memory: each thread loads its own p vectors one
+// plane ahead into registers.
 __host__ __device__ inline size_t ring_bytes(int P, int D) {
-    return (((size_t)(2 * D + 9 + 3 * LAG) * P + 3) & ~(size_t)3) * 4;
+    return (((size_t)(D + 7 + 2 * LAG) * P + 3) & ~(size_t)3) * 4;
+}
+
+// Thread-block cluster: size and rank of this CTA, barrier, and an FP64 read
+// of another CTA's shared memory.
+__device__ __forceinline__ int cluster_size() {
+    unsigned n;
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return (int)n;
+}
+__device__ __forceinline__ int cluster_rank() {
+    unsigned r;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+// Every thread of every CTA of the cluster; orders this thread's earlier
+// global and shared writes before the other CTAs' later reads.
+__device__ __forceinline__ void cluster_barrier() {
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ double ld_cluster_f64(const double *local, int rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+// Chain-wide sum of NV per-thread values: the CTA's fixed-order block sum,
+// then (cs > 1) the CTAs' block sums added in rank order through the
+// exchange buffer xch (NV <= XCH_WORDS doubles in every CTA's shared memory;
+// two alternating buffers so a buffer is rewritten only after a later
+// cluster barrier).  Every CTA's thread 0 ends with the same totals in v.
+template <int NV>
+__device__ __forceinline__ void chain_sum(double (&v)[NV], double *red, double *xch, int cs) {
+    static_assert(NV <= XCH_WORDS, "exchange buffer");
+    block_sum<NV>(v, red);
+    if (cs == 1) return;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) xch[k] = v[k];
+    }
+    cluster_barrier();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int r = 0; r < cs; ++r) t += ld_cluster_f64(xch + k, r);
+            v[k] = t;
+        }
+    }
+}
+
+// Periodic plane index of an absolute plane that may lie up to two planes
+// outside [0, nz) (any nz >= 1).
+__device__ __forceinline__ int wrap_plane(int z, int nz) {
+    z %= nz;
+    return z < 0 ? z + nz : z;
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -122,17 +196,42 @@ struct Nbr {
     Vec<VEC> ym, yp, zm, zp;
 };
 
-template <int DIM, int VEC>
+// Loads of a gather: from shared memory, or (GL) from global memory through
+// L2 only, so that planes another CTA of the cluster rewrote are never served
+// from a stale L1 line.
+template <int VEC, bool GL>
+__device__ __forceinline__ Vec<VEC> ldg_or_s(const float *p) {
+    if constexpr (!GL) {
+        return ldv<VEC>(p);
+    } else {
+        Vec<VEC> r;
+        if constexpr (VEC == 4) {
+            const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+            r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) r.v[k] = __ldcg(p + k);
+        }
+        return r;
+    }
+}
+template <bool GL>
+__device__ __forceinline__ float ld1(const float *p) {
+    if constexpr (GL) return __ldcg(p);
+    else return *p;
+}
+
+template <int DIM, int VEC, bool GL = false>
 __device__ __forceinline__ void gather(const Geometry &g, const float *pm, const float *pc,
                                        const float *pq, int e0, int x0, Nbr<DIM, VEC> &n) {
     const int X = g.X;
-    n.c = ldv<VEC>(pc + e0);
+    n.c = ldg_or_s<VEC, GL>(pc + e0);
     // x-neighbours of the end sites straight from shared memory (measured
     // faster than lane shuffles with the wrap fix-ups)
     const int lidx = (x0 == 0) ? e0 + X - 1 : e0 - 1;
     const int ridx = (x0 + VEC == X) ? e0 + VEC - X : e0 + VEC;
-    n.lw = pc[lidx];
-    n.rx = pc[ridx];
+    n.lw = ld1<GL>(pc + lidx);
+    n.rx = ld1<GL>(pc + ridx);
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         const float l = (k == 0) ? n.lw : n.c.v[k - 1];
@@ -143,14 +242,14 @@ __device__ __forceinline__ void gather(const Geometry &g, const float *pm, const
         const int P = g.P;
         const int ym = (e0 < X) ? e0 + P - X : e0 - X;
         const int yp = (e0 + X >= P) ? e0 + X - P : e0 + X;
-        n.ym = ldv<VEC>(pc + ym);
-        n.yp = ldv<VEC>(pc + yp);
+        n.ym = ldg_or_s<VEC, GL>(pc + ym);
+        n.yp = ldg_or_s<VEC, GL>(pc + yp);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) n.nb.v[k] += n.ym.v[k] + n.yp.v[k];
     }
     if constexpr (DIM >= 2) {
-        n.zm = ldv<VEC>(pm + e0);
-        n.zp = ldv<VEC>(pq + e0);
+        n.zm = ldg_or_s<VEC, GL>(pm + e0);
+        n.zp = ldg_or_s<VEC, GL>(pq + e0);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) n.nb.v[k] += n.zm.v[k] + n.zp.v[k];
     }
@@ -306,33 +405,48 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
     return pv;
 }
 
+template <int VEC>
+__device__ __forceinline__ Vec<VEC> ldv_global(const float *p) {
+    Vec<VEC> r;
+    if constexpr (VEC == 4) {
+        const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+        r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) r.v[k] = __ldcg(p + k);
+    }
+    return r;
+}
+
 // FIRST: the first pass of the trajectory (draws the momenta, sums K0);
 // LAST: the final pass (no drift; sums K1 and evaluates the proposal's
 // action).  Both are compiled apart so the other passes keep a lean loop.
+// The pass covers the slab of planes [z0, z0 + nzs) of the chain; plane
+// indices inside are slab-local, site indices (random-number counters)
+// absolute.
 template <int DIM, int VEC, int D, bool FIRST, bool LAST>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
-                         const Slots &sl, float *smem, const float4 *tab, Acc &acc) {
+                         const Slots &sl, float *smem, const float4 *tab, Acc &acc, int z0,
+                         int nzs) {
     constexpr int R = D + 4 + LAG;   // psi ring slots
-    constexpr int RP = D + 2 + LAG;  // p ring slots
     constexpr int RU = 3 + LAG;      // u ring slots
     const Geometry &g = A.g;
     const int P = g.P;
     float *psi_ring = smem;
-    float *p_ring = psi_ring + R * P;
-    float *u_ring = p_ring + RP * P;
+    float *u_ring = psi_ring + R * P;
     const int64_t cbase = (int64_t)chain * g.N;
     const float *__restrict__ gsrc = sel3(A, pc.src) + cbase;
-    float *__restrict__ gdst = sel3(A, pc.dst) + cbase;
-    float *__restrict__ gp = A.p + cbase;
+    float *__restrict__ gdst = sel3(A, pc.dst) + cbase + (int64_t)z0 * P;
+    float *__restrict__ gp = A.p + cbase + (int64_t)z0 * P;
     const int nz = g.nplanes;
     const int nvec = P / VEC;
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    // copy group s: psi plane s-2 (periodic) and p plane s-4
+    // copy group s: psi plane z0 + s - 2 (periodic)
     auto issue = [&](int s) {
         const int zpsi = s - 2;
-        if (zpsi <= nz + 1) {
-            const int zw = zpsi < 0 ? zpsi + nz : (zpsi >= nz ? zpsi - nz : zpsi);
+        if (zpsi <= nzs + 1) {
+            const int zw = wrap_plane(z0 + zpsi, nz);
             const float *src = gsrc + (int64_t)zw * P;
             float *dst = psi_ring + (unsigned)s % R * P;
             if constexpr (VEC == 4) {
@@ -341,38 +455,35 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 for (int v = tid; v < P; v += nt) cp_async4(dst + v, src + v);
             }
         }
-        const int zp = s - 4;
-        if (zp >= 0 && zp < nz && !FIRST) {   // the first pass draws p itself
-            const float *src = gp + (int64_t)zp * P;
-            float *dst = p_ring + (unsigned)s % RP * P;
-            if constexpr (VEC == 4) {
-                for (int v = tid; v < nvec; v += nt) cp_async16(dst + 4 * v, src + 4 * v);
-            } else {
-                for (int v = tid; v < P; v += nt) cp_async4(dst + v, src + v);
-            }
-        }
         cp_commit();
     };
-    // ring slot of psi plane z (z >= -2) and u plane z (z >= -1)
+    // ring slot of psi plane z (z >= -2) and u plane z (z >= -1), slab-local
     auto psi_slot = [&](int z) -> const float * { return psi_ring + (unsigned)(z + 2) % R * P; };
     auto u_slot = [&](int z) -> float * { return u_ring + (unsigned)(z + 4) % RU * P; };
 
     for (int s = 0; s <= D + 2; ++s) issue(s);
     int s_next = D + 3;
+    // momenta of the next force plane, loaded one plane ahead into registers
+    Vec<VEC> pn[NVMAX];
+    if constexpr (!FIRST) {
+#pragma unroll
+        for (int k = 0; k < NVMAX; ++k)
+            if (k < sl.nwarp) pn[k] = ldv_global<VEC>(gp + sl.e0[k]);
+    }
 
     const float Cf = prm.Cf, bJf = prm.bJf;
     ActConst kc;
     if constexpr (LAST) kc = act_const(prm);
 
-    for (int it = -1; it <= nz + LAG; ++it) {
+    for (int it = -1; it <= nzs + LAG; ++it) {
         cp_wait<D>();
         __syncthreads();
         issue(s_next++);
         // ---- u(it) = tanh(A psi + h') - psi on plane it ----
-        if (it <= nz) {
+        if (it <= nzs) {
             const float *pm = psi_slot(it - 1), *pcen = psi_slot(it), *pq = psi_slot(it + 1);
             float *uo = u_slot(it);
-            const int zw = it < 0 ? it + nz : (it >= nz ? it - nz : it);
+            const int zw = wrap_plane(z0 + it, nz);
 #pragma unroll
             for (int k = 0; k < NVMAX; ++k) {
                 if (k >= sl.nwarp) break;
@@ -397,9 +508,9 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     // the last pass's configuration is the proposal: its action
                     // from the neighbourhood already gathered (each plane once)
                     if constexpr (LAST) {
-                        if (it >= 0 && it < nz)
-                            vector_action<DIM, VEC>(A, kc, n, (int64_t)it * P + e0, 1.0f, pc.traj,
-                                                    A.seed, chain, tab, acc, &t);
+                        if (it >= 0 && it < nzs)
+                            vector_action<DIM, VEC>(A, kc, n, (int64_t)(z0 + it) * P + e0, 1.0f,
+                                                    pc.traj, A.seed, chain, tab, acc, &t);
                     }
                 }
             }
@@ -407,12 +518,12 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         if constexpr (LAG == 0) __syncthreads();
         // ---- F(z) = A u, kick and drift on plane z = it - 1 - LAG ----
         const int z = it - 1 - LAG;
-        if (z >= 0 && z < nz) {
+        if (z >= 0 && z < nzs) {
             const float *um = u_slot(z - 1), *uc = u_slot(z), *uq = u_slot(z + 1);
             const float *psz = psi_slot(z);
-            const float *ppz = p_ring + (unsigned)(z + 4) % RP * P;
             float *gpz = gp + (int64_t)z * P;
             float *gdz = gdst + (int64_t)z * P;
+            const bool more = z + 1 < nzs;
 #pragma unroll
             for (int k = 0; k < NVMAX; ++k) {
                 if (k >= sl.nwarp) break;
@@ -420,10 +531,12 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 Nbr<DIM, VEC> n;
                 gather<DIM, VEC>(g, um, uc, uq, e0, sl.x0[k], n);
                 Vec<VEC> pv;
-                if constexpr (FIRST)
-                    pv = draw_momenta<VEC>((int64_t)z * P + e0, pc.traj, chain, A.seed);
-                else
-                    pv = ldv<VEC>(ppz + e0);
+                if constexpr (FIRST) {
+                    pv = draw_momenta<VEC>((int64_t)(z0 + z) * P + e0, pc.traj, chain, A.seed);
+                } else {
+                    pv = pn[k];
+                    if (more) pn[k] = ldv_global<VEC>(gpz + P + e0);
+                }
                 if (FIRST && sl.valid[k]) {
 #pragma unroll
                     for (int q = 0; q < VEC; ++q)
@@ -442,10 +555,10 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                             acc_add(acc.K1, acc.K1lo, two_prod(pv.v[q], 0.5f * pv.v[q]));
                     } else {
                         const Vec<VEC> ps = ldv<VEC>(psz + e0);
-                        Vec<VEC> pn;
+                        Vec<VEC> pnew;
 #pragma unroll
-                        for (int q = 0; q < VEC; ++q) pn.v[q] = fmaf(pc.drift, pv.v[q], ps.v[q]);
-                        stv<VEC>(gdz + e0, pn);
+                        for (int q = 0; q < VEC; ++q) pnew.v[q] = fmaf(pc.drift, pv.v[q], ps.v[q]);
+                        stv<VEC>(gdz + e0, pnew);
                     }
                 }
             }
@@ -458,10 +571,11 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
 // Momentum refresh (Sec. 3): p ~ N(0,1) for every site of the chain, written
 // to global memory.  No barriers: every thread streams its own vectors.
 template <int VEC>
-__device__ void momenta_sweep(const FusedArgs &A, int chain, uint32_t traj, const Slots &sl) {
+__device__ void momenta_sweep(const FusedArgs &A, int chain, uint32_t traj, const Slots &sl,
+                              int z0, int z1) {
     const Geometry &g = A.g;
     float *gp = A.p + (int64_t)chain * g.N;
-    for (int z = 0; z < g.nplanes; ++z) {
+    for (int z = z0; z < z1; ++z) {
 #pragma unroll
         for (int k = 0; k < NVMAX; ++k) {
             if (k >= sl.nwarp) break;
@@ -488,20 +602,21 @@ __device__ void momenta_sweep(const FusedArgs &A, int chain, uint32_t traj, cons
 // Action S(sign*psi) (Sec. 2, Eq. phi_psi_substitution in the form
 // S = 1/2 psi.A psi - sum_i log 2cosh((A psi)_i + h'_i)) to FP64 accuracy in
 // double-float arithmetic, and the Sec. 4 estimators with one conditional
-// spin draw, over the chain stored in buffer `buf`.  No barriers: every
-// thread streams its own vectors, neighbours come from global memory (L1/L2).
+// spin draw, over the planes [z0, z1) of the chain stored in buffer `buf`.
+// No barriers: every thread streams its own vectors, neighbours come from
+// global memory (L1/L2).
 // (The proposal's action at the end of a trajectory is evaluated inside the
 // last force pass instead; this sweep serves the sign flip and the current
 // state.)
 template <int DIM, int VEC>
 __device__ void action_sweep(const FusedArgs &A, const ChainParams &prm, int chain, int buf,
                              float sign, uint32_t spin_traj, uint64_t seed, const Slots &sl,
-                             const float4 *tab, Acc &acc) {
+                             const float4 *tab, Acc &acc, int z0, int z1) {
     const Geometry &g = A.g;
     const int P = g.P, nz = g.nplanes;
     const float *psi = sel3(A, buf) + (int64_t)chain * g.N;
     const ActConst kc = act_const(prm);
-    for (int z = 0; z < nz; ++z) {
+    for (int z = z0; z < z1; ++z) {
         const float *pc = psi + (int64_t)z * P;
         const float *pm = psi + (int64_t)(z == 0 ? nz - 1 : z - 1) * P;
         const float *pq = psi + (int64_t)(z == nz - 1 ? 0 : z + 1) * P;
@@ -511,7 +626,7 @@ __device__ void action_sweep(const FusedArgs &A, const ChainParams &prm, int cha
             if (!sl.valid[k]) continue;
             const int e0 = sl.e0[k];
             Nbr<DIM, VEC> n;
-            gather<DIM, VEC>(g, pm, pc, pq, e0, sl.x0[k], n);
+            gather<DIM, VEC, true>(g, pm, pc, pq, e0, sl.x0[k], n);
             vector_action<DIM, VEC>(A, kc, n, (int64_t)z * P + e0, sign, spin_traj, seed, chain,
                                     tab, acc);
         }
@@ -536,9 +651,7 @@ template <int DIM, int VEC, int D>
 __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Schedule S) {
     extern __shared__ float4 smem_f4[];
     float *smem = reinterpret_cast<float *>(smem_f4);
-    constexpr int R = D + 4 + LAG, RP = D + 2 + LAG;
     const Geometry &g = A.g;
-    static_assert(R + RP + 3 + LAG == 2 * D + 9 + 3 * LAG, "ring layout");
     const size_t rb = ring_bytes(g.P, D);
     // The launch's shared-memory size says where the log(1 + e^-y) table
     // lives: copied into shared memory when the host gave room for it (it
@@ -551,16 +664,23 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
     const float4 *tab = tab_in_smem ? tab_s : A.lpe_tab;
     double *red = reinterpret_cast<double *>(smem + rb / 4 + (tab_in_smem ? LOG1PEXP_NODES * 4 : 0));
     int *bcast = reinterpret_cast<int *>(red + 32 * 8);
+    double *xch = red + 32 * 8 + 2;   // two exchange buffers of XCH_WORDS
 
-    const int chain = A.chain0 + blockIdx.x;
-    if (chain >= A.n_chains) return;
+    // CTAs per chain (the launch's cluster size) and this CTA's slab
+    const int cs = cluster_size(), cr = cluster_rank();
+    const int chain = A.chain0 + (int)(blockIdx.x / (unsigned)cs);
+    if (chain >= A.n_chains) return;   // uniform over the cluster
+    if (cs != A.cs && threadIdx.x == 0 && cr == 0) atomicOr(A.err, KERR_BOUNDS);
+    const int nz = g.nplanes;
+    const int z0 = (int)((int64_t)cr * nz / cs), z1 = (int)((int64_t)(cr + 1) * nz / cs);
+    const bool lead = cr == 0;   // writes the chain's state
     ChainState *st = A.state + chain;
     const ChainParams prm = A.params[chain];
     const double invN = 1.0 / (double)g.N;
     const Slots sl = make_slots<VEC>(g);
 
     if (A.mode == MODE_MOMENTA) {
-        momenta_sweep<VEC>(A, chain, A.traj0, sl);
+        momenta_sweep<VEC>(A, chain, A.traj0, sl, z0, z1);
         return;
     }
     if (tab_in_smem) {
@@ -571,19 +691,23 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
     if (A.mode == MODE_EVAL) {
         Acc acc = acc_zero();
         const int start = st->start;
-        action_sweep<DIM, VEC>(A, prm, chain, start, 1.0f, TRAJ_INIT, 0, sl, tab, acc);
+        action_sweep<DIM, VEC>(A, prm, chain, start, 1.0f, TRAJ_INIT, 0, sl, tab, acc, z0, z1);
         double v[5] = {acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
                        kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
-        block_sum<5>(v, red);
-        if (threadIdx.x == 0) {
+        chain_sum<5>(v, red, xch, cs);
+        if (threadIdx.x == 0 && lead) {
             st->S = v[0];
             set_obs(st, prm, v[1], v[2], v[3], v[4], invN);
             st->prop = start;
         }
+        if (cs > 1) cluster_barrier();   // no CTA leaves while its buffer may be read
         return;
     }
 
+    // the chain's state as every CTA of the cluster tracks it (the same
+    // values in all of them: they add the same sums in the same order)
     int start = st->start;
+    double S_cur = st->S;
     for (int k = 0; k < A.n_traj; ++k) {
         const uint32_t traj = A.traj0 + (uint32_t)k;
         Acc acc = acc_zero();
@@ -599,38 +723,44 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
             pc.last = (j == S.n_pass - 1);
             pc.traj = traj;
             if (pc.first && pc.last)
-                run_pass<DIM, VEC, D, true, true>(A, pc, prm, chain, sl, smem, tab, acc);
+                run_pass<DIM, VEC, D, true, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
             else if (pc.first)
-                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc);
+                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
             else if (pc.last)
-                run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc);
+                run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
             else
-                run_pass<DIM, VEC, D, false, false>(A, pc, prm, chain, sl, smem, tab, acc);
+                run_pass<DIM, VEC, D, false, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
+            // the next pass reads (and the one after rewrites) the planes
+            // beyond this slab's ends, written by the neighbouring CTAs
+            if (cs > 1) cluster_barrier();
         }
         const int prop = buf_loc(start, S.n_pass - 1);
         double v[7] = {acc_val(acc.K0, acc.K0lo), acc_val(acc.K1, acc.K1lo),
                        acc_val(acc.S, acc.Slo), kahan_val(acc.sT, acc.cT),
                        kahan_val(acc.sAT, acc.cAT), kahan_val(acc.sHT, acc.cHT), (double)acc.sS};
-        block_sum<7>(v, red);
+        chain_sum<7>(v, red, xch, cs);
         if (threadIdx.x == 0) {
-            const double S0 = st->S;
+            const double S0 = S_cur;
             const double dH = (v[1] + v[2]) - (v[0] + S0);
             const double logu = accept_logu(traj, (uint32_t)chain, A.seed, PURPOSE_ACC);
             const bool accd = logu < -dH;
-            st->prop = prop;
-            st->rec[ISING_REC_DH] = dH;
-            st->rec[ISING_REC_LOGU] = logu;
-            st->rec[ISING_REC_ACCEPTED] = accd ? 1.0 : 0.0;
-            st->rec[ISING_REC_K0] = v[0];
-            st->rec[ISING_REC_S0] = S0;
-            st->rec[ISING_REC_K1] = v[1];
-            st->rec[ISING_REC_S1] = v[2];
-            st->rec[ISING_REC_FLIPPED] = 0.0;
-            if (accd) {
-                st->start = prop;
-                st->S = v[2];
-                set_obs(st, prm, v[3], v[4], v[5], v[6], invN);
+            if (lead) {
+                st->prop = prop;
+                st->rec[ISING_REC_DH] = dH;
+                st->rec[ISING_REC_LOGU] = logu;
+                st->rec[ISING_REC_ACCEPTED] = accd ? 1.0 : 0.0;
+                st->rec[ISING_REC_K0] = v[0];
+                st->rec[ISING_REC_S0] = S0;
+                st->rec[ISING_REC_K1] = v[1];
+                st->rec[ISING_REC_S1] = v[2];
+                st->rec[ISING_REC_FLIPPED] = 0.0;
+                if (accd) {
+                    st->start = prop;
+                    st->S = v[2];
+                    set_obs(st, prm, v[3], v[4], v[5], v[6], invN);
+                }
             }
+            if (accd) S_cur = v[2];
             bcast[0] = accd ? prop : start;
         }
         __syncthreads();
@@ -639,17 +769,20 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
         // ---- optional global sign flip psi -> -psi (Sec. 3, ergodicity) ----
         if (A.flip_every > 0 && ((traj + 1) % (uint32_t)A.flip_every) == 0) {
             Acc fa = acc_zero();
-            action_sweep<DIM, VEC>(A, prm, chain, start, -1.0f, traj, A.seed, sl, tab, fa);
+            action_sweep<DIM, VEC>(A, prm, chain, start, -1.0f, traj, A.seed, sl, tab, fa, z0, z1);
             double w[5] = {acc_val(fa.S, fa.Slo), kahan_val(fa.sT, fa.cT),
                            kahan_val(fa.sAT, fa.cAT), kahan_val(fa.sHT, fa.cHT), (double)fa.sS};
-            block_sum<5>(w, red);
+            chain_sum<5>(w, red, xch + XCH_WORDS, cs);
             if (threadIdx.x == 0) {
                 const double lu = accept_logu(traj, (uint32_t)chain, A.seed, PURPOSE_FLIP);
-                const bool fl = lu < -(w[0] - st->S);
+                const bool fl = lu < -(w[0] - S_cur);
                 if (fl) {
-                    st->S = w[0];
-                    set_obs(st, prm, w[1], w[2], w[3], w[4], invN);
-                    st->rec[ISING_REC_FLIPPED] = 1.0;
+                    S_cur = w[0];
+                    if (lead) {
+                        st->S = w[0];
+                        set_obs(st, prm, w[1], w[2], w[3], w[4], invN);
+                        st->rec[ISING_REC_FLIPPED] = 1.0;
+                    }
                 }
                 bcast[1] = fl ? 1 : 0;
             }
@@ -658,16 +791,19 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
                 // -psi goes to the buffer that is neither current nor the proposal,
                 // so the MD end point stays readable
                 const int f = (start != prop) ? 3 - start - prop : (start + 1) % 3;
-                const float *gs = sel3(A, start) + (int64_t)chain * g.N;
-                float *gf = sel3(A, f) + (int64_t)chain * g.N;
-                for (int64_t i = threadIdx.x; i < g.N; i += blockDim.x) gf[i] = -gs[i];
+                const int64_t off = (int64_t)chain * g.N + (int64_t)z0 * g.P;
+                const int64_t cnt = (int64_t)(z1 - z0) * g.P;
+                const float *gs = sel3(A, start) + off;
+                float *gf = sel3(A, f) + off;
+                for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) gf[i] = -gs[i];
                 start = f;
-                if (threadIdx.x == 0) st->start = f;
+                if (threadIdx.x == 0 && lead) st->start = f;
+                if (cs > 1) cluster_barrier();   // the next pass reads the other slabs' planes
             }
             __syncthreads();
         }
         // ---- measurement: a repeated configuration repeats its measurement ----
-        if (threadIdx.x == 0 && (int64_t)traj >= (int64_t)A.n_therm) {
+        if (threadIdx.x == 0 && lead && (int64_t)traj >= (int64_t)A.n_therm) {
             double *sm = st->sums;
             const double dH = st->rec[ISING_REC_DH];
             sm[ISING_SUM_NMEAS] += 1.0;
@@ -683,6 +819,7 @@ __global__ void __launch_bounds__(256, 2) fused_lattice_kernel(FusedArgs A, Sche
         }
         __syncthreads();
     }
+    if (cs > 1) cluster_barrier();   // no CTA leaves while its exchange buffers may be read
 }
 
 // Shared-memory size of a launch: with the table if that leaves as many CTAs
@@ -724,7 +861,7 @@ cudaError_t kernel_node(const FusedArgs &a, int threads, cudaKernelNodeParams *n
     }
     const int smem = launch_smem(kern, a.g, D, threads);
     np->func = reinterpret_cast<void *>(kern);
-    np->gridDim = dim3((unsigned)(a.n_chains - a.chain0), 1, 1);
+    np->gridDim = dim3((unsigned)((a.n_chains - a.chain0) * a.cs), 1, 1);
     np->blockDim = dim3((unsigned)threads, 1, 1);
     np->sharedMemBytes = (unsigned)smem;
     np->kernelParams = args;
@@ -802,6 +939,42 @@ int fused_lattice_valid_launch(const Geometry &g, int threads, int depth) {
     return fused_lattice_smem_bytes(g, depth, vec) <= 227 * 1024;
 }
 
+// A chain split over cs CTAs: cs in {1, 2, 4, 8}, a 2D or 3D lattice with at
+// least two planes per slab, and a cluster of cs such CTAs must fit on the
+// device (asked of the occupancy calculator).
+int fused_lattice_valid_split(const Geometry &g, int threads, int depth, int cs) {
+    if (cs == 1) return fused_lattice_valid_launch(g, threads, depth);
+    if (cs != 2 && cs != 4 && cs != MAX_CS) return 0;
+    if (g.dim < 2 || g.nplanes < 2 * cs) return 0;
+    if (!fused_lattice_valid_launch(g, threads, depth)) return 0;
+    FusedArgs a{};
+    a.g = g;
+    a.n_chains = 1;
+    a.cs = cs;
+    Schedule sched{};
+    cudaKernelNodeParams np;
+    void *args[2] = {&a, &sched};
+    if (fused_lattice_node(a, threads, depth, &np, args) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)cs, 1, 1);
+    cfg.blockDim = np.blockDim;
+    cfg.dynamicSmemBytes = np.sharedMemBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, np.func, &cfg);
+    cudaGetLastError();
+    return e == cudaSuccess && n >= 1;
+}
+
 cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
                                  int depth, cudaStream_t s) {
     cudaKernelNodeParams np;
@@ -809,7 +982,30 @@ cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int 
     cudaError_t e = fused_lattice_node(a, threads, depth, &np, args);
     if (e != cudaSuccess) return e;
     if (np.gridDim.x == 0) return cudaSuccess;
-    return cudaLaunchKernel(np.func, np.gridDim, np.blockDim, np.kernelParams, np.sharedMemBytes, s);
+    if (a.cs == 1)
+        return cudaLaunchKernel(np.func, np.gridDim, np.blockDim, np.kernelParams,
+                                np.sharedMemBytes, s);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = np.gridDim;
+    cfg.blockDim = np.blockDim;
+    cfg.dynamicSmemBytes = np.sharedMemBytes;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, np.func, np.kernelParams);
+}
+
+cudaError_t fused_lattice_node_cluster(cudaGraphNode_t node, int cs) {
+    cudaLaunchAttributeValue v{};
+    v.clusterDim.x = (unsigned)cs;
+    v.clusterDim.y = 1;
+    v.clusterDim.z = 1;
+    return cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeClusterDimension, &v);
 }
 
 cudaError_t launch_tanh_selftest(const float *x, float *y, int64_t n, cudaStream_t s) {

@@ -63,6 +63,7 @@ struct FusedArgs {
     int mode;                // 0 trajectories, 1 evaluate current state, 2 write momenta
     int chain0;              // first chain of this launch
     int n_chains;
+    int cs;                  // CTAs per chain (the launch's cluster size; lattice kernel)
     int *err;
 };
 
@@ -84,6 +85,10 @@ cudaError_t fused_lattice_node(const FusedArgs &a, int threads, int depth,
                                cudaKernelNodeParams *np, void **args);
 // 1 if (threads, depth) is a valid launch shape for this geometry.
 int fused_lattice_valid_launch(const Geometry &g, int threads, int depth);
+// 1 if a chain may be split over cs CTAs (a thread-block cluster) at that shape.
+int fused_lattice_valid_split(const Geometry &g, int threads, int depth, int cs);
+// Cluster size of a graph kernel node made from fused_lattice_node (cs > 1).
+cudaError_t fused_lattice_node_cluster(cudaGraphNode_t node, int cs);
 int fused_lattice_pick(const Geometry &g, int *threads, int *depth);
 
 // Infinite-range (all-to-all) model, FP32 form: the same arguments, modes and

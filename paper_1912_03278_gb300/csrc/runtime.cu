@@ -39,8 +39,8 @@ struct ising_hmc {
     double *d_J = nullptr;
     float *d_lpe = nullptr;
     int *d_err = nullptr;
-    // launch shape of the fused kernel
-    int threads = 0, depth = 0;
+    // launch shape of the fused kernel: threads per CTA, prefetch depth, CTAs per chain
+    int threads = 0, depth = 0, cs = 1;
     // dense couplings on the tensor cores
     bool dense_tc = false;
     int b_pad = 0;
@@ -328,6 +328,7 @@ static FusedArgs fused_args(ising_hmc *h) {
     a.flip_every = h->flip_every;
     a.chain0 = 0;
     a.n_chains = h->n_chains;
+    a.cs = is_fp32_lattice(h) ? h->cs : 1;
     a.err = h->d_err;
     return a;
 }
@@ -1216,6 +1217,9 @@ ising_status ising_hmc_set_launch(ising_hmc_t *h, int threads, int depth) {
     if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "launch shape applies to the FP32 lattice form");
     if (!fused_lattice_valid_launch(h->g, threads, depth))
         return fail(h, ISING_EINVAL, "invalid launch shape threads=%d depth=%d", threads, depth);
+    if (h->cs > 1 && !fused_lattice_valid_split(h->g, threads, depth, h->cs))
+        return fail(h, ISING_EINVAL, "launch shape threads=%d depth=%d does not fit a split of %d",
+                    threads, depth, h->cs);
     h->threads = threads;
     h->depth = depth;
     return ISING_OK;
@@ -1228,9 +1232,18 @@ ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth
     return ISING_OK;
 }
 
-// Autotuner: time one trajectory of every valid (threads, depth) on a
-// temporary copy of the handle's geometry and parameters (so the handle's own
-// chains do not move) and keep the fastest.
+ising_status ising_hmc_set_chain_split(ising_hmc_t *h, int ctas) {
+    if (!h) return ISING_EINVAL;
+    if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "chain split applies to the FP32 lattice form");
+    if (!fused_lattice_valid_split(h->g, h->threads, h->depth, ctas))
+        return fail(h, ISING_EINVAL, "invalid chain split %d (threads=%d depth=%d, %d planes)", ctas,
+                    h->threads, h->depth, h->g.nplanes);
+    h->cs = ctas;
+    return ISING_OK;
+}
+
+int ising_hmc_get_chain_split(const ising_hmc_t *h) { return h ? h->cs : -1; }
+
 ising_status ising_hmc_dense_forces(ising_hmc_t *h, int n) {
     if (!h) return ISING_EINVAL;
     if (!is_dense_tc(h)) return fail(h, ISING_EINVAL, "dense_forces applies to the BF16 dense form");
@@ -1243,17 +1256,10 @@ ising_status ising_hmc_dense_forces(ising_hmc_t *h, int n) {
     return ISING_OK;
 }
 
-ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
-    if (!h) return ISING_EINVAL;
-    if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "autotune applies to the FP32 lattice form");
-    if (reps < 1) reps = 1;
-    ising_status st = ising_hmc_sync(h);
-    if (st != ISING_OK) return st;
-    // temporary handle: same lattice and first chains' parameters, at most 2 waves of CTAs
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int nt = std::min(h->n_chains, std::max(1, 2 * nsm));
+// A temporary FP32 lattice handle with h's lattice, integrator and the
+// parameters of h's first nt chains, on h's stream (for the autotuners: the
+// handle's own chains never move).
+static ising_status clone_for_tuning(ising_hmc *h, int nt, ising_hmc **out) {
     ising_hmc_config cfg{};
     cfg.kind = ISING_KIND_LATTICE;
     cfg.dim = h->dim;
@@ -1278,35 +1284,83 @@ ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     cfg.precision = ISING_PREC_FP32;
     cfg.integrator = h->integrator;
     cfg.stream = h->stream;
+    ising_status st = ising_hmc_create(&cfg, out);
+    if (st == ISING_OK) {
+        (*out)->threads = h->threads;
+        (*out)->depth = h->depth;
+        (*out)->cs = h->cs;
+    }
+    return st;
+}
+
+// Time of `reps` trajectories (after one untimed) of handle t, in ms per
+// trajectory; negative if the launch failed.
+static double time_trajectories(ising_hmc *t, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+    if (ising_hmc_trajectories(t, 1, 99) != ISING_OK) return -1.0;   // warm-up
+    cudaEventRecord(e0, t->stream);
+    if (ising_hmc_trajectories(t, reps, 99) != ISING_OK) return -1.0;
+    cudaEventRecord(e1, t->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+}
+
+// Autotuner: time one trajectory of every valid (threads, depth) on a
+// temporary copy of the handle's geometry and parameters (so the handle's own
+// chains do not move) and keep the fastest; then try splitting every chain
+// over 2, 4 and 8 CTAs at the best thread count and every depth.
+ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
+    if (!h) return ISING_EINVAL;
+    if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "autotune applies to the FP32 lattice form");
+    if (reps < 1) reps = 1;
+    ising_status st = ising_hmc_sync(h);
+    if (st != ISING_OK) return st;
+    // temporary handle: same lattice and first chains' parameters, at most 2 waves of CTAs
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nt = std::min(h->n_chains, std::max(1, 2 * nsm));
     ising_hmc *t = nullptr;
-    st = ising_hmc_create(&cfg, &t);
+    st = clone_for_tuning(h, nt, &t);
     if (st != ISING_OK) return fail(h, st, "autotune: %s", ising_hmc_last_create_error());
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double best = 1e300;
-    int bt = h->threads, bd = h->depth;
+    int bt = h->threads, bd = h->depth, bc = 1;
     const int cand_t[] = {32, 64, 96, 128, 160, 192, 224, 256};
     const int cand_d[] = {1, 2, 4};
+    const int cand_c[] = {2, 4, 8};
+    t->cs = 1;
     for (int th : cand_t) {
         for (int dp : cand_d) {
             if (!fused_lattice_valid_launch(h->g, th, dp)) continue;
             t->threads = th;
             t->depth = dp;
-            if (ising_hmc_trajectories(t, 1, 99) != ISING_OK) continue;  // warm-up
-            cudaEventRecord(e0, t->stream);
-            ising_hmc_trajectories(t, reps, 99);
-            cudaEventRecord(e1, t->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms / reps < best) {
-                best = ms / reps;
+            const double ms = time_trajectories(t, reps, e0, e1);
+            if (ms > 0 && ms < best) {
+                best = ms;
                 bt = th;
                 bd = dp;
+            }
+        }
+    }
+    const int th = bt;
+    for (int c : cand_c) {
+        for (int dp : cand_d) {
+            if (!fused_lattice_valid_split(h->g, th, dp, c)) continue;
+            t->threads = th;
+            t->depth = dp;
+            t->cs = c;
+            const double ms = time_trajectories(t, reps, e0, e1);
+            if (ms > 0 && ms < best) {
+                best = ms;
+                bd = dp;
+                bc = c;
             }
         }
     }
@@ -1315,6 +1369,7 @@ ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     ising_hmc_destroy(t);
     h->threads = bt;
     h->depth = bd;
+    h->cs = bc;
     if (best_ms) *best_ms = best;
     return ISING_OK;
 }
@@ -1329,7 +1384,7 @@ struct ising_group {
     std::vector<FusedArgs> args;
     std::vector<std::array<void *, 2>> argv;
     std::vector<cudaGraphNode_t> nodes;
-    std::vector<int> shape;  // threads, depth per member at instantiation
+    std::vector<int> shape;  // threads, depth, CTAs per chain of every member at instantiation
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t stream = nullptr;
@@ -1360,7 +1415,7 @@ static ising_status group_build_graph(ising_group *g) {
     g->args.resize(n);
     g->argv.resize(n);
     g->nodes.resize(n);
-    g->shape.assign(2 * n, 0);
+    g->shape.assign(3 * n, 0);
     if (cudaGraphCreate(&g->graph, 0) != cudaSuccess) return gfail(g, ISING_ECUDA, "graph create failed");
     for (size_t i = 0; i < n; ++i) {
         ising_hmc *h = g->m[i];
@@ -1371,9 +1426,11 @@ static ising_status group_build_graph(ising_group *g) {
         cudaKernelNodeParams np;
         cudaError_t e = fused_lattice_node(g->args[i], h->threads, h->depth, &np, g->argv[i].data());
         if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g->nodes[i], g->graph, nullptr, 0, &np);
+        if (e == cudaSuccess && h->cs > 1) e = fused_lattice_node_cluster(g->nodes[i], h->cs);
         if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph node: %s", cudaGetErrorString(e));
-        g->shape[2 * i] = h->threads;
-        g->shape[2 * i + 1] = h->depth;
+        g->shape[3 * i] = h->threads;
+        g->shape[3 * i + 1] = h->depth;
+        g->shape[3 * i + 2] = h->cs;
     }
     cudaError_t e = cudaGraphInstantiate(&g->exec, g->graph, 0);
     if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -1428,7 +1485,8 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
     if (n == 0) return ISING_OK;
     // rebuild if a member's launch shape changed (autotune, set_launch)
     for (size_t i = 0; i < g->m.size(); ++i)
-        if (g->shape[2 * i] != g->m[i]->threads || g->shape[2 * i + 1] != g->m[i]->depth) {
+        if (g->shape[3 * i] != g->m[i]->threads || g->shape[3 * i + 1] != g->m[i]->depth ||
+            g->shape[3 * i + 2] != g->m[i]->cs) {
             ising_status st = group_build_graph(g);
             if (st != ISING_OK) return st;
             break;
@@ -1476,6 +1534,92 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
         if (cudaStreamWaitEvent(h->stream, g->ev, 0) != cudaSuccess)
             return gfail(g, ISING_ECUDA, "group: stream ordering failed");
     return ISING_OK;
+}
+
+// Group autotuner: the members' chains are split over CTAs by what the
+// whole mixed launch gains, not what a size gains alone (a size that fills
+// the GPU alone competes with the others in the group).  On temporary copies
+// of every member (all their chains, same launch shapes), one member at a
+// time, largest work first, each split in {1, 2, 4, 8} that fits is timed on
+// the whole group's launch and the fastest kept; two rounds.
+ising_status ising_group_autotune(ising_group_t *g, int reps, double *best_ms) {
+    if (!g) return ISING_EINVAL;
+    if (reps < 1) reps = 1;
+    ising_status st = ising_group_sync(g);
+    if (st != ISING_OK) return st;
+    const size_t n = g->m.size();
+    int64_t need = 0;
+    for (ising_hmc *h : g->m) need += h->bytes;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || (double)need > 0.8 * (double)fr)
+        return gfail(g, ISING_ENOMEM, "group autotune: temporary copies need %lld bytes",
+                     (long long)need);
+    std::vector<ising_hmc *> tmp(n, nullptr);
+    ising_group *tg = nullptr;
+    auto cleanup = [&]() {
+        if (tg) ising_group_destroy(tg);
+        for (ising_hmc *t : tmp)
+            if (t) ising_hmc_destroy(t);
+    };
+    for (size_t i = 0; i < n; ++i) {
+        st = clone_for_tuning(g->m[i], g->m[i]->n_chains, &tmp[i]);
+        if (st != ISING_OK) {
+            cleanup();
+            return gfail(g, st, "group autotune: %s", ising_hmc_last_create_error());
+        }
+    }
+    st = ising_group_create(tmp.data(), (int)n, &tg);
+    if (st != ISING_OK) {
+        cleanup();
+        return gfail(g, st, "group autotune: %s", g_create_err);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_group = [&]() -> double {
+        if (ising_group_trajectories(tg, 1, 99) != ISING_OK) return -1.0;
+        cudaEventRecord(e0, tg->stream);
+        if (ising_group_trajectories(tg, reps, 99) != ISING_OK) return -1.0;
+        cudaEventRecord(e1, tg->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            return -1.0;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / reps;
+    };
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const double wa = (double)g->m[a]->N * g->m[a]->n_chains * g->m[a]->sched.n_pass;
+        const double wb = (double)g->m[b]->N * g->m[b]->n_chains * g->m[b]->sched.n_pass;
+        return wa > wb;
+    });
+    double best = time_group();
+    for (int round = 0; round < 2; ++round) {
+        for (size_t i : order) {
+            ising_hmc *t = tmp[i];
+            const int keep = t->cs;
+            int bc = keep;
+            for (int c : {1, 2, 4, 8}) {
+                if (c == keep || !fused_lattice_valid_split(t->g, t->threads, t->depth, c)) continue;
+                t->cs = c;
+                const double ms = time_group();
+                if (ms > 0 && (best < 0 || ms < best)) {
+                    best = ms;
+                    bc = c;
+                }
+            }
+            t->cs = bc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t i = 0; i < n; ++i) g->m[i]->cs = tmp[i]->cs;
+    cleanup();
+    if (best_ms) *best_ms = best;
+    return best > 0 ? ISING_OK : gfail(g, ISING_ECUDA, "group autotune: no launch succeeded");
 }
 
 ising_status ising_group_sync(ising_group_t *g) {

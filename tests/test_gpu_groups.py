@@ -47,6 +47,59 @@ def test_group_matches_members_run_alone():
             s.close()
 
 
+def test_group_with_split_members_matches_members_run_alone():
+    def members():
+        out = [pkg.IsingHMC(**kw) for kw in _members()]
+        out.append(pkg.IsingHMC(dim=3, L=(32, 32, 16), beta=0.2217, h=0.05, eps=0.1, n_md=5,
+                                n_chains=3, flip_every=2))
+        out[1].set_chain_split(2)   # 3D 8^3, slabs of 4 planes
+        out[-1].set_chain_split(8)
+        return out
+    alone, mixed = members(), members()
+    grp = pkg.IsingGroup(mixed)
+    try:
+        for s in alone:
+            s.trajectories(5, 77)
+        grp.trajectories(3, 77)
+        grp.trajectories(2, 77)
+        grp.sync()
+        for a, b in zip(alone, mixed):
+            assert np.array_equal(a.state(), b.state())
+            assert np.array_equal(a.chain_sums(), b.chain_sums())
+        # a split changed between calls: the group rebuilds its graph
+        mixed[-1].set_chain_split(4)
+        alone[-1].set_chain_split(4)
+        grp.trajectories(2, 78)
+        alone[-1].trajectories(2, 78)
+        assert np.array_equal(alone[-1].state(), mixed[-1].state())
+    finally:
+        grp.close()
+        for s in alone + mixed:
+            s.close()
+
+
+def test_group_autotune_sets_valid_splits_and_keeps_chains():
+    sims = [pkg.IsingHMC(dim=3, L=(L, L, L), beta=0.2217, h=0.05, eps=0.1, n_md=4, n_chains=8)
+            for L in (16, 32, 48)]
+    grp = pkg.IsingGroup(sims)
+    try:
+        before = [s.state() for s in sims]
+        ms = grp.autotune(reps=1)
+        assert ms > 0
+        for s, b in zip(sims, before):
+            assert s.chain_split in (1, 2, 4, 8)
+            assert np.array_equal(b, s.state())
+            assert s.traj_index == 0
+        grp.trajectories(2, 4)
+        grp.sync()
+        for s in sims:
+            assert np.all(np.isfinite(s.state()))
+    finally:
+        grp.close()
+        for s in sims:
+            s.close()
+
+
 def test_group_then_member_calls_stay_ordered():
     sims = [pkg.IsingHMC(**kw) for kw in _members()[:2]]
     ref = [pkg.IsingHMC(**kw) for kw in _members()[:2]]
@@ -73,6 +126,7 @@ def test_autotune_picks_valid_shape_and_keeps_chain():
         assert ms > 0
         t, d = sim.launch
         assert 32 <= t <= 256 and d in (1, 2, 4)
+        assert sim.chain_split in (1, 2, 4, 8)
         assert np.array_equal(before, sim.state())   # the handle's chains did not move
         assert sim.traj_index == 0
         sim.trajectories(2, 9)

@@ -51,7 +51,7 @@ def _count_near_ties(model, psi, form, seed, chain, traj):
 
 def _parity_setup(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,), C=None,
                   eps=0.1, n_md=5, prec=FP32, integrator=0, flip_every=0, traj=3, seed=11,
-                  psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0, launch=None):
+                  psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0, launch=None, split=None):
     """Create a handle at a common start state; returns the context of one
     parity case (the handle and everything the oracle needs)."""
     n_chains = len(betas)
@@ -79,6 +79,9 @@ def _parity_setup(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,),
         if launch is not None:
             sim.set_launch(*launch)
             assert sim.launch == tuple(launch)
+        if split is not None:
+            sim.set_chain_split(split)
+            assert sim.chain_split == split
         sim.set_state(psi0, next_traj=traj)
         for k in range(n_traj - 1):
             sim.trajectories(1, seed)
@@ -255,6 +258,8 @@ def test_mixed_size_group_launch_against_oracle():
         dict(dim=3, L=(6, 5, 7), betas=(0.2,), h=0.0),
         dict(dim=2, L=(32, 32), betas=(0.4,), h=0.05, launch=(32, 1)),
         dict(dim=3, L=(16, 16, 16), betas=(0.2217, 0.25), h=0.05),
+        dict(dim=3, L=(32, 32, 16), betas=(0.2217,), h=0.05, split=4),
+        dict(dim=3, L=(24, 24, 12), betas=(0.23, 0.21), h=0.05, split=2),
     ]
     ctxs = []
     try:
@@ -277,6 +282,80 @@ def test_mixed_size_group_launch_against_oracle():
         _parity_after(c)
     for c in ctxs:
         _parity_check(c)
+
+
+# ------------------------------------------- chains split over a CTA cluster ----
+# With a chain split over a cluster of CTAs every CTA streams a slab of planes
+# and reads the planes beyond its slab's ends from the previous pass; the
+# per-chain sums are added across the cluster in rank order.
+@pytest.mark.parametrize("dim,L,split,extra", [
+    (3, (48, 48, 8), 2, {}),                            # slabs of 4 planes, 3 vectors per thread
+    (3, (20, 12, 10), 4, {}),                           # ragged slabs: 2, 3, 2, 3 planes
+    (3, (64, 64, 16), 8, {}),                           # slabs of 2 planes, 4 vectors per thread
+    (2, (1024, 16), 8, {}),                             # 2D rows: slabs of 2 rows
+    (2, (1001, 12), 4, {}),                             # scalar path, ragged vectors, 3-row slabs
+    (3, (8, 8, 8), 4, dict(integrator=1)),              # Omelyan
+    (3, (16, 16, 16), 2, dict(launch=(64, 4))),         # explicit launch shape, depth 4
+])
+def test_fp32_split_chains(dim, L, split, extra):
+    one_trajectory_parity(dim=dim, L=L, betas=(0.30, 0.2217), h=0.05, eps=0.08, n_md=6,
+                          split=split, **extra)
+
+
+def test_fp32_split_with_site_fields_flip_and_several_trajectories():
+    N = 16 * 12 * 10
+    h = workloads.dense_fields(N, sigma=0.2, seed=9)
+    one_trajectory_parity(dim=3, L=(16, 12, 10), betas=(0.25, 0.2), h=h, eps=0.08, n_md=5,
+                          n_traj=3, traj=0, split=4)
+    rec = one_trajectory_parity(dim=3, L=(12, 12, 8), betas=(0.5, 0.45), h=0.0, eps=0.1, n_md=4,
+                                flip_every=1, traj=0, split=2)
+    assert np.all(rec[:, 7] == 1.0)  # S(-psi) = S(psi) at h = 0: always accepted
+
+
+@pytest.mark.parametrize("split", [2, 4, 8])
+def test_split_is_bitwise_in_psi_and_close_in_sums(split):
+    """psi and p are computed by the same per-site arithmetic whatever the
+    split, so the chains agree bit for bit; the per-chain sums differ only in
+    how sites are grouped into per-thread partial sums (double-float energies:
+    ~1e-12 relative; FP32 Kahan estimator sums: ~1e-7, inside the 1e-6 the
+    FP32 observables are held to)."""
+    kw = dict(dim=3, L=(24, 24, 16), beta=np.array([0.2217, 0.24, 0.2]), h=0.05, eps=0.09,
+              n_md=6, n_chains=3, flip_every=2)
+    a = pkg.IsingHMC(**kw)
+    b = pkg.IsingHMC(**kw)
+    try:
+        b.set_chain_split(split)
+        a.trajectories(6, 21)
+        b.trajectories(4, 21)
+        b.trajectories(2, 21)
+        assert np.array_equal(a.state(), b.state())
+        assert np.array_equal(a.state(pkg.ISING_STATE_P_END), b.state(pkg.ISING_STATE_P_END))
+        ra, rb = a.records(), b.records()
+        assert np.array_equal(ra[:, 2], rb[:, 2])
+        np.testing.assert_allclose(rb[:, [0, 3, 4, 5, 6]], ra[:, [0, 3, 4, 5, 6]], rtol=1e-11,
+                                   atol=1e-7)
+        np.testing.assert_allclose(b.chain_sums(), a.chain_sums(), rtol=0, atol=1e-6)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_invalid_splits_rejected():
+    sim = pkg.IsingHMC(dim=3, L=(8, 8, 6), beta=0.22, eps=0.1, n_md=2)
+    try:
+        for bad in (3, 0, 16, 4):   # 4: 6 planes give slabs below two planes
+            with pytest.raises(pkg.IsingError):
+                sim.set_chain_split(bad)
+        sim.set_chain_split(2)
+        assert sim.chain_split == 2
+    finally:
+        sim.close()
+    ring = pkg.IsingHMC(dim=1, L=(64,), beta=0.4, eps=0.1, n_md=2)
+    try:
+        with pytest.raises(pkg.IsingError):
+            ring.set_chain_split(2)
+    finally:
+        ring.close()
 
 
 # ------------------------------------------------------------ plain FP64 ----
