@@ -1332,7 +1332,7 @@ ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     cudaEventCreate(&e1);
     double best = 1e300;
     int bt = h->threads, bd = h->depth, bc = 1;
-    const int cand_t[] = {32, 64, 96, 128, 160, 192, 224, 256};
+    const int cand_t[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
     const int cand_d[] = {1, 2, 4};
     const int cand_c[] = {2, 4, 8};
     t->cs = 1;
