@@ -224,10 +224,11 @@ int64_t ising_hmc_launch_count(const ising_hmc_t *h);
 /* Synchronise the handle's stream; ETIMEOUT if a device wait gave up. */
 ising_status ising_hmc_sync(ising_hmc_t *h);
 
-/* Launch shape of the fused FP32 lattice kernel: threads per CTA (32..512, a
- * multiple of 32, at most 4 float4 vectors of a plane per thread) and the
- * prefetch depth in planes (1, 2 or 4; the shared-memory rings must fit).
- * EINVAL for other forms or invalid shapes. */
+/* Launch shape of the fused FP32 lattice kernel: threads per CTA (a multiple
+ * of 32, at most 4 float4 vectors of a plane per thread; 32..256 with one CTA
+ * per chain, up to 512 when chains are split over CTAs, see
+ * ising_hmc_set_chain_split) and the prefetch depth in planes (1, 2 or 4; the
+ * shared-memory rings must fit).  EINVAL for other forms or invalid shapes. */
 ising_status ising_hmc_set_launch(ising_hmc_t *h, int threads, int depth);
 ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth);
 

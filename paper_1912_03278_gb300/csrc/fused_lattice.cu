@@ -67,23 +67,27 @@ cudaError_t fused_lattice_node(const FusedArgs &a, int threads, int depth,
     return fused_node_1d(a, threads, depth, vec, np, args);
 }
 
-int fused_lattice_valid_launch(const Geometry &g, int threads, int depth) {
+static int valid_shape(const Geometry &g, int threads, int depth, int max_threads) {
     const int vec = (g.X % 4 == 0 && g.P % 4 == 0) ? 4 : 1;
     const int nvec = g.P / vec;
-    if (threads < 32 || threads > MAX_THREADS || threads % 32) return 0;
+    if (threads < 32 || threads > max_threads || threads % 32) return 0;
     if ((nvec + threads - 1) / threads > NVMAX) return 0;
     if (depth != 1 && depth != 2 && depth != 4) return 0;
     return fused_lattice_smem_bytes(g, depth, vec) <= 227 * 1024;
 }
 
+int fused_lattice_valid_launch(const Geometry &g, int threads, int depth) {
+    return valid_shape(g, threads, depth, MAX_THREADS_UNSPLIT);
+}
+
 // A chain split over cs CTAs: cs in {1, 2, 4, 8}, a 2D or 3D lattice with at
-// least two planes per slab, and a cluster of cs such CTAs must fit on the
-// device (asked of the occupancy calculator).
+// least two planes per slab, up to 512 threads per CTA, and a cluster of cs
+// such CTAs must fit on the device (asked of the occupancy calculator).
 int fused_lattice_valid_split(const Geometry &g, int threads, int depth, int cs) {
     if (cs == 1) return fused_lattice_valid_launch(g, threads, depth);
     if (cs != 2 && cs != 4 && cs != MAX_CS) return 0;
     if (g.dim < 2 || g.nplanes < 2 * cs) return 0;
-    if (!fused_lattice_valid_launch(g, threads, depth)) return 0;
+    if (!valid_shape(g, threads, depth, MAX_THREADS)) return 0;
     FusedArgs a{};
     a.g = g;
     a.n_chains = 1;

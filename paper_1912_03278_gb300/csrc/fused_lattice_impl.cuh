@@ -38,10 +38,11 @@ namespace ihmc {
 namespace {
 
 constexpr int NVMAX = 4;
-// Threads per CTA: up to 512 (16 warps for the large 3D planes, which hold one
-// CTA per SM); the register cap this gives (65536 / 512 = 128) also lets two
-// CTAs of 256 threads share an SM.
+// Threads per CTA: up to 256 (two CTAs per SM) for a chain on one CTA, up to
+// 512 (16 warps for the large planes, which hold one CTA per SM) for a chain
+// split over a cluster; both give a cap of 128 registers per thread.
 constexpr int MAX_THREADS = 512;
+constexpr int MAX_THREADS_UNSPLIT = 256;
 constexpr int MAX_CS = 8;                    // CTAs per chain (portable cluster size)
 constexpr int XCH_WORDS = 8;                 // per-CTA sums exchanged in a cluster
 // block reduction (32 warps x 8 doubles), broadcast words, two exchange buffers
@@ -437,13 +438,15 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     const int nvec = P / VEC;
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    // copy group s: psi plane z0 + s - 2 (periodic) and p plane z0 + s - 4
-    auto issue = [&](int s) {
+    // copy group s: psi plane z0 + s - 2 (periodic) into psi slot s % R and
+    // p plane z0 + s - 4 into p slot s % RP (slots passed in: the loop below
+    // advances them without a division)
+    auto issue = [&](int s, int slot_psi, int slot_p) {
         const int zpsi = s - 2;
         if (zpsi <= nzs + 1) {
             const int zw = wrap_plane(z0 + zpsi, nz);
             const float *src = gsrc + (int64_t)zw * P;
-            float *dst = psi_ring + (unsigned)s % R * P;
+            float *dst = psi_ring + slot_psi * P;
             if constexpr (VEC == 4) {
                 for (int v = tid; v < nvec; v += nt) cp_async16(dst + 4 * v, src + 4 * v);
             } else {
@@ -453,7 +456,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         const int zp = s - 4;
         if (zp >= 0 && zp < nzs && !FIRST) {   // the first pass draws p itself
             const float *src = gp + (int64_t)zp * P;
-            float *dst = p_ring + (unsigned)s % RP * P;
+            float *dst = p_ring + slot_p * P;
             if constexpr (VEC == 4) {
                 for (int v = tid; v < nvec; v += nt) cp_async16(dst + 4 * v, src + 4 * v);
             } else {
@@ -462,12 +465,17 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         }
         cp_commit();
     };
-    // ring slot of psi plane z (z >= -2) and u plane z (z >= -1), slab-local
-    auto psi_slot = [&](int z) -> const float * { return psi_ring + (unsigned)(z + 2) % R * P; };
+    // ring slots: psi plane z (slab-local, z >= -2) lives in slot (z + 2) % R,
+    // u plane z (z >= -1) in (z + 4) % RU, the p plane of copy group s in s % RP
     auto u_slot = [&](int z) -> float * { return u_ring + (unsigned)(z + 4) % RU * P; };
+    auto wrapR = [](int x) { return x >= R ? x - R : (x < 0 ? x + R : x); };
+    auto wrapRP = [](int x) { return x >= RP ? x - RP : x; };
 
-    for (int s = 0; s <= D + 2; ++s) issue(s);
+    for (int s = 0; s <= D + 2; ++s) issue(s, s % R, s % RP);
     int s_next = D + 3;
+    // at iteration it: sq = slot of psi plane it + 1, sp = p slot of copy group
+    // it + D + 4 (the group issued in that iteration)
+    int sq = 2 % R, sp = (D + 3) % RP;
 
     const float Cf = prm.Cf, bJf = prm.bJf;
     ActConst kc;
@@ -476,12 +484,16 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     for (int it = -1; it <= nzs + LAG; ++it) {
         cp_wait<D>();
         __syncthreads();
-        issue(s_next++);
+        // group it + D + 4 takes the psi slot of plane it - 3 (used last by the
+        // previous iteration's drift) and the p slot it + 1
+        issue(s_next++, wrapR(sq - 4), sp);
         // ---- u(it) = tanh(A psi + h') - psi on plane it ----
         if (it <= nzs) {
-            const float *pm = psi_slot(it - 1), *pcen = psi_slot(it), *pq = psi_slot(it + 1);
+            const float *pm = psi_ring + wrapR(sq - 2) * P;
+            const float *pcen = psi_ring + wrapR(sq - 1) * P;
+            const float *pq = psi_ring + sq * P;
             float *uo = u_slot(it);
-            const int zw = wrap_plane(z0 + it, nz);
+            const int zw = A.hdf ? wrap_plane(z0 + it, nz) : 0;
 #pragma unroll
             for (int k = 0; k < NVMAX; ++k) {
                 if (k >= sl.nwarp) break;
@@ -518,8 +530,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         const int z = it - 1 - LAG;
         if (z >= 0 && z < nzs) {
             const float *um = u_slot(z - 1), *uc = u_slot(z), *uq = u_slot(z + 1);
-            const float *psz = psi_slot(z);
-            const float *ppz = p_ring + (unsigned)(z + 4) % RP * P;
+            const float *psz = psi_ring + wrapR(sq - 1 - LAG - 1) * P;   // psi plane z
+            const float *ppz = p_ring + wrapRP(sp + 1) * P;   // p plane z: group z + 4
             float *gpz = gp + (int64_t)z * P;
             float *gdz = gdst + (int64_t)z * P;
 #pragma unroll
@@ -559,6 +571,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 }
             }
         }
+        sq = wrapR(sq + 1);
+        sp = wrapRP(sp + 1);
     }
     cp_wait<0>();
     __syncthreads();
@@ -646,7 +660,8 @@ __device__ __forceinline__ void set_obs(ChainState *st, const ChainParams &prm, 
 // CL: compiled for chains split over a cluster (launched with a cluster
 // size); the unsplit instance carries no cluster instructions at all.
 template <int DIM, int VEC, int D, bool CL>
-__global__ void __launch_bounds__(MAX_THREADS, 1) fused_lattice_kernel(FusedArgs A, Schedule S) {
+__global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1 : 2)
+    fused_lattice_kernel(FusedArgs A, Schedule S) {
     extern __shared__ float4 smem_f4[];
     float *smem = reinterpret_cast<float *>(smem_f4);
     const Geometry &g = A.g;

@@ -1215,10 +1215,8 @@ ising_status ising_hmc_selftest(int which, const void *in, void *out, int64_t n)
 ising_status ising_hmc_set_launch(ising_hmc_t *h, int threads, int depth) {
     if (!h) return ISING_EINVAL;
     if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "launch shape applies to the FP32 lattice form");
-    if (!fused_lattice_valid_launch(h->g, threads, depth))
-        return fail(h, ISING_EINVAL, "invalid launch shape threads=%d depth=%d", threads, depth);
-    if (h->cs > 1 && !fused_lattice_valid_split(h->g, threads, depth, h->cs))
-        return fail(h, ISING_EINVAL, "launch shape threads=%d depth=%d does not fit a split of %d",
+    if (!fused_lattice_valid_split(h->g, threads, depth, h->cs))
+        return fail(h, ISING_EINVAL, "invalid launch shape threads=%d depth=%d (%d CTAs per chain)",
                     threads, depth, h->cs);
     h->threads = threads;
     h->depth = depth;
@@ -1312,7 +1310,8 @@ static double time_trajectories(ising_hmc *t, int reps, cudaEvent_t e0, cudaEven
 // Autotuner: time one trajectory of every valid (threads, depth) on a
 // temporary copy of the handle's geometry and parameters (so the handle's own
 // chains do not move) and keep the fastest; then try splitting every chain
-// over 2, 4 and 8 CTAs at the best thread count and every depth.
+// over 2, 4 and 8 CTAs at the best thread count and at 256..512 threads, every
+// depth.
 ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     if (!h) return ISING_EINVAL;
     if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "autotune applies to the FP32 lattice form");
@@ -1332,7 +1331,7 @@ ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     cudaEventCreate(&e1);
     double best = 1e300;
     int bt = h->threads, bd = h->depth, bc = 1;
-    const int cand_t[] = {32, 64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512};
+    const int cand_t[] = {32, 64, 96, 128, 160, 192, 224, 256};
     const int cand_d[] = {1, 2, 4};
     const int cand_c[] = {2, 4, 8};
     t->cs = 1;
@@ -1349,18 +1348,24 @@ ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
             }
         }
     }
-    const int th = bt;
+    const int th1 = bt;
+    const int cand_ts[] = {th1, 256, 320, 384, 448, 512};
     for (int c : cand_c) {
-        for (int dp : cand_d) {
-            if (!fused_lattice_valid_split(h->g, th, dp, c)) continue;
-            t->threads = th;
-            t->depth = dp;
-            t->cs = c;
-            const double ms = time_trajectories(t, reps, e0, e1);
-            if (ms > 0 && ms < best) {
-                best = ms;
-                bd = dp;
-                bc = c;
+        for (int i = 0; i < 6; ++i) {
+            const int th = cand_ts[i];
+            if (i > 0 && th == th1) continue;
+            for (int dp : cand_d) {
+                if (!fused_lattice_valid_split(h->g, th, dp, c)) continue;
+                t->threads = th;
+                t->depth = dp;
+                t->cs = c;
+                const double ms = time_trajectories(t, reps, e0, e1);
+                if (ms > 0 && ms < best) {
+                    best = ms;
+                    bt = th;
+                    bd = dp;
+                    bc = c;
+                }
             }
         }
     }
