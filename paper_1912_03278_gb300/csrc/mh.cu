@@ -2,7 +2,8 @@
 // checkerboard sweeps of single-spin-flip proposals over many chains, to set
 // the cost of a sweep against the cost of an HMC trajectory.
 //
-// Spins are int8 (+-1), chain-major.  A sweep is three launches: colour 0,
+// Spins are int8 (+-1), chain-major, or, when rows are a multiple of 32 long,
+// packed 32 per word (multi-spin coding, mh_packed_kernel).  A sweep is three launches: colour 0,
 // colour 1 (c = (x + y + z) mod 2; with every extent even each bond joins the
 // two colours, so the sites of one colour see only the other colour and are
 // updated in parallel with the result of any sequential order), then a
@@ -44,6 +45,8 @@ struct MHChain {
 
 struct MHArgs {
     int8_t *s;
+    uint32_t *sw;                   // packed form: 32 spins per word, bit = (s == +1)
+    const uint32_t *ttab;           // packed form, per chain: [2][8] thresholds, index (s > 0, count)
     const float *ptab;              // per chain: [2][MH_TAB], index (s > 0, nb + 6)
     unsigned long long *acc;        // per chain: M, B, flips (two's complement)
     MHChain *chains;
@@ -192,6 +195,110 @@ __global__ void __launch_bounds__(MH_THREADS) mh_colour_row8_kernel(MHArgs a, in
     }
 }
 
+// Multi-spin-coded form, rows a multiple of 32 long: 32 spins of a row per
+// 32-bit word (bit j = site x0 + j, set for spin +1).  A thread owns one word:
+// the neighbour words give the left/right neighbour bit-vectors by shifts
+// (the row's end bits from the adjacent words, periodic), the other
+// directions whole words; a bit-sliced adder counts each lane's +1
+// neighbours (cnt = (nb + 2 dim) / 2).  The 16 lanes of the launch's colour
+// take their decisions with the same Philox words as the byte kernels (site i
+// uses word (i/2) mod 4 of block i/8, so lane k0 + 2m uses word m & 3 of block
+// 4w + m/4) against an integer threshold: (x >> 9) < T with T the number of
+// 23-bit values k with (k + 1/2) 2^-23 < p, i.e. exactly the FP32 test
+// u23(x) < p.  Spins, flips and sums equal the byte kernels' bit for bit.
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) {
+    return (a & b) | (c & (a ^ b));
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(MH_THREADS) mh_packed_kernel(MHArgs a, int colour) {
+    __shared__ uint32_t tt[16];
+    const int chain = blockIdx.y;
+    if (threadIdx.x < 16) tt[threadIdx.x] = a.ttab[chain * 16 + threadIdx.x];
+    __syncthreads();
+    const uint32_t X = (uint32_t)a.X, Y = (uint32_t)a.Y, Z = (uint32_t)a.Z;
+    const uint32_t XW = X >> 5;                        // words per row
+    const uint32_t nw = (uint32_t)(a.N >> 5);          // words per chain
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    int dM = 0, dB = 0, dF = 0;
+    if (w < nw) {
+        uint32_t *sw = a.sw + (int64_t)chain * nw;
+        const uint32_t row = w / XW;                   // 32-bit index arithmetic: N <= 2^31
+        const uint32_t xw = w - row * XW;
+        const uint32_t y = row % Y, z = row / Y;
+        const uint32_t c = sw[w];
+        const uint32_t wl = xw > 0 ? w - 1 : w + XW - 1;
+        const uint32_t wr = xw + 1 < XW ? w + 1 : w + 1 - XW;
+        const uint32_t Lv = (c << 1) | (sw[wl] >> 31);      // lane j: site x - 1
+        const uint32_t Rv = (c >> 1) | (sw[wr] << 31);      // lane j: site x + 1
+        uint32_t b0, b1, b2 = 0u;
+        if constexpr (DIM == 1) {
+            b0 = Lv ^ Rv;
+            b1 = Lv & Rv;
+        } else {
+            const uint32_t RW = XW * Y;                // words per plane
+            const uint32_t Uv = sw[y > 0 ? w - XW : w + (Y - 1) * XW];
+            const uint32_t Dv = sw[y + 1 < Y ? w + XW : w - (Y - 1) * XW];
+            if constexpr (DIM == 2) {
+                const uint32_t s1 = Lv ^ Rv, c1 = Lv & Rv, s2 = Uv ^ Dv, c2 = Uv & Dv;
+                b0 = s1 ^ s2;
+                const uint32_t k = s1 & s2;
+                b1 = c1 ^ c2 ^ k;
+                b2 = maj3(c1, c2, k);
+            } else {
+                const uint32_t Fv = sw[z > 0 ? w - RW : w + (Z - 1) * RW];
+                const uint32_t Bv = sw[z + 1 < Z ? w + RW : w - (Z - 1) * RW];
+                const uint32_t s1 = Lv ^ Rv ^ Uv, c1 = maj3(Lv, Rv, Uv);
+                const uint32_t s2 = Dv ^ Fv ^ Bv, c2 = maj3(Dv, Fv, Bv);
+                b0 = s1 ^ s2;
+                const uint32_t k = s1 & s2;
+                b1 = c1 ^ c2 ^ k;
+                b2 = maj3(c1, c2, k);
+            }
+        }
+        // lanes of this colour: j = k0 + 2m (x0 is a multiple of 32, so even)
+        const uint32_t k0 = (uint32_t)(colour + y + z) & 1u;
+        const uint32_t e0 = b0 >> k0, e1 = b1 >> k0, e2 = b2 >> k0, es = c >> k0;
+        uint32_t fl = 0u;   // flips, lane m at bit 2m
+#pragma unroll
+        for (int blk = 0; blk < 4; ++blk) {
+            const u32x4 r = philox(4 * w + (uint32_t)blk, a.half, (uint32_t)chain, PURPOSE_MH,
+                                   a.seed);
+            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = 4 * blk + q, sh = 2 * m;
+                const uint32_t idx = ((es >> sh) & 1u) << 3 | ((e2 >> sh) & 1u) << 2 |
+                                     ((e1 >> sh) & 1u) << 1 | ((e0 >> sh) & 1u);
+                fl |= (uint32_t)((rw[q] >> 9) < tt[idx]) << sh;
+            }
+        }
+        const uint32_t lanes = 0x55555555u << k0;
+        const uint32_t flips = fl << k0;
+        const uint32_t nc = c ^ flips;
+        sw[w] = nc;
+        const int up = __popc(nc & lanes);
+        dM = 2 * up - 16;
+        dF = __popc(flips);
+        if (colour == 1) {
+            // sum over the lanes of s * nb, nb = 2 cnt - 2 DIM
+            const uint32_t pl = nc & lanes, mi = ~nc & lanes;
+            const int cp = __popc(b0 & pl) + 2 * __popc(b1 & pl) + 4 * __popc(b2 & pl);
+            const int cm = __popc(b0 & mi) + 2 * __popc(b1 & mi) + 4 * __popc(b2 & mi);
+            dB = (2 * cp - 2 * DIM * up) - (2 * cm - 2 * DIM * (16 - up));
+        }
+    }
+    dM = __reduce_add_sync(0xffffffffu, dM);
+    dB = __reduce_add_sync(0xffffffffu, dB);
+    dF = __reduce_add_sync(0xffffffffu, dF);
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long *acc = a.acc + 3 * chain;
+        if (dM) atomicAdd(acc + 0, (unsigned long long)(long long)dM);
+        if (dB) atomicAdd(acc + 1, (unsigned long long)(long long)dB);
+        if (dF) atomicAdd(acc + 2, (unsigned long long)(long long)dF);
+    }
+}
+
 // Observables of the sweep just finished (if measured), then clear the sums.
 __global__ void mh_measure_kernel(MHArgs a, int n_chains) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,7 +336,10 @@ struct ising_mh {
     int n_chains = 0, n_therm = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int8_t *s = nullptr;
+    bool packed = false;            // rows a multiple of 32: 32 spins per word
+    int8_t *s = nullptr;            // byte form: one int8 per spin
+    uint32_t *sw = nullptr;         // packed form
+    uint32_t *ttab = nullptr;       // packed form: per chain [2][8] thresholds
     float *ptab = nullptr;
     unsigned long long *acc = nullptr;
     MHChain *chains = nullptr;
@@ -248,6 +358,10 @@ static ising_status mh_fail(ising_mh *h, ising_status st, const char *fmt, ...) 
 
 static void mh_free(ising_mh *h) {
     if (h->s) cudaFree(h->s);
+    if (h->sw) cudaFree(h->sw);
+    if (h->ttab) cudaFree(h->ttab);
+    h->sw = nullptr;
+    h->ttab = nullptr;
     if (h->ptab) cudaFree(h->ptab);
     if (h->acc) cudaFree(h->acc);
     if (h->chains) cudaFree(h->chains);
@@ -269,9 +383,19 @@ static float accept_prob(double beta, double J, double h, int s, int nb) {
     return (float)p;
 }
 
+// Number of 23-bit values k with (k + 1/2) 2^-23 < p: the packed kernel's
+// integer test (x >> 9) < T equals the FP32 test u23(x) < p exactly (p and
+// p 2^23 are exact in FP64).
+static uint32_t accept_threshold(float p) {
+    const double t = std::ceil((double)p * 8388608.0 - 0.5);
+    return t <= 0.0 ? 0u : t >= 8388608.0 ? 8388608u : (uint32_t)t;
+}
+
 static MHArgs mh_args(ising_mh *h) {
     MHArgs a{};
     a.s = h->s;
+    a.sw = h->sw;
+    a.ttab = h->ttab;
     a.ptab = h->ptab;
     a.acc = h->acc;
     a.chains = h->chains;
@@ -316,8 +440,10 @@ ising_status ising_mh_create(const ising_hmc_config *cfg, ising_mh_t **out) {
     h->n_chains = cfg->n_chains;
     h->n_therm = cfg->n_therm;
     const int C = h->n_chains;
+    h->packed = h->L[0] % 32 == 0;
     std::vector<MHChain> ch(C);
     std::vector<float> tab((size_t)C * 2 * MH_TAB, 0.0f);
+    std::vector<uint32_t> ttab((size_t)C * 16, 0u);
     for (int c = 0; c < C; ++c) {
         const double beta = cfg->beta_chain ? cfg->beta_chain[c] : cfg->beta;
         const double h0 = cfg->h0_chain ? cfg->h0_chain[c] : cfg->h0;
@@ -328,9 +454,12 @@ ising_status ising_mh_create(const ising_hmc_config *cfg, ising_mh_t **out) {
         ch[c].J = cfg->Jnn;
         ch[c].h = h0;
         for (int sp = 0; sp < 2; ++sp)
-            for (int nb = -2 * h->dim; nb <= 2 * h->dim; ++nb)
-                tab[(size_t)c * 2 * MH_TAB + sp * MH_TAB + nb + 6] =
-                    accept_prob(beta, cfg->Jnn, h0, sp ? 1 : -1, nb);
+            for (int nb = -2 * h->dim; nb <= 2 * h->dim; ++nb) {
+                const float pr = accept_prob(beta, cfg->Jnn, h0, sp ? 1 : -1, nb);
+                tab[(size_t)c * 2 * MH_TAB + sp * MH_TAB + nb + 6] = pr;
+                if ((nb + 2 * h->dim) % 2 == 0)   // cnt = number of +1 neighbours
+                    ttab[(size_t)c * 16 + sp * 8 + (nb + 2 * h->dim) / 2] = accept_threshold(pr);
+            }
     }
     if (cfg->stream) {
         h->stream = (cudaStream_t)cfg->stream;
@@ -339,15 +468,20 @@ ising_status ising_mh_create(const ising_hmc_config *cfg, ising_mh_t **out) {
             return bail(mh_fail(h, ISING_ECUDA, "stream creation failed"));
         h->own_stream = true;
     }
-    const size_t sb = (size_t)C * N;
-    if (cudaMalloc((void **)&h->s, sb) != cudaSuccess ||
+    const size_t sb = h->packed ? (size_t)C * (N / 32) * 4 : (size_t)C * N;
+    if ((h->packed ? cudaMalloc((void **)&h->sw, sb) : cudaMalloc((void **)&h->s, sb)) != cudaSuccess ||
+        cudaMalloc((void **)&h->ttab, ttab.size() * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc((void **)&h->ptab, tab.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void **)&h->acc, (size_t)C * 3 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc((void **)&h->chains, (size_t)C * sizeof(MHChain)) != cudaSuccess) {
         cudaGetLastError();
         return bail(mh_fail(h, ISING_ENOMEM, "device allocation failed (%zu bytes of spins)", sb));
     }
-    if (cudaMemsetAsync(h->s, 1, sb, h->stream) != cudaSuccess ||
+    // every spin +1: bytes of 1, or all bits set
+    if (cudaMemsetAsync(h->packed ? (void *)h->sw : (void *)h->s, h->packed ? 0xff : 1, sb,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->ttab, ttab.data(), ttab.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->acc, 0, (size_t)C * 3 * sizeof(unsigned long long), h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->ptab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess ||
@@ -369,7 +503,10 @@ ising_status ising_mh_sweeps(ising_mh_t *h, int64_t n, uint64_t seed) {
     const int64_t groups = (h->N + 7) / 8;
     dim3 grid((unsigned)((groups + MH_THREADS - 1) / MH_THREADS), (unsigned)h->n_chains, 1);
     auto kern = h->dim == 3 ? mh_colour_kernel<3> : h->dim == 2 ? mh_colour_kernel<2> : mh_colour_kernel<1>;
-    if (h->L[0] % 8 == 0) {
+    if (h->packed) {
+        kern = h->dim == 3 ? mh_packed_kernel<3> : h->dim == 2 ? mh_packed_kernel<2> : mh_packed_kernel<1>;
+        grid.x = (unsigned)((h->N / 32 + MH_THREADS - 1) / MH_THREADS);   // one word per thread
+    } else if (h->L[0] % 8 == 0) {
         kern = h->dim == 3   ? mh_colour_row8_kernel<3>
                : h->dim == 2 ? mh_colour_row8_kernel<2>
                              : mh_colour_row8_kernel<1>;
@@ -424,6 +561,15 @@ ising_status ising_mh_get_spins(ising_mh_t *h, int8_t *out) {
     if (!h || !out) return ISING_EINVAL;
     ising_status st = ising_mh_sync(h);
     if (st != ISING_OK) return st;
+    if (h->packed) {
+        const size_t nw = (size_t)h->n_chains * (h->N / 32);
+        std::vector<uint32_t> w(nw);
+        if (cudaMemcpy(w.data(), h->sw, nw * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return mh_fail(h, ISING_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+        for (size_t k = 0; k < nw; ++k)
+            for (int j = 0; j < 32; ++j) out[32 * k + j] = ((w[k] >> j) & 1u) ? 1 : -1;
+        return ISING_OK;
+    }
     if (cudaMemcpy(out, h->s, (size_t)h->n_chains * h->N, cudaMemcpyDeviceToHost) != cudaSuccess)
         return mh_fail(h, ISING_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
     return ISING_OK;
@@ -438,8 +584,15 @@ ising_status ising_mh_set_spins(ising_mh_t *h, const int8_t *in, int64_t next_sw
         if (in[i] != 1 && in[i] != -1) return mh_fail(h, ISING_EINVAL, "spin %zu is not +-1", i);
     ising_status st = ising_mh_sync(h);
     if (st != ISING_OK) return st;
-    if (cudaMemcpy(h->s, in, n, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (h->packed) {
+        std::vector<uint32_t> w(n / 32, 0u);
+        for (size_t i = 0; i < n; ++i)
+            if (in[i] > 0) w[i / 32] |= 1u << (i % 32);
+        if (cudaMemcpy(h->sw, w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return mh_fail(h, ISING_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+    } else if (cudaMemcpy(h->s, in, n, cudaMemcpyHostToDevice) != cudaSuccess) {
         return mh_fail(h, ISING_ECUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+    }
     h->sweep = next_sweep;
     return ISING_OK;
 }

@@ -36,6 +36,11 @@ def _oracle_chains(dim, L, betas, h, seed, n, n_therm, spins=None, sweep0=0):
 
 
 @pytest.mark.parametrize("dim,L,h", [
+    (2, (32, 6), 0.02),     # rows a multiple of 32: 32 spins per word (multi-spin coding)
+    (2, (64, 10), 0.0),
+    (3, (32, 4, 6), 0.02),
+    (3, (64, 8, 4), 0.03),
+    (1, (64,), 0.1),
     (2, (16, 16), 0.0),     # rows a multiple of 8: one 8-byte word per thread
     (2, (24, 6), 0.03),
     (3, (8, 4, 6), 0.02),
@@ -57,8 +62,9 @@ def test_sweeps_match_oracle_bitwise(dim, L, h):
     assert np.array_equal(sums_gpu, sums_ref)
 
 
-def test_split_and_resume_are_bitwise():
-    kw = dict(dim=2, L=(12, 8), beta=np.array([0.4, 0.5]), h=0.01, n_chains=2, n_therm=1)
+@pytest.mark.parametrize("L", [(12, 8), (32, 8)])   # byte form, packed form
+def test_split_and_resume_are_bitwise(L):
+    kw = dict(dim=2, L=L, beta=np.array([0.4, 0.5]), h=0.01, n_chains=2, n_therm=1)
     a, b = pkg.IsingMH(**kw), pkg.IsingMH(**kw)
     try:
         a.sweeps(7, 3)
