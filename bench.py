@@ -541,6 +541,10 @@ def summary(line):
     out["t_hmc_over_t_mh"] = g("mh", "t_hmc_over_t_mh")
     out["infinite_resident_frac"] = g("infinite", "resident", "roofline", "frac")
     out["serve_p50_p99_s"] = [g("serve", "p50_s"), g("serve", "p99_s")]
+    out["serve_queue_end_by_rho"] = {k: v.get("queued_at_end_of_arrivals")
+                                     for k, v in (g("serve", "by_rho") or {}).items()}
+    out["serve_served_over_rho_cap"] = {k: round(v.get("served_over_rho_capacity", 0), 3)
+                                        for k, v in (g("serve", "by_rho") or {}).items()}
     return out
 
 
@@ -1159,35 +1163,91 @@ def _serve_window(pkg, reqs, arrivals, budget_gb, drain=True):
             "peak_queue": int(st_sub["queued"])}
 
 
-def serve_run(pkg, seconds, rate=200.0, rhos=(0.5, 0.8, 0.95), seed=2, budget_gb=120.0):
-    """Serving: measure the server's capacity on a saturating batch, then
-    Poisson arrivals at `rate` requests/s for `seconds` (half as long for the
-    other loads), with trajectory counts scaled so the offered load is rho of
-    that capacity, for each rho; p50/p99 latency.  Last, the literal workload
-    (unscaled trajectory counts, far beyond any GPU) for a short window:
-    queue growth and admissions."""
-    rng = np.random.default_rng(seed)
+def _scaled(reqs, scale):
+    """The same requests with their trajectory counts times `scale` (at least 1)."""
+    out = []
+    for r in reqs:
+        q = dict(r)
+        q["n_traj"] = max(1, int(round(r["n_traj"] * scale)))
+        out.append(q)
+    return out
+
+
+def _serve_burst(pkg, reqs, budget_gb):
+    """Submit every request at once to a fresh server and drain it: the work
+    served per second with the queue never empty (the server's capacity for
+    requests of this mix and size)."""
     work = lambda r: (request_sites(r) * r["n_chains"] * r["n_traj"] * r["n_md"])
-    # mean work of an unscaled request, from a large sample
-    mean_w = float(np.mean([work(r) for r in serve_requests(np.random.default_rng(7), 4000, 1.0)]))
     srv = pkg.IsingServer(int(budget_gb * 1e9), 4)
     try:
-        cal = serve_requests(rng, 64, 0.02)
         t0 = time.perf_counter()
-        for r in cal:
+        for r in reqs:
             srv.submit(**r)
         srv.drain(600.0)
-        cap = sum(work(r) for r in cal) / (time.perf_counter() - t0)
+        dt = time.perf_counter() - t0
     finally:
         srv.close()
+    return sum(work(r) for r in reqs) / dt
+
+
+def serve_run(pkg, seconds, rate=200.0, rhos=(0.5, 0.8, 0.95), seed=2, budget_gb=120.0):
+    """Serving: Poisson arrivals of the serving mix at `rate` requests/s with
+    trajectory counts scaled so the offered load is rho of the server's
+    capacity (where one trajectory per request already offers more, one
+    trajectory each at a lower arrival rate), for each rho; p50/p99 latency,
+    the queue when arrivals end, and the served rate.  The capacity is measured on the same mix at the same
+    trajectory scale (a burst of one second's requests submitted at once and
+    drained), twice: per-request costs make it depend on the scale.  Last, the
+    literal workload (unscaled trajectory counts, far beyond any GPU) for a
+    short window: queue growth and admissions."""
+    rng = np.random.default_rng(seed)
+    work = lambda r: (request_sites(r) * r["n_chains"] * r["n_traj"] * r["n_md"])
+    sample = serve_requests(np.random.default_rng(7), 4000, 1.0)
+
+    def mean_work(scale):
+        return float(np.mean([work(r) for r in _scaled(sample, scale)]))
+
+    def scale_for(load):
+        """Trajectory scale at which `rate` requests/s offer `load` site-steps/s."""
+        lo, hi = 1e-7, 1.0
+        for _ in range(60):
+            mid = math.sqrt(lo * hi)
+            if rate * mean_work(mid) < load:
+                lo = mid
+            else:
+                hi = mid
+        return math.sqrt(lo * hi)
+
+    floor_w = mean_work(1e-9)   # one trajectory per request
+
+    def plan(load):
+        """(trajectory scale, arrival rate) offering `load` site-steps/s: the
+        workload's rate with scaled trajectory counts, or, where even one
+        trajectory per request offers more, one trajectory each at a lower rate."""
+        if rate * floor_w >= load:
+            return 1e-9, load / floor_w
+        return scale_for(load), rate
+
+    cap = 1.0e11
+    calib = []
+    for _ in range(2):
+        sc, _r = plan(cap)
+        burst = _scaled(serve_requests(rng, int(rate), 1.0), sc)
+        cap = _serve_burst(pkg, burst, budget_gb)
+        calib.append({"trajectory_scale": sc, "capacity_site_steps_per_s": cap})
     by_rho = {}
     main = None
+    # common random numbers: one request list and one unit-rate Poisson
+    # process for every load, so the loads differ only in rate and scale
+    secs = seconds
+    base_reqs = serve_requests(rng, int(rate * secs * 1.5) + 64, 1.0)
+    base_t = np.cumsum(rng.exponential(1.0, len(base_reqs)))
     for rho in rhos:
-        secs = seconds if rho == 0.8 else seconds / 2
-        scale = rho * cap / (rate * mean_w)
-        n = int(rng.poisson(rate * secs))
-        arrivals = np.sort(rng.uniform(0, secs, n))
-        reqs = serve_requests(rng, n, scale)
+        scale, rate_rho = plan(rho * cap)
+        arrivals = base_t / rate_rho
+        n = int(np.searchsorted(arrivals, secs))
+        arrivals = arrivals[:n]
+        reqs = _scaled(base_reqs[:n], scale)
         w = _serve_window(pkg, reqs, arrivals, budget_gb)
         res, st = w["res"], w["st"]
         lat = np.array([r["latency"] for r in res if r["state"] == 2])
@@ -1196,15 +1256,26 @@ def serve_run(pkg, seconds, rate=200.0, rhos=(0.5, 0.8, 0.95), seed=2, budget_gb
                "mean_s": float(lat.mean()), "requests": n, "completed": int(st["completed"]),
                "rejected": int(st["rejected"]), "arrival_seconds": secs,
                "total_seconds": w["t_all"], "site_steps_per_s": done_work / w["t_all"],
-               "trajectory_scale": scale, "queued_at_end_of_arrivals": w["peak_queue"],
+               "offered_site_steps_per_s": sum(work(r) for r in reqs) / secs,
+               "served_over_rho_capacity": done_work / w["t_all"] / (rho * cap),
+               "trajectory_scale": scale, "arrival_rate": rate_rho,
+               "queued_at_end_of_arrivals": w["peak_queue"],
+               "server_seconds": {k: round(st[k], 3) for k in ("create_s", "graph_s", "quanta_s",
+                                                                "retire_s")},
+               "drain_seconds": w["t_all"] - w["t_sub"],
                "dense_requests": int(sum(1 for r in reqs if r.get("kind") == "dense"))}
         by_rho[str(rho)] = row
         if rho == 0.8:
-            main = dict(row, rho=rho, arrival_rate=rate, submit_seconds=w["t_sub"],
+            main = dict(row, rho=rho, submit_seconds=w["t_sub"],
                         capacity_site_steps_per_s=cap,
                         shared_graph_launches=int(st["group_launches"]), quanta=int(st["quanta"]))
     out = main if main is not None else {}
     out["by_rho"] = by_rho
+    out["calibration"] = calib
+    ks = sorted(by_rho, key=float)
+    out["p50_p99_rise_with_rho"] = bool(all(
+        by_rho[a]["p50_s"] <= by_rho[b]["p50_s"] and by_rho[a]["p99_s"] <= by_rho[b]["p99_s"]
+        for a, b in zip(ks, ks[1:])))
     lit_secs = 2.0
     n = int(rng.poisson(rate * lit_secs))
     arrivals = np.sort(rng.uniform(0, lit_secs, n))

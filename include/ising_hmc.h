@@ -310,8 +310,10 @@ ising_status ising_server_wait(ising_server_t *s, int64_t request_id, double tim
 ising_status ising_server_drain(ising_server_t *s, double timeout_s);
 /* out[ISING_SERVER_NSTATS]: admitted, completed, rejected, queued, active,
  * device bytes in use, site-steps done, shared graph launches, quanta,
- * seconds since creation. */
-#define ISING_SERVER_NSTATS 10
+ * seconds since creation, then seconds spent creating handles (admission
+ * thread), building group graphs, running quanta (launch to completion) and
+ * retiring requests (observables, release; worker thread). */
+#define ISING_SERVER_NSTATS 14
 ising_status ising_server_stats(ising_server_t *s, double *out);
 const char *ising_server_last_error(const ising_server_t *s);
 void ising_server_destroy(ising_server_t *s);

@@ -626,9 +626,10 @@ def _scheck(s, st):
         raise IsingError(st, (msg or b"").decode())
 
 
-ISING_SERVER_NSTATS = 10
+ISING_SERVER_NSTATS = 14
 SERVER_STAT_NAMES = ["admitted", "completed", "rejected", "queued", "active", "bytes_in_use",
-                     "site_steps", "group_launches", "quanta", "seconds"]
+                     "site_steps", "group_launches", "quanta", "seconds",
+                     "create_s", "graph_s", "quanta_s", "retire_s"]
 
 
 def ising_server_create(budget_bytes, quantum_traj) -> int:

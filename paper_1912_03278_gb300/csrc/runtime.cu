@@ -124,6 +124,28 @@ static void make_schedule(int integrator, int n_md, Schedule &s) {
     }
 }
 
+// Device memory of a handle comes from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the handle's stream): destroying a
+// handle queues its frees behind its own work instead of synchronising the
+// whole device, so a server retiring requests does not stall the others, and
+// the pool keeps up to POOL_KEEP_BYTES of freed memory for the next handles.
+static constexpr uint64_t POOL_KEEP_BYTES = (uint64_t)16 << 30;
+
+static cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
+    static thread_local int configured_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev != configured_dev) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = POOL_KEEP_BYTES;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+        configured_dev = dev;
+    }
+    return cudaMallocAsync(ptr, bytes, s);
+}
+
 // Smallest eigenvalue of a dense symmetric matrix by Lanczos with full
 // reorthogonalisation (Lanczos 1950), then Sturm-sequence bisection on the
 // tridiagonal matrix.  Used only to validate the shift C (Sec. 2).  The
@@ -133,8 +155,8 @@ static double lanczos_lambda_min(const double *J, const double *dJ, int64_t N, i
     steps = (int)std::min<int64_t>(steps, N);
     std::vector<double> Q((size_t)steps * N), w(N), alpha(steps), beta(steps);
     double *dq = nullptr, *dw = nullptr;
-    if (dJ && (cudaMalloc(&dq, N * sizeof(double)) != cudaSuccess ||
-               cudaMalloc(&dw, N * sizeof(double)) != cudaSuccess)) {
+    if (dJ && (pool_alloc((void **)&dq, N * sizeof(double), nullptr) != cudaSuccess ||
+               pool_alloc((void **)&dw, N * sizeof(double), nullptr) != cudaSuccess)) {
         cudaGetLastError();
         dJ = nullptr;
     }
@@ -212,8 +234,8 @@ static double lanczos_lambda_min(const double *J, const double *dJ, int64_t N, i
         if (count_below(mid) >= 1) hi = mid;
         else lo = mid;
     }
-    if (dq) cudaFree(dq);
-    if (dw) cudaFree(dw);
+    if (dq) cudaFreeAsync(dq, nullptr);
+    if (dw) cudaFreeAsync(dw, nullptr);
     return 0.5 * (lo + hi);
 }
 
@@ -234,7 +256,7 @@ void ihmc::build_log1pexp_table(float *out) {
 
 static void free_all(ising_hmc *h) {
     for (auto &b : h->psi) {
-        if (b) cudaFree(b);
+        if (b) cudaFreeAsync(b, h->stream);
         b = nullptr;
     }
     void *bufs[] = {h->p, h->plain_a, h->plain_u, h->plain_F, h->partials, h->flags, h->d_params,
@@ -243,7 +265,7 @@ static void free_all(ising_hmc *h) {
                     h->dJdig, h->dpsidig, h->drow_exp, h->dchain_exp, h->dGint, h->dsJ8,
                     h->series};
     for (void *b : bufs)
-        if (b) cudaFree(b);
+        if (b) cudaFreeAsync(b, h->stream);
     h->p = nullptr;
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->stream = nullptr;
@@ -280,10 +302,12 @@ static int64_t plan_bytes(int kind, int prec, int64_t N, int n_chains, bool has_
 
 template <typename T>
 static ising_status dalloc(ising_hmc *h, T **ptr, size_t bytes) {
-    cudaError_t e = cudaMalloc((void **)ptr, bytes ? bytes : 16);
+    cudaError_t e = pool_alloc((void **)ptr, bytes ? bytes : 16, h->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(h, ISING_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        *ptr = nullptr;
+        return fail(h, ISING_ENOMEM, "device allocation (%zu bytes) failed: %s", bytes,
+                    cudaGetErrorString(e));
     }
     h->bytes += (int64_t)bytes;
     return ISING_OK;
@@ -553,12 +577,13 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         // form derives its operands from them), also used by the Lanczos check
         const size_t jb = (size_t)N * N * sizeof(double);
         int dev0 = 0;
-        if (cudaGetDevice(&dev0) == cudaSuccess && cudaMalloc((void **)&h->d_J, jb) == cudaSuccess &&
+        if (cudaGetDevice(&dev0) == cudaSuccess &&
+            pool_alloc((void **)&h->d_J, jb, nullptr) == cudaSuccess &&
             cudaMemcpy(h->d_J, cfg->J, jb, cudaMemcpyHostToDevice) == cudaSuccess) {
             h->bytes += (int64_t)jb;
         } else {
             cudaGetLastError();
-            if (h->d_J) cudaFree(h->d_J);
+            if (h->d_J) cudaFreeAsync(h->d_J, nullptr);
             h->d_J = nullptr;
         }
         lam_min = lanczos_lambda_min(cfg->J, h->d_J, N, (int)std::min<int64_t>(N, 96));
@@ -649,8 +674,8 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         std::vector<float> tab(4 * LOG1PEXP_NODES);
         build_log1pexp_table(tab.data());
         if ((st = dalloc(h, &h->d_lpe, tab.size() * sizeof(float))) != ISING_OK) return bail(st);
-        if (cudaMemcpy(h->d_lpe, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+        if (cudaMemcpyAsync(h->d_lpe, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "table upload failed"));
     }
     if (h->has_h) {
@@ -662,8 +687,10 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         }
         if ((st = dalloc(h, &h->d_h32, 2 * N * sizeof(float))) != ISING_OK) return bail(st);
         if ((st = dalloc(h, &h->d_h64, N * sizeof(double))) != ISING_OK) return bail(st);
-        if (cudaMemcpy(h->d_h32, h32.data(), 2 * N * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(h->d_h64, cfg->h, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(h->d_h32, h32.data(), 2 * N * sizeof(float), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess ||
+            cudaMemcpyAsync(h->d_h64, cfg->h, N * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "field upload failed"));
     }
     if (is_dense_tc(h)) {
@@ -677,8 +704,10 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
         if (!h->d_J) return bail(fail(h, ISING_ECUDA, "coupling upload failed"));
         if ((st = dalloc(h, &h->dJ16, (size_t)N * N * lb)) != ISING_OK) return bail(st);
         if (fp8 && (st = dalloc(h, &h->dsJ8, (size_t)N * sizeof(float))) != ISING_OK) return bail(st);
-        if (cudaMemset(h->dpsi16, 0, bn * lb) != cudaSuccess || cudaMemset(h->du32, 0, bn * 4) != cudaSuccess ||
-            cudaMemset(h->du16, 0, bn * lb) != cudaSuccess || cudaMemset(h->psi[1], 0, bn * 4) != cudaSuccess)
+        if (cudaMemsetAsync(h->dpsi16, 0, bn * lb, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->du32, 0, bn * 4, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->du16, 0, bn * lb, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->psi[1], 0, bn * 4, h->stream) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "dense upload failed"));
         if (act_tc) {
             // J in ACT_DIGITS base-2^ACT_BITS digit planes of row-scaled J (exact)
@@ -689,7 +718,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             if ((st = dalloc(h, &h->dchain_exp, (size_t)h->b_pad * sizeof(int))) != ISING_OK)
                 return bail(st);
             if ((st = dalloc(h, &h->dGint, bn * 8)) != ISING_OK) return bail(st);
-            if (cudaMemset(h->dpsidig, 0, (size_t)ACT_DIGITS * bn * 2) != cudaSuccess)
+            if (cudaMemsetAsync(h->dpsidig, 0, (size_t)ACT_DIGITS * bn * 2, h->stream) != cudaSuccess)
                 return bail(fail(h, ISING_ECUDA, "dense upload failed"));
         } else {
             if ((st = dalloc(h, &h->dGhi, bn * 4)) != ISING_OK) return bail(st);
@@ -706,7 +735,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             cudaStreamSynchronize(h->stream) != cudaSuccess)
             return bail(fail(h, ISING_ECUDA, "dense set-up failed: %s",
                              cudaGetErrorString(cudaGetLastError())));
-        cudaFree(h->d_J);
+        cudaFreeAsync(h->d_J, h->stream);
         h->d_J = nullptr;
         h->bytes -= (int64_t)N * N * (int64_t)sizeof(double);
         DenseArgs &d = h->dense;
@@ -749,8 +778,10 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
     std::vector<ChainState> hs(h->n_chains);
     std::memset(hs.data(), 0, sizeof(ChainState) * h->n_chains);
     for (auto &s : hs) { s.start = 0; s.prop = 0; }
-    if (cudaMemcpy(h->d_state, hs.data(), sizeof(ChainState) * h->n_chains, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
+    // every upload of the set-up runs on the handle's stream, which the
+    // stream-ordered allocations above are ordered on
+    if (cudaMemcpyAsync(h->d_state, hs.data(), sizeof(ChainState) * h->n_chains,
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->psi[0], 0, sbytes, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->p, 0, sbytes, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream) != cudaSuccess ||
@@ -828,7 +859,7 @@ ising_status ising_hmc_series_enable(ising_hmc_t *h, int64_t capacity) {
     ising_status st = ising_hmc_sync(h);
     if (st != ISING_OK) return st;
     if (h->series) {
-        cudaFree(h->series);
+        cudaFreeAsync(h->series, h->stream);
         h->bytes -= h->series_cap * h->n_chains * 3 * (int64_t)sizeof(double);
         h->series = nullptr;
     }

@@ -1,10 +1,10 @@
 // serve.cu -- continuous-batching request loop for HMC ensemble jobs.
 //
-// A server owns two threads.  Requests (a model configuration, a number of
-// trajectories, a seed) are queued from any host thread; the admission thread
-// takes them in arrival order while their device memory fits the budget and
-// creates their handles (host set-up and uploads) while the worker keeps the
-// device busy; the worker keeps every admitted request's state resident (one
+// A server owns a worker thread and ADMIT_THREADS admission threads.  Requests
+// (a model configuration, a number of trajectories, a seed) are queued from any
+// host thread; the admission threads take them in arrival order while their
+// device memory fits the budget and create their handles (host set-up and
+// uploads) while the worker keeps the device busy; the worker keeps every admitted request's state resident (one
 // simulation handle per request) and advances all active FP32 lattice
 // requests together by one CUDA-graph launch per quantum (other requests on
 // their own streams, overlapping on the device).  A request
@@ -65,15 +65,24 @@ struct ising_server {
     std::vector<int64_t> active;
     int64_t next_id = 1;
     bool stop = false;
-    std::thread admitter, worker;
+    std::vector<std::thread> admitters;   // handle creation runs on several host threads
+    std::thread worker;
     // statistics
     int64_t admitted = 0, completed = 0, rejected = 0, group_launches = 0, quanta = 0;
     double site_steps = 0.0;
+    // seconds spent: creating handles (admission thread), building group
+    // graphs, queueing and waiting for quanta, retiring requests (worker)
+    double t_create = 0.0, t_graph = 0.0, t_quanta = 0.0, t_retire = 0.0;
     clk::time_point t0;
     char err[512] = {0};
 };
 
 static thread_local char g_server_err[512];
+
+// Admission threads: requests leave the queue in arrival order, but their
+// handles (host set-up, uploads, the dense forms' Lanczos check) are created
+// concurrently.
+constexpr int ADMIT_THREADS = 4;
 
 static ising_status sfail(ising_server *s, ising_status st, const char *fmt, ...) {
     va_list ap;
@@ -130,10 +139,14 @@ static void admit_loop(ising_server *s) {
             s->in_use += q.bytes;
             s->admitting += 1;
             r = &q;
+            if (!s->queue.empty()) s->cv_admit.notify_one();   // another admission thread
         }
         ising_hmc_t *sim = nullptr;
+        const auto tc0 = clk::now();
         const ising_status st = ising_hmc_create(&r->cfg, &sim);
+        const double tc = std::chrono::duration<double>(clk::now() - tc0).count();
         std::lock_guard<std::mutex> lk(s->mu);
+        s->t_create += tc;
         s->admitting -= 1;
         if (st != ISING_OK) {
             r->state = 3;
@@ -171,6 +184,8 @@ static void worker_loop(ising_server *s) {
             for (int64_t id : s->active) act.push_back(&s->req[id]);
         }
         if (act.empty()) continue;
+        const auto tq0 = clk::now();
+        double tg = 0.0;
         // quantum: the same number of trajectories for every active request
         int64_t k = s->quantum;
         for (Request *r : act) k = std::min(k, r->target - ising_hmc_traj_index(r->sim));
@@ -190,10 +205,12 @@ static void worker_loop(ising_server *s) {
         }
         if (!lat.empty()) {
             if (lat_ids != grp_members) {
+                const auto tg0 = clk::now();
                 if (grp) ising_group_destroy(grp);
                 grp = nullptr;
                 if (ising_group_create(lat.data(), (int)lat.size(), &grp) != ISING_OK) grp = nullptr;
                 grp_members = lat_ids;
+                tg = std::chrono::duration<double>(clk::now() - tg0).count();
             }
             if (grp) {
                 const bool ok = ising_group_trajectories_seeds(grp, k, seeds.data()) == ISING_OK;
@@ -209,9 +226,12 @@ static void worker_loop(ising_server *s) {
             }
         }
         for (Request *r : act) ising_hmc_sync(r->sim);
+        const auto tr0 = clk::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->quanta += 1;
+            s->t_graph += tg;
+            s->t_quanta += std::chrono::duration<double>(tr0 - tq0).count() - tg;
         }
         // retire finished requests
         for (Request *r : act) {
@@ -243,8 +263,12 @@ static void worker_loop(ising_server *s) {
                 s->completed += 1;
                 s->active.erase(std::find(s->active.begin(), s->active.end(), r->id));
                 s->cv_done.notify_all();
-                s->cv_admit.notify_one();   // memory freed
+                s->cv_admit.notify_all();   // memory freed
             }
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->t_retire += std::chrono::duration<double>(clk::now() - tr0).count();
         }
     }
     if (grp) ising_group_destroy(grp);
@@ -262,7 +286,7 @@ ising_status ising_server_create(int64_t budget_bytes, int quantum_traj, ising_s
     s->quantum = quantum_traj;
     cudaGetDevice(&s->device);
     s->t0 = clk::now();
-    s->admitter = std::thread(admit_loop, s);
+    for (int i = 0; i < ADMIT_THREADS; ++i) s->admitters.emplace_back(admit_loop, s);
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return ISING_OK;
@@ -341,6 +365,10 @@ ising_status ising_server_stats(ising_server_t *s, double *out /* ISING_SERVER_N
     out[7] = (double)s->group_launches;
     out[8] = (double)s->quanta;
     out[9] = std::chrono::duration<double>(clk::now() - s->t0).count();
+    out[10] = s->t_create;
+    out[11] = s->t_graph;
+    out[12] = s->t_quanta;
+    out[13] = s->t_retire;
     return ISING_OK;
 }
 
@@ -354,7 +382,8 @@ void ising_server_destroy(ising_server_t *s) {
     }
     s->cv_admit.notify_all();
     s->cv_work.notify_all();
-    if (s->admitter.joinable()) s->admitter.join();
+    for (std::thread &t : s->admitters)
+        if (t.joinable()) t.join();
     if (s->worker.joinable()) s->worker.join();
     for (auto &kv : s->req)
         if (kv.second.sim) ising_hmc_destroy(kv.second.sim);
