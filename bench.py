@@ -174,11 +174,13 @@ def traffic_record(kernel, workload):
     current kernel source."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1912_03278_gb300", "csrc", "fused_lattice.cu")
+    csrc = os.path.join(ROOT, "paper_1912_03278_gb300", "csrc")
+    srcs = [os.path.join(csrc, f) for f in ("fused_lattice_impl.cuh", "fused_lattice_2d.cu",
+                                            "df32.cuh", "device_common.cuh")]
     try:
         with open(p) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256(b"".join(open(x, "rb").read() for x in srcs)).hexdigest()[:16]
         rec = d.get(kernel, {}).get(workload)
         if rec and rec.get("source_sha") == h:
             return rec.get("bytes_per_launch")
