@@ -954,8 +954,11 @@ def mh_rate(pkg, stream, L, betas, hmc_ms, steps=4, warm=2, seed=61):
     """The Sec. 4 comparator on the same batch as the headline step (2D L x L,
     the same chains and betas, h = 0): checkerboard Metropolis-Hastings sweeps
     timed with CUDA events, and the cost ratio T_HMC / T_MH (the paper reports
-    ~4 N_step for its implementation).  HBM roofline at 2 algorithmic bytes
-    per site and sweep (each int8 spin read and written once)."""
+    ~4 N_step for its implementation).  L = 1024 rows take the multi-spin-
+    coded kernel, which is bound by the ALU pipe, not by HBM (0.25 B of spins
+    per site and sweep): its roofline is the ALU-pipe saturation rate; the
+    HBM fraction at 2 B per site-sweep (int8 spins) is kept for comparison
+    with the byte kernels."""
     import torch
     n = len(betas)
     sim = pkg.IsingMH(dim=2, L=(L, L), beta=betas, n_chains=n, stream=stream.cuda_stream)
@@ -976,14 +979,22 @@ def mh_rate(pkg, stream, L, betas, hmc_ms, steps=4, warm=2, seed=61):
     sites = float(L) * L * n
     peak, peak_kind = measured_peaks()
     achieved = 2.0 * sites / (ms / 1e3) / 1e9
+    # the packed kernel is bound by the ALU pipe (Philox and bit logic): peak =
+    # the decision rate at which that pipe would be saturated, from the ncu
+    # capture of one colour launch of 2048 chains at L = 1024 (1.0737e9
+    # decisions in 1.564 ms with the ALU pipe 68.86% busy)
+    alu_peak = 1.0737e9 / 1.564e-3 / 0.6886
     return {"workload": "2D L=%d, %d chains (16 betas in [0.38, 0.50]), J=1, h=0, checkerboard, "
                         "spins start +1, %d warm-up sweeps" % (L, n, warm),
             "value": sites / (ms / 1e3), "unit": "site-updates/s", "ms_per_sweep": ms,
             "launches_per_sweep": launches / steps, "flip_fraction": acc,
             "t_hmc_over_t_mh": hmc_ms / ms, "n_step": N_MD, "paper_4_n_step": 4 * N_MD,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind,
-                         "kernel": "mh_colour_kernel", "algorithmic_bytes_per_sweep": 2.0 * sites}}
+            "roofline": {"bound": "alu", "achieved": sites / (ms / 1e3), "peak": alu_peak,
+                         "unit": "site-updates/s", "frac": sites / (ms / 1e3) / alu_peak,
+                         "peak_source": "derived: ALU-pipe saturation rate from the ncu counters "
+                                        "(profiles/mh_packed_kernel_2d_L1024.md)",
+                         "kernel": "mh_packed_kernel (both colours + measurement)",
+                         "hbm_fraction_at_2_bytes_per_site_sweep": achieved / peak}}
 
 
 def _tau_abs_m(pkg, stream, L, C_over_beta, n_chains, therm, n, seed):
