@@ -167,9 +167,13 @@ ising_status ising_hmc_get_state(ising_hmc_t *h, int which, double *out);
 ising_status ising_hmc_get_chains(ising_hmc_t *h, int which, int chain0, int count, double *out);
 
 /* Set every chain's configuration from host psi[n_chains*N] (rounded to the
- * state precision), set the index of the next trajectory, and recompute S and
- * the observables of the new configurations on the device.  Checkpoint /
- * resume: get_state + the trajectory index + the sums restore a run exactly. */
+ * state precision), set the index of the next trajectory, and have S and the
+ * observables of the new configurations computed on the device: by the next
+ * trajectory's first force pass in the FP32 lattice form (which reads every
+ * site and its neighbours anyway: no extra sweep, same values), during the
+ * call in the other forms.  Returns once the copy is complete (the caller may
+ * reuse its buffer).  Checkpoint / resume: get_state + the trajectory index +
+ * the sums restore a run exactly. */
 ising_status ising_hmc_set_state(ising_hmc_t *h, const double *psi, int64_t next_traj);
 
 /* Same from a buffer in the state precision (FP64 for the plain form, FP32
@@ -379,6 +383,21 @@ ising_status ising_hmc_selftest_gemm(int M, int N, int K, const uint16_t *A, con
  * configurations, records and sums are untouched.  Asynchronous.  Errors:
  * EINVAL (not the BF16 dense form, n < 0), ECUDA. */
 ising_status ising_hmc_dense_forces(ising_hmc_t *h, int n);
+
+/* Test hooks for the failure paths (no counterpart in the paper).  They make
+ * a failure on the host side, so no device wait ever has to run out:
+ *  - ising_hmc_inject_alloc_failure(k): the k-th next device allocation made
+ *    by the library fails as if the device were out of memory (k <= 0
+ *    cancels); the call that made it returns ENOMEM and releases what it
+ *    had allocated.
+ *  - ising_hmc_inject_device_error(h, bits): ORs bits (1 = a bounded device
+ *    wait gave up, 2 = a bounds check failed) into the handle's device error
+ *    word, which kernels set when they give up; the next call that
+ *    synchronises reports ETIMEOUT (bit 1) or ECUDA.  The word is not
+ *    cleared: the handle stays in error until destroyed.  EINVAL for other
+ *    bits. */
+void ising_hmc_inject_alloc_failure(int64_t k);
+ising_status ising_hmc_inject_device_error(ising_hmc_t *h, int bits);
 
 void ising_hmc_destroy(ising_hmc_t *h);
 const char *ising_hmc_last_error(const ising_hmc_t *h);

@@ -121,6 +121,8 @@ def load(path: str | None = None):
                                              c_int, P, P, P, P]),
         "ising_hmc_energy_noalloc_error": (c_char_p, []),
         "ising_hmc_destroy": (None, [P]),
+        "ising_hmc_inject_alloc_failure": (None, [c_int64]),
+        "ising_hmc_inject_device_error": (c_int, [P, c_int]),
         "ising_hmc_solve_A": (c_int, [P, c_int, P, P, c_double, c_int, P, P]),
         "ising_hmc_series_enable": (c_int, [P, c_int64]),
         "ising_hmc_series_get": (c_int, [P, P, P]),
@@ -749,6 +751,16 @@ def ising_hmc_selftest_gemm(A_bf16_bits, B_bf16_bits) -> np.ndarray:
     _check(None, load().ising_hmc_selftest_gemm(M, N, K, A.ctypes.data, B.ctypes.data,
                                                 D.ctypes.data))
     return D
+
+
+def ising_hmc_inject_alloc_failure(k):
+    """Test hook: the k-th next device allocation fails (k <= 0 cancels)."""
+    load().ising_hmc_inject_alloc_failure(int(k))
+
+
+def ising_hmc_inject_device_error(h, bits):
+    """Test hook: OR bits into the handle's device error word."""
+    _check(h, load().ising_hmc_inject_device_error(h, int(bits)))
 
 
 def ising_hmc_destroy(h):

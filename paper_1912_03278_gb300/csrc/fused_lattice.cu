@@ -141,6 +141,22 @@ cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int 
     return cudaLaunchKernelExC(&cfg, np.func, np.kernelParams);
 }
 
+namespace {
+__global__ void reset_chain_start_kernel(ChainState *st, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) {
+        st[c].start = 0;
+        st[c].prop = 0;
+    }
+}
+}  // namespace
+
+cudaError_t launch_reset_chain_start(ChainState *st, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    reset_chain_start_kernel<<<(n + 255) / 256, 256, 0, s>>>(st, n);
+    return cudaGetLastError();
+}
+
 cudaError_t fused_lattice_node_cluster(cudaGraphNode_t node, int cs) {
     cudaLaunchAttributeValue v{};
     v.clusterDim.x = (unsigned)cs;

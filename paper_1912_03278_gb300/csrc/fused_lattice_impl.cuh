@@ -418,10 +418,14 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 // The pass covers the slab of planes [z0, z0 + nzs) of the chain; plane
 // indices inside are slab-local, site indices (random-number counters)
 // absolute.
+// eacc (first pass only, may be null): also accumulate the action and
+// estimators of the start configuration (psi read by this pass) with the
+// spin draw of a configuration set from outside -- the same per-site code, in
+// the same per-thread order, as the evaluation sweep.
 template <int DIM, int VEC, int D, bool FIRST, bool LAST>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
                          const Slots &sl, float *smem, const float4 *tab, Acc &acc, int z0,
-                         int nzs) {
+                         int nzs, Acc *eacc = nullptr) {
     constexpr int R = D + 4 + LAG;   // psi ring slots
     constexpr int RP = D + 2 + LAG;  // p ring slots
     constexpr int RU = 3 + LAG;      // u ring slots
@@ -479,7 +483,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
 
     const float Cf = prm.Cf, bJf = prm.bJf;
     ActConst kc;
-    if constexpr (LAST) kc = act_const(prm);
+    if constexpr (LAST || FIRST) kc = act_const(prm);
 
     for (int it = -1; it <= nzs + LAG; ++it) {
         cp_wait<D>();
@@ -521,6 +525,11 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                         if (it >= 0 && it < nzs)
                             vector_action<DIM, VEC>(A, kc, n, (int64_t)(z0 + it) * P + e0, 1.0f,
                                                     pc.traj, A.seed, chain, tab, acc, &t);
+                    }
+                    if constexpr (FIRST) {
+                        if (eacc && it >= 0 && it < nzs)
+                            vector_action<DIM, VEC>(A, kc, n, (int64_t)(z0 + it) * P + e0, 1.0f,
+                                                    TRAJ_INIT, 0, chain, tab, *eacc, &t);
                     }
                 }
             }
@@ -724,6 +733,10 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
     for (int k = 0; k < A.n_traj; ++k) {
         const uint32_t traj = A.traj0 + (uint32_t)k;
         Acc acc = acc_zero();
+        // a configuration set from outside: its action and observables come
+        // from the first force pass of the first trajectory
+        const bool eval_start = k == 0 && A.eval_start;
+        Acc ea = acc_zero();
         // the integrator's force passes; the first draws the momenta (Sec. 3
         // refresh), the last evaluates the proposal's action
         for (int j = 0; j < S.n_pass; ++j) {
@@ -736,9 +749,11 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
             pc.last = (j == S.n_pass - 1);
             pc.traj = traj;
             if (pc.first && pc.last)
-                run_pass<DIM, VEC, D, true, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
+                run_pass<DIM, VEC, D, true, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0,
+                                                  eval_start ? &ea : nullptr);
             else if (pc.first)
-                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
+                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0,
+                                                   eval_start ? &ea : nullptr);
             else if (pc.last)
                 run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
             else
@@ -746,6 +761,19 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
             // the next pass reads (and the one after rewrites) the planes
             // beyond this slab's ends, written by the neighbouring CTAs
             if (CL && cs > 1) cluster_barrier();
+        }
+        if (eval_start) {
+            double ev[5] = {acc_val(ea.S, ea.Slo), kahan_val(ea.sT, ea.cT),
+                            kahan_val(ea.sAT, ea.cAT), kahan_val(ea.sHT, ea.cHT), (double)ea.sS};
+            chain_sum<5, CL>(ev, red, xch + XCH_WORDS, cs);
+            if (threadIdx.x == 0) {
+                S_cur = ev[0];
+                if (lead) {
+                    st->S = ev[0];
+                    set_obs(st, prm, ev[1], ev[2], ev[3], ev[4], invN);
+                    st->prop = start;
+                }
+            }
         }
         const int prop = buf_loc(start, S.n_pass - 1);
         double v[7] = {acc_val(acc.K0, acc.K0lo), acc_val(acc.K1, acc.K1lo),

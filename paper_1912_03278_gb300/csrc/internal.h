@@ -64,6 +64,8 @@ struct FusedArgs {
     int chain0;              // first chain of this launch
     int n_chains;
     int cs;                  // CTAs per chain (the launch's cluster size; lattice kernel)
+    int eval_start;          // lattice kernel: evaluate S and the observables of the start
+                             // configuration in the first trajectory's first pass
     int *err;
 };
 
@@ -78,6 +80,8 @@ enum { KERR_TIMEOUT = 1, KERR_BOUNDS = 2 };
 
 cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
                                  int depth, cudaStream_t s);
+// start = prop = 0 in every chain's state (a configuration was set from outside)
+cudaError_t launch_reset_chain_start(ChainState *st, int n, cudaStream_t s);
 int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec);
 // Kernel-node parameters of the same launch (for CUDA graphs); args[0..1]
 // must point at the FusedArgs and Schedule values to pass.

@@ -26,6 +26,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -496,6 +498,8 @@ ising_status ising_mh_create(const ising_hmc_config *cfg, ising_mh_t **out) {
 
 ising_status ising_mh_sweeps(ising_mh_t *h, int64_t n, uint64_t seed) {
     if (!h) return ISING_EINVAL;
+    nvtxRangePushA("ising_mh_sweeps");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     if (n < 0) return mh_fail(h, ISING_EINVAL, "n must be >= 0");
     if (h->sweep + n > (int64_t)0x7fffffff) return mh_fail(h, ISING_EINVAL, "sweep counter overflow");
     MHArgs a = mh_args(h);

@@ -12,6 +12,9 @@
 #include <new>
 #include <vector>
 
+#include <atomic>
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace ihmc;
@@ -41,6 +44,9 @@ struct ising_hmc {
     int *d_err = nullptr;
     // launch shape of the fused kernel: threads per CTA, prefetch depth, CTAs per chain
     int threads = 0, depth = 0, cs = 1;
+    // FP32 lattice form: the configurations were set from outside and their
+    // action is evaluated by the next trajectory's first force pass
+    bool eval_pending = false;
     // dense couplings on the tensor cores
     bool dense_tc = false;
     int b_pad = 0;
@@ -131,7 +137,22 @@ static void make_schedule(int integrator, int n_md, Schedule &s) {
 // the pool keeps up to POOL_KEEP_BYTES of freed memory for the next handles.
 static constexpr uint64_t POOL_KEEP_BYTES = (uint64_t)16 << 30;
 
+// NVTX range for the duration of a scope (a profiler's timeline shows the
+// library's calls; no cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Test hook (ising_hmc_inject_alloc_failure): the k-th next device
+// allocation fails as if the device were out of memory.
+static std::atomic<int64_t> g_fail_alloc_in{0};
+
 static cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t s) {
+    if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     static thread_local int configured_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && dev != configured_dev) {
@@ -480,6 +501,7 @@ int64_t ising_hmc_estimate_bytes(const ising_hmc_config *cfg) {
 }
 
 ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
+    NvtxRange nvtx_range("ising_hmc_create");
     g_create_err[0] = 0;
     if (!cfg || !out) return fail(nullptr, ISING_EINVAL, "null config or output pointer");
     *out = nullptr;
@@ -650,6 +672,10 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             return bail(fail(h, ISING_ECUDA, "stream creation failed"));
         h->own_stream = true;
     }
+    // every dense form computes from the FP64 couplings on the device
+    if (h->kind == ISING_KIND_DENSE && !h->d_J)
+        return bail(fail(h, ISING_ENOMEM, "device allocation of the %lld x %lld couplings failed",
+                         (long long)N, (long long)N));
     const size_t elem = state_elem(h);
     const size_t sbytes = (size_t)(h->dense_tc ? h->b_pad : h->n_chains) * N * elem;
     ising_status st;
@@ -799,6 +825,7 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
 static ising_status run_trajectories(ising_hmc *h, int64_t n, uint64_t seed);
 
 ising_status ising_hmc_trajectories(ising_hmc_t *h, int64_t n, uint64_t seed) {
+    NvtxRange nvtx_range("ising_hmc_trajectories");
     if (!h) return ISING_EINVAL;
     if (n < 0) return fail(h, ISING_EINVAL, "n must be >= 0");
     if (n == 0) return ISING_OK;
@@ -964,7 +991,9 @@ static ising_status run_trajectories(ising_hmc *h, int64_t n, uint64_t seed) {
             a.seed = seed;
             a.traj0 = (uint32_t)(h->traj + done);
             a.n_traj = (int)k;
+            a.eval_start = done == 0 && h->eval_pending;
             CUDA_OR_FAIL(h, launch_fused(h, a));
+            h->eval_pending = false;
             h->launches += 1;
             done += k;
         }
@@ -1047,6 +1076,7 @@ ising_status ising_hmc_set_sums(ising_hmc_t *h, const double *in) {
 }
 
 ising_status ising_hmc_observables(ising_hmc_t *h, ising_obs *out) {
+    NvtxRange nvtx_range("ising_hmc_observables");
     if (!h || !out) return ISING_EINVAL;
     std::vector<ChainState> hs;
     ising_status st = fetch_states(h, hs);
@@ -1096,6 +1126,14 @@ ising_status ising_hmc_get_state(ising_hmc_t *h, int which, double *out) {
 }
 
 static ising_status after_set_state(ising_hmc_t *h, int64_t next_traj) {
+    if (is_fp32_lattice(h)) {
+        // current configuration in buffer 0; S and the observables come from
+        // the first force pass of the next trajectory (no extra sweep)
+        CUDA_OR_FAIL(h, launch_reset_chain_start(h->d_state, h->n_chains, h->stream));
+        h->eval_pending = true;
+        h->traj = next_traj;
+        return ising_hmc_sync(h);
+    }
     std::vector<ChainState> hs;
     ising_status st = fetch_states(h, hs);
     if (st != ISING_OK) return st;
@@ -1109,6 +1147,7 @@ static ising_status after_set_state(ising_hmc_t *h, int64_t next_traj) {
 }
 
 ising_status ising_hmc_set_state(ising_hmc_t *h, const double *psi, int64_t next_traj) {
+    NvtxRange nvtx_range("ising_hmc_set_state");
     if (!h || !psi) return ISING_EINVAL;
     if (next_traj < 0 || next_traj > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "bad trajectory index");
     ising_status st = ising_hmc_sync(h);
@@ -1125,6 +1164,7 @@ ising_status ising_hmc_set_state(ising_hmc_t *h, const double *psi, int64_t next
 }
 
 ising_status ising_hmc_set_state_native(ising_hmc_t *h, const void *psi_dev, int64_t next_traj) {
+    NvtxRange nvtx_range("ising_hmc_set_state_native");
     if (!h || !psi_dev) return ISING_EINVAL;
     if (next_traj < 0 || next_traj > (int64_t)0xfffffffe) return fail(h, ISING_EINVAL, "bad trajectory index");
     ising_status st = ising_hmc_sync(h);
@@ -1344,6 +1384,7 @@ static double time_trajectories(ising_hmc *t, int reps, cudaEvent_t e0, cudaEven
 // over 2, 4 and 8 CTAs at the best thread count and at 256..512 threads, every
 // depth.
 ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
+    NvtxRange nvtx_range("ising_hmc_autotune");
     if (!h) return ISING_EINVAL;
     if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "autotune applies to the FP32 lattice form");
     if (reps < 1) reps = 1;
@@ -1516,6 +1557,7 @@ ising_status ising_group_trajectories(ising_group_t *g, int64_t n, uint64_t seed
 }
 
 ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const uint64_t *seeds) {
+    NvtxRange nvtx_range("ising_group_trajectories");
     if (!g || !seeds) return ISING_EINVAL;
     if (n < 0) return gfail(g, ISING_EINVAL, "n must be >= 0");
     if (n == 0) return ISING_OK;
@@ -1550,6 +1592,7 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
             g->args[i].seed = seeds[i];
             g->args[i].traj0 = (uint32_t)(h->traj + done);
             g->args[i].n_traj = (int)k;
+            g->args[i].eval_start = done == 0 && h->eval_pending;
             cudaKernelNodeParams np;
             cudaError_t e = fused_lattice_node(g->args[i], h->threads, h->depth, &np, g->argv[i].data());
             if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(g->exec, g->nodes[i], &np);
@@ -1563,6 +1606,7 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
     for (ising_hmc *h : g->m) {
         h->traj += n;
         h->launches += (n + per - 1) / per;
+        h->eval_pending = false;
     }
     // members' later work waits for the group's
     if (cudaEventRecord(g->ev, g->stream) != cudaSuccess) return gfail(g, ISING_ECUDA, "group: event");
@@ -1579,6 +1623,7 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
 // time, largest work first, each split in {1, 2, 4, 8} that fits is timed on
 // the whole group's launch and the fastest kept; two rounds.
 ising_status ising_group_autotune(ising_group_t *g, int reps, double *best_ms) {
+    NvtxRange nvtx_range("ising_group_autotune");
     if (!g) return ISING_EINVAL;
     if (reps < 1) reps = 1;
     ising_status st = ising_group_sync(g);
@@ -1710,6 +1755,23 @@ ising_status ising_hmc_selftest_gemm(int M, int N, int K, const uint16_t *A, con
     cudaFree(dB);
     cudaFree(dD);
     cudaFree(derr);
+    return st;
+}
+
+void ising_hmc_inject_alloc_failure(int64_t k) { g_fail_alloc_in.store(k > 0 ? k : 0); }
+
+ising_status ising_hmc_inject_device_error(ising_hmc_t *h, int bits) {
+    if (!h) return ISING_EINVAL;
+    if (bits & ~(KERR_TIMEOUT | KERR_BOUNDS)) return fail(h, ISING_EINVAL, "unknown error bits %d", bits);
+    // OR into the word on the device, ordered after the handle's queued work
+    int cur = 0;
+    ising_status st = ISING_OK;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess ||
+        cudaMemcpy(&cur, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(h, ISING_ECUDA, "inject: %s", cudaGetErrorString(cudaGetLastError()));
+    cur |= bits;
+    if (cudaMemcpy(h->d_err, &cur, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = fail(h, ISING_ECUDA, "inject: %s", cudaGetErrorString(cudaGetLastError()));
     return st;
 }
 

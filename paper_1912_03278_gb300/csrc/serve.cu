@@ -28,6 +28,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ising_hmc.h"
 
 namespace {
@@ -143,7 +145,9 @@ static void admit_loop(ising_server *s) {
         }
         ising_hmc_t *sim = nullptr;
         const auto tc0 = clk::now();
+        nvtxRangePushA("server admission");
         const ising_status st = ising_hmc_create(&r->cfg, &sim);
+        nvtxRangePop();
         const double tc = std::chrono::duration<double>(clk::now() - tc0).count();
         std::lock_guard<std::mutex> lk(s->mu);
         s->t_create += tc;
@@ -185,6 +189,7 @@ static void worker_loop(ising_server *s) {
         }
         if (act.empty()) continue;
         const auto tq0 = clk::now();
+        nvtxRangePushA("server quantum");
         double tg = 0.0;
         // quantum: the same number of trajectories for every active request
         int64_t k = s->quantum;
@@ -226,6 +231,7 @@ static void worker_loop(ising_server *s) {
             }
         }
         for (Request *r : act) ising_hmc_sync(r->sim);
+        nvtxRangePop();
         const auto tr0 = clk::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
