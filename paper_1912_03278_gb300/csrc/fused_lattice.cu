@@ -142,6 +142,24 @@ cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int 
 }
 
 namespace {
+// Copy by the SMs themselves: every thread moves 16-byte words with a grid
+// stride, so a source in pinned host memory is read over the coherent
+// CPU-GPU link by all SMs at once instead of by one copy engine.
+__global__ void copy16_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst, int64_t n) {
+    // four independent 16-byte loads in flight per thread (the link's latency
+    // is long); the ragged tail one word at a time
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
 __global__ void reset_chain_start_kernel(ChainState *st, int n) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) {
@@ -150,6 +168,16 @@ __global__ void reset_chain_start_kernel(ChainState *st, int n) {
     }
 }
 }  // namespace
+
+cudaError_t launch_copy16(const void *src, void *dst, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    copy16_kernel<<<nsm * 4, 512, 0, s>>>(static_cast<const uint4 *>(src), static_cast<uint4 *>(dst),
+                                          (int64_t)(bytes / 16));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_reset_chain_start(ChainState *st, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

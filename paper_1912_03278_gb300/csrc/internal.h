@@ -80,6 +80,9 @@ enum { KERR_TIMEOUT = 1, KERR_BOUNDS = 2 };
 
 cudaError_t launch_fused_lattice(const FusedArgs &a, const Schedule &sched, int threads,
                                  int depth, cudaStream_t s);
+// dst <- src, bytes a multiple of 16 and both 16-byte aligned, by a grid-stride
+// kernel (src may be pinned host memory the device can address)
+cudaError_t launch_copy16(const void *src, void *dst, size_t bytes, cudaStream_t s);
 // start = prop = 0 in every chain's state (a configuration was set from outside)
 cudaError_t launch_reset_chain_start(ChainState *st, int n, cudaStream_t s);
 int fused_lattice_smem_bytes(const Geometry &g, int depth, int vec);

@@ -1170,7 +1170,19 @@ ising_status ising_hmc_set_state_native(ising_hmc_t *h, const void *psi_dev, int
     ising_status st = ising_hmc_sync(h);
     if (st != ISING_OK) return st;
     const size_t bytes = (size_t)h->n_chains * h->N * state_elem(h);
-    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->psi[0], psi_dev, bytes, cudaMemcpyDefault, h->stream));
+    // pinned (or mapped) host memory the device can read, 16-byte aligned:
+    // the SMs copy it over the CPU-GPU link; anything else by cudaMemcpyAsync
+    cudaPointerAttributes pa{};
+    const bool host_mapped = cudaPointerGetAttributes(&pa, psi_dev) == cudaSuccess &&
+                             pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
+    cudaGetLastError();
+    if (host_mapped && bytes % 16 == 0 && ((uintptr_t)pa.devicePointer % 16) == 0 &&
+        ((uintptr_t)h->psi[0] % 16) == 0) {
+        CUDA_OR_FAIL(h, launch_copy16(pa.devicePointer, h->psi[0], bytes, h->stream));
+        h->launches += 1;
+    } else {
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->psi[0], psi_dev, bytes, cudaMemcpyDefault, h->stream));
+    }
     return after_set_state(h, next_traj);
 }
 

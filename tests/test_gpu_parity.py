@@ -558,3 +558,36 @@ def test_fp32_action_matches_fp64_on_random_states():
         for c, beta in enumerate((0.3, 0.44, 0.6)):
             model = oracle.Model(dim=2, L=(L, L), beta=beta, h=0.07)
             assert abs(rec[c, 4] - oracle.action(model, psi[c])) <= 1e-6, (scale, c)
+
+
+@pytest.mark.parametrize("dim,L,n", [(2, (64, 64), 5), (2, (5, 7), 3)])   # 3*35 floats: not 16-byte
+def test_set_state_native_from_pinned_device_and_pageable_memory(dim, L, n):
+    """set_state_native reads a pinned host buffer with a copy kernel (16-byte
+    words), anything else with cudaMemcpyAsync; every source gives the same
+    chains as set_state from FP64 host memory, bit for bit."""
+    import torch
+    N = int(np.prod(L))
+    psi = workloads.start_psi(n, N, scale=0.7, seed=3).astype(np.float32)
+    kw = dict(dim=dim, L=L, beta=np.linspace(0.3, 0.45, n), h=0.02, eps=0.1, n_md=4, n_chains=n)
+    ref = pkg.IsingHMC(**kw)
+    try:
+        ref.set_state(psi.astype(np.float64), next_traj=7)
+        ref.trajectories(3, 19)
+        want, want_sums = ref.state(), ref.chain_sums()
+    finally:
+        ref.close()
+    pinned = torch.from_numpy(psi.ravel().copy()).pin_memory()
+    dev = torch.from_numpy(psi.ravel().copy()).cuda()
+    page = np.ascontiguousarray(psi.ravel())
+    for src in (pinned.data_ptr(), dev.data_ptr(), page.ctypes.data):
+        sim = pkg.IsingHMC(**kw)
+        try:
+            pkg.ising_hmc_set_state_native(sim.h, src, 7)
+            back = torch.empty(n * N, dtype=torch.float32).pin_memory()
+            pkg.ising_hmc_get_state_native(sim.h, back.data_ptr())
+            assert np.array_equal(back.numpy(), psi.ravel())
+            sim.trajectories(3, 19)
+            assert np.array_equal(sim.state(), want)
+            assert np.array_equal(sim.chain_sums(), want_sums)
+        finally:
+            sim.close()
