@@ -422,7 +422,7 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 // estimators of the start configuration (psi read by this pass) with the
 // spin draw of a configuration set from outside -- the same per-site code, in
 // the same per-thread order, as the evaluation sweep.
-template <int DIM, int VEC, int D, bool FIRST, bool LAST>
+template <int DIM, int VEC, int D, bool FIRST, bool LAST, bool EV = false>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
                          const Slots &sl, float *smem, const float4 *tab, Acc &acc, int z0,
                          int nzs, Acc *eacc = nullptr) {
@@ -483,7 +483,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
 
     const float Cf = prm.Cf, bJf = prm.bJf;
     ActConst kc;
-    if constexpr (LAST || FIRST) kc = act_const(prm);
+    if constexpr (LAST || EV) kc = act_const(prm);
 
     for (int it = -1; it <= nzs + LAG; ++it) {
         cp_wait<D>();
@@ -526,8 +526,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                             vector_action<DIM, VEC>(A, kc, n, (int64_t)(z0 + it) * P + e0, 1.0f,
                                                     pc.traj, A.seed, chain, tab, acc, &t);
                     }
-                    if constexpr (FIRST) {
-                        if (eacc && it >= 0 && it < nzs)
+                    if constexpr (FIRST && EV) {
+                        if (it >= 0 && it < nzs)
                             vector_action<DIM, VEC>(A, kc, n, (int64_t)(z0 + it) * P + e0, 1.0f,
                                                     TRAJ_INIT, 0, chain, tab, *eacc, &t);
                     }
@@ -748,12 +748,12 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
             pc.first = (j == 0);
             pc.last = (j == S.n_pass - 1);
             pc.traj = traj;
-            if (pc.first && pc.last)
-                run_pass<DIM, VEC, D, true, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0,
-                                                  eval_start ? &ea : nullptr);
+            // (n_pass >= 2: the first pass is never the last)
+            if (pc.first && eval_start)
+                run_pass<DIM, VEC, D, true, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0,
+                                                         z1 - z0, &ea);
             else if (pc.first)
-                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0,
-                                                   eval_start ? &ea : nullptr);
+                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
             else if (pc.last)
                 run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
             else
