@@ -1062,7 +1062,7 @@ def mixed_3d_rate(pkg, steps=4, seed=31):
     grp = pkg.IsingGroup(sims)
     try:
         # the members' chain splits (CTAs per chain) for the whole group's launch
-        group_ms = grp.autotune(reps=2)
+        group_ms = grp.autotune(reps=4)
         for s in sims:
             tuned[s.kw["L"][0]]["ctas_per_chain"] = s.chain_split
         grp.trajectories(2, seed)

@@ -275,10 +275,11 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
 
 /* Group autotuner: picks every member's chain split (CTAs per chain, see
  * ising_hmc_set_chain_split) for the fastest launch of the whole group, by
- * timing `reps` group trajectories per candidate on temporary copies of the
- * members (all their chains, their current launch shapes; the members'
- * chains are not advanced).  Greedy: members in order of work, each split in
- * {1, 2, 4, 8} that fits, two rounds.  Sets the members' splits; *best_ms
+ * timing `reps` group trajectories per candidate (twice, the better time
+ * kept) on temporary copies of the members (all their chains, their current
+ * launch shapes; the members' chains are not advanced).  Greedy from the
+ * better of the current splits and none: members in order of work, each
+ * split in {1, 2, 4, 8} that fits, two rounds.  Sets the members' splits; *best_ms
  * (may be NULL) gets the time per group trajectory.  Allocates the copies
  * (ENOMEM if they would take more than 80% of the free device memory);
  * synchronises. */
