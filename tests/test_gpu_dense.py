@@ -49,14 +49,14 @@ BF16 = pkg.ISING_PREC_BF16
 
 
 def _dense_parity(N, n_chains, samples, beta=0.5, n_md=8, eps=0.06, traj=2, seed=5, h=True,
-                  psi_scale=0.4, prec=BF16, tol=2e-2):
+                  psi_scale=0.4, prec=BF16, tol=2e-2, default_shift=False):
     J = workloads.dense_couplings(N, seed=1)
     hv = workloads.dense_fields(N, 0.1) if h else 0.0
-    lam = np.linalg.eigvalsh(J)[0]
-    C = beta * abs(lam) + 0.1
+    C = None if default_shift else beta * abs(np.linalg.eigvalsh(J)[0]) + 0.1
     psi0 = workloads.start_psi(n_chains, N, scale=psi_scale, seed=23).astype(np.float32).astype(np.float64)
     sim = pkg.IsingHMC(kind="dense", J=J, h=hv, beta=beta, C=C, eps=eps, n_md=n_md,
                        n_chains=n_chains, precision=prec)
+    C = float(sim.params[0, 1])   # the library's choice when none was given
     try:
         sim.set_state(psi0, next_traj=traj)
         sim.trajectories(1, seed)
@@ -91,6 +91,15 @@ def test_dense_parity_single_cta_tiles(prec, tol):
     """N = 384 and 100 chains are not multiples of 256: the forces and the
     action run on single-CTA 128 x 128 tiles instead of CTA pairs."""
     _dense_parity(384, 100, samples=(0, 57, 99), prec=prec, tol=tol)
+
+
+@pytest.mark.parametrize("N,n_chains", [(4224, 130), (4352, 256)])
+def test_dense_bf16_parity_beyond_exact_digit_range(N, n_chains):
+    """N > 4096: the digit-plane product is no longer exact in the FP32
+    accumulator, so the action's A psi runs on the double-float CUDA-core
+    product instead; N = 4224 on single-CTA force tiles, N = 4352 on CTA pairs.
+    C is the library's default shift."""
+    _dense_parity(N, n_chains, samples=(0, n_chains - 1), n_md=6, eps=0.05, default_shift=True)
 
 
 def test_dense_bf16_parity_config_size():
