@@ -90,7 +90,9 @@ typedef struct {
     int n_therm;          /* trajectories with index < n_therm are not measured (Sec. 3) */
     int precision;        /* ISING_PREC_*                                               */
     int integrator;       /* ISING_INTEGRATOR_*                                         */
-    int flip_every;       /* >0: global sign-flip proposal after every k-th trajectory  */
+    int flip_every;       /* >0: global sign-flip proposal after every k-th trajectory
+                             (every form; the tensor-core dense forms evaluate the
+                             current configuration's A psi once more for it)       */
     void *stream;         /* cudaStream_t to queue work on, or NULL for an own stream   */
 } ising_hmc_config;
 

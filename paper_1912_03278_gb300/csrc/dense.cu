@@ -390,7 +390,12 @@ __global__ void __launch_bounds__(256) k_df_gemm(const float *__restrict__ Jhi,
 // ----------------------------------------- per-chain action, dH, Metropolis
 // mode 0: end of a trajectory (psi_w = proposal, p = end momenta, K0 from the
 // regenerated momenta, Metropolis test, copy to psi_cur on accept);
-// mode 1: evaluate S and the estimators of psi_cur (G computed from psi_cur).
+// mode 1: evaluate S and the estimators of psi_cur (G computed from psi_cur);
+// mode 2: global sign flip (Sec. 3): S and the estimators of -psi_cur (G
+// computed from psi_cur, so A(-psi) = -A psi), the flip's Metropolis test
+// against S(psi_cur), psi_cur negated on acceptance.
+// Modes 0 and 2 add the measurement of the trajectory when `measure` is set
+// (a flip trajectory measures after the flip, in mode 2).
 __global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode, uint32_t traj,
                                                         uint64_t seed, int measure) {
     __shared__ float4 tab[LOG1PEXP_NODES];
@@ -408,8 +413,9 @@ __global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode
     float Slo = 0.f, K0lo = 0.f, K1lo = 0.f;
     float sT = 0.f, cT = 0.f, sAT = 0.f, cAT = 0.f, sHT = 0.f, cHT = 0.f;
     int sS = 0;
-    const uint32_t spin_traj = mode == 0 ? traj : TRAJ_INIT;
-    const uint64_t spin_seed = mode == 0 ? seed : 0;
+    const uint32_t spin_traj = mode == 1 ? TRAJ_INIT : traj;
+    const uint64_t spin_seed = mode == 1 ? 0 : seed;
+    const float sg = mode == 2 ? -1.0f : 1.0f;   // the configuration is sg * psi
     for (int q = threadIdx.x; q < d.N / 4; q += blockDim.x) {
         const float4 su = spin_u4_f32((uint32_t)q, spin_traj, (uint32_t)n, spin_seed);
         const float suv[4] = {su.x, su.y, su.z, su.w};
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode
         for (int k = 0; k < 4; ++k) {
             const int m = 4 * q + k;
             const int64_t idx = (int64_t)n * d.N + m;
-            const float ps = psi[m];
+            const float ps = sg * psi[m];
             f2 G;
             if (d.action_tc) {   // exact integer digit sum -> double-float (48 bits)
                 const long long gi = d.Gint[idx];
@@ -431,6 +437,7 @@ __global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode
             } else {
                 G = f2{d.Ghi[idx], d.Glo[idx]};
             }
+            if (mode == 2) G = df_neg(G);
             const f2 a = df_add(df_mul(beta2, G), df_mul_f(C2, ps));
             f2 x = a;
             float hq = pr.hpf;
@@ -470,10 +477,34 @@ __global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode
             st->obs[2] = fabs(v[6]) * invN;
             st->obs[3] = fabs(m);
         };
+        auto add_measurement = [&]() {
+            const double dH = st->rec[ISING_REC_DH];
+            double *sm = st->sums;
+            sm[ISING_SUM_NMEAS] += 1.0;
+            sm[ISING_SUM_NACC] += st->rec[ISING_REC_ACCEPTED];
+            sm[ISING_SUM_M] += st->obs[0];
+            sm[ISING_SUM_M2] += st->obs[0] * st->obs[0];
+            sm[ISING_SUM_E] += st->obs[1];
+            sm[ISING_SUM_E2] += st->obs[1] * st->obs[1];
+            sm[ISING_SUM_ABSM] += st->obs[2];
+            sm[ISING_SUM_ABSM2] += st->obs[2] * st->obs[2];
+            sm[ISING_SUM_DH] += dH;
+            sm[ISING_SUM_EXPMDH] += exp(-dH);
+        };
         if (mode == 1) {
             st->S = v[2];
             set_obs();
             bcast = 0;
+        } else if (mode == 2) {
+            const double lu = accept_logu(traj, (uint32_t)n, seed, PURPOSE_FLIP);
+            const bool fl = lu < -(v[2] - st->S);
+            if (fl) {
+                st->S = v[2];
+                set_obs();
+                st->rec[ISING_REC_FLIPPED] = 1.0;
+            }
+            if (measure) add_measurement();
+            bcast = fl ? 1 : 0;
         } else {
             const double S0 = st->S;
             const double dH = (v[1] + v[2]) - (v[0] + S0);
@@ -491,26 +522,15 @@ __global__ void __launch_bounds__(256, 4) k_dense_finalize(DenseArgs d, int mode
                 st->S = v[2];
                 set_obs();
             }
-            if (measure) {
-                double *sm = st->sums;
-                sm[ISING_SUM_NMEAS] += 1.0;
-                sm[ISING_SUM_NACC] += acc ? 1.0 : 0.0;
-                sm[ISING_SUM_M] += st->obs[0];
-                sm[ISING_SUM_M2] += st->obs[0] * st->obs[0];
-                sm[ISING_SUM_E] += st->obs[1];
-                sm[ISING_SUM_E2] += st->obs[1] * st->obs[1];
-                sm[ISING_SUM_ABSM] += st->obs[2];
-                sm[ISING_SUM_ABSM2] += st->obs[2] * st->obs[2];
-                sm[ISING_SUM_DH] += dH;
-                sm[ISING_SUM_EXPMDH] += exp(-dH);
-            }
+            if (measure) add_measurement();
             bcast = acc ? 1 : 0;
         }
     }
     __syncthreads();
     if (bcast) {
+        // mode 0: the proposal becomes current; mode 2: psi_cur = -psi_cur
         float *dst = d.psi_cur + (int64_t)n * d.N;
-        for (int m = threadIdx.x; m < d.N; m += blockDim.x) dst[m] = psi[m];
+        for (int m = threadIdx.x; m < d.N; m += blockDim.x) dst[m] = sg * psi[m];
     }
 }
 
@@ -788,7 +808,7 @@ static int grid_elems(int64_t n) {
 }
 
 cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
-                             int measure, cudaStream_t s, int64_t *launches) {
+                             int measure, int flip, cudaStream_t s, int64_t *launches) {
     const int64_t nel = (int64_t)d.b_pad * d.N;
     int64_t n = 0;
     k_copy_state<<<grid_elems(nel), 256, 0, s>>>(d.psi_cur, d.psi, d.fp8 ? nullptr : d.psi16,
@@ -811,7 +831,17 @@ cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed,
         *launches += n;
         return e;
     }
-    k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 0, traj, seed, measure); ++n;
+    k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 0, traj, seed, flip ? 0 : measure); ++n;
+    if (flip) {
+        // sign-flip proposal of the current configuration: its A psi first
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_action_product(d, d.psi_cur, s, &n);
+        if (e != cudaSuccess) {
+            *launches += n;
+            return e;
+        }
+        k_dense_finalize<<<d.n_chains, 256, 0, s>>>(d, 2, traj, seed, measure); ++n;
+    }
     *launches += n;
     return cudaGetLastError();
 }

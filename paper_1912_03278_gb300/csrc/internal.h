@@ -184,7 +184,7 @@ cudaError_t dense_matvec_f64(const double *J, const double *x, double *y, int64_
 cudaError_t dense_prepare(const double *J, int64_t N, uint16_t *J16, uint16_t *dig, int *row_exp,
                           float *Jhi, float *Jlo, uint8_t *J8, float *sJ8, cudaStream_t s);
 cudaError_t dense_trajectory(DenseArgs &d, const Schedule &sched, uint64_t seed, uint32_t traj,
-                             int measure, cudaStream_t s, int64_t *launches);
+                             int measure, int flip, cudaStream_t s, int64_t *launches);
 cudaError_t dense_eval(DenseArgs &d, cudaStream_t s, int64_t *launches);
 cudaError_t dense_momenta(DenseArgs &d, uint64_t seed, uint32_t traj, cudaStream_t s,
                           int64_t *launches);

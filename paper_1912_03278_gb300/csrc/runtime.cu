@@ -562,9 +562,6 @@ ising_status ising_hmc_create(const ising_hmc_config *cfg, ising_hmc_t **out) {
             if (h->N % 128)
                 return bail(fail(h, ISING_EINVAL,
                                  "tensor-core dense form needs n_sites a multiple of 128"));
-            if (h->flip_every)
-                return bail(fail(h, ISING_EINVAL,
-                                 "sign flip not available in the tensor-core dense form"));
             h->dense_tc = true;
             h->b_pad = (h->n_chains + 127) / 128 * 128;
         } else if (h->prec != ISING_PREC_PLAIN_FP64) {
@@ -971,8 +968,9 @@ static ising_status run_trajectories(ising_hmc *h, int64_t n, uint64_t seed) {
     if (is_dense_tc(h)) {
         for (int64_t t = 0; t < n; ++t) {
             const uint32_t tr = (uint32_t)(h->traj + t);
+            const int flip = h->flip_every > 0 && ((tr + 1) % (uint32_t)h->flip_every) == 0;
             CUDA_OR_FAIL(h, dense_trajectory(h->dense, h->sched, seed, tr,
-                                             (int64_t)tr >= (int64_t)h->n_therm, h->stream,
+                                             (int64_t)tr >= (int64_t)h->n_therm, flip, h->stream,
                                              &h->launches));
         }
         h->traj += n;

@@ -44,6 +44,7 @@ def test_tcgen05_bf16_gemm(M, N, K):
 # ---------------------------------------------------------------- HMC with dense couplings
 import oracle
 import workloads
+from tests.stats_util import within
 
 BF16 = pkg.ISING_PREC_BF16
 
@@ -189,3 +190,49 @@ def test_dense_forces_timing_aid_leaves_chains_untouched():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("prec", [BF16, pkg.ISING_PREC_FP8])
+def test_dense_sign_flip_always_accepted_at_zero_field(prec):
+    """Sec. 3 global flip in the tensor-core form: at h = 0, S(-psi) = S(psi),
+    so every chain flips after its trajectory and the current configuration
+    is exactly minus the one the Metropolis step kept."""
+    N, B, beta, traj = 256, 130, 0.5, 3
+    J = workloads.dense_couplings(N, seed=1)
+    psi0 = workloads.start_psi(B, N, scale=0.4, seed=23).astype(np.float32).astype(np.float64)
+    sim = pkg.IsingHMC(kind="dense", J=J, h=0.0, beta=beta, eps=0.05, n_md=4, n_chains=B,
+                       precision=prec, flip_every=1)
+    try:
+        sim.set_state(psi0, next_traj=traj)
+        sim.trajectories(1, 5)
+        rec = sim.records()
+        prop = sim.state(pkg.ISING_STATE_PSI_PROPOSAL)
+        cur = sim.state(pkg.ISING_STATE_PSI)
+    finally:
+        sim.close()
+    assert np.all(rec[:, 7] == 1.0)
+    for c in range(B):
+        kept = prop[c] if rec[c, 2] else psi0[c]
+        assert np.array_equal(cur[c], -kept), c
+
+
+def test_dense_sign_flip_samples_both_magnetisations():
+    """Infinite-range couplings as a dense BF16 matrix (K_ij = 1/N) in the
+    ordered phase, beta J = 1.5, with a small field h = 0.01: chains started at
+    psi = 0 settle near +m or -m, and only the flip moves them between the two
+    with the right weights; with flips every other trajectory <beta eps>
+    matches the appendix's exact finite-N sum."""
+    N, beta, h = 128, 1.5, 0.01
+    J = workloads.infinite_range_couplings(N, 1.0)
+    exact = oracle.infinite_range_energy(beta, 1.0, h, N)
+    sim = pkg.IsingHMC(kind="dense", J=J, h=h, beta=beta, C=1.0, eps=0.15, n_md=6, n_chains=256,
+                       n_therm=100, precision=BF16, flip_every=2)
+    try:
+        sim.trajectories(600, 3)
+        o = sim.observables()
+        rec = sim.records()
+    finally:
+        sim.close()
+    assert o["acceptance"] > 0.5
+    assert rec[:, 7].sum() > 0          # trajectory 599 was a flip trajectory
+    assert within(o["E"], exact, o["E_err"]), (o["E"], exact, o["E_err"])
