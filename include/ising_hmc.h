@@ -413,8 +413,10 @@ const char *ising_hmc_last_create_error(void);
  * (Kt = K + C_p*1 = A/J').  b, x: host arrays of N doubles.  Stops when the
  * recursive residual satisfies ||r|| <= tol ||b|| or after max_iter
  * iterations; *iters (may be NULL) gets the count, *resid (may be NULL)
- * ||r||/||b||.  Lattice and infinite-range models.  Synchronises.
- * Errors: EINVAL (kind, chain, tol <= 0, max_iter < 1), ENOMEM, ECUDA. */
+ * ||r||/||b||.  Lattice and infinite-range models, and dense couplings in the
+ * plain FP64 form (which keeps J in FP64 on the device; one warp per row of
+ * J).  Synchronises.
+ * Errors: EINVAL (kind or form, chain, tol <= 0, max_iter < 1), ENOMEM, ECUDA. */
 ising_status ising_hmc_solve_A(ising_hmc_t *h, int chain, const double *b, double *x, double tol,
                                int max_iter, int *iters, double *resid);
 

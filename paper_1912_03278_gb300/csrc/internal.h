@@ -105,12 +105,12 @@ cudaError_t launch_infinite(const FusedArgs &a, const Schedule &sched, cudaStrea
 cudaError_t infinite_node(const FusedArgs &a, cudaKernelNodeParams *np, void **args);
 int infinite_threads(int64_t N);
 
-// A x = b by conjugate gradients in FP64, one CTA (lattice or infinite-range
-// A with coupling bJ and shift C); work holds 3N doubles; iters and resid are
-// device scalars.
+// A x = b by conjugate gradients in FP64, one CTA (lattice, infinite-range or
+// dense A with coupling bJ and shift C; J the dense couplings on the device or
+// null); work holds 3N doubles; iters and resid are device scalars.
 cudaError_t solve_A(const double *b_dev, double *x_dev, double *work, int64_t N, int kind, int dim,
                     const int L[3], double bJ, double C, double tol, int max_iter, int *iters_dev,
-                    double *resid_dev, cudaStream_t s);
+                    double *resid_dev, cudaStream_t s, const double *J = nullptr);
 
 // Chain-averaged observables from per-chain sums (ISING_NSUMS per chain).
 void obs_from_sums(const double *sums, int n_chains, int64_t n_traj, ising_obs *out);

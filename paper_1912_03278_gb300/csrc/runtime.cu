@@ -843,8 +843,9 @@ ising_status ising_hmc_solve_A(ising_hmc_t *h, int chain, const double *b, doubl
                                int max_iter, int *iters, double *resid) {
     if (!h || !b || !x) return ISING_EINVAL;
     if (chain < 0 || chain >= h->n_chains) return fail(h, ISING_EINVAL, "chain %d out of range", chain);
-    if (h->kind != ISING_KIND_LATTICE && h->kind != ISING_KIND_INFINITE)
-        return fail(h, ISING_EINVAL, "solve_A applies to lattice and infinite-range models");
+    if (h->kind == ISING_KIND_DENSE && !(h->prec == ISING_PREC_PLAIN_FP64 && h->d_J))
+        return fail(h, ISING_EINVAL,
+                    "solve_A with dense couplings needs the plain FP64 form (it keeps J in FP64)");
     if (!(tol > 0) || max_iter < 1) return fail(h, ISING_EINVAL, "need tol > 0 and max_iter >= 1");
     ising_status st = ising_hmc_sync(h);
     if (st != ISING_OK) return st;
@@ -861,7 +862,7 @@ ising_status ising_hmc_solve_A(ising_hmc_t *h, int chain, const double *b, doubl
     cudaError_t e = cudaMemcpyAsync(buf, b, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = solve_A(buf, buf + N, buf + 2 * N, N, h->kind, h->dim, h->L, p.bJ, p.C, tol, max_iter,
-                    dit, dres, h->stream);
+                    dit, dres, h->stream, h->kind == ISING_KIND_DENSE ? h->d_J : nullptr);
     double res = 0;
     int it = 0;
     if (e == cudaSuccess)

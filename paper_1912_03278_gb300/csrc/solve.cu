@@ -21,11 +21,13 @@ namespace {
 constexpr int SOLVE_THREADS = 1024;
 
 struct SolveArgs {
+    const double *J;   // dense couplings (N x N, row-major) or null
     const double *b;
     double *x, *r, *d, *Ad;
     int64_t N;
     int kind, dim, X, Y, Z;
-    double bJ, C;   // beta*J (lattice) or kappa = beta*J/N (infinite range); the shift
+    double bJ, C;   // beta*J (lattice), kappa = beta*J/N (infinite range) or beta (dense);
+                    // the shift
     double tol;
     int max_iter;
     int *iters;     // out: iterations taken (max_iter if the tolerance was not reached)
@@ -42,9 +44,21 @@ __device__ double dot(const double *u, const double *v, int64_t N, double *red) 
 }
 
 // out = A v.  Lattice: periodic nearest neighbours; infinite range: every
-// other site with weight kappa.
+// other site with weight kappa; dense: beta J v, one warp per row (lanes
+// stride the row, then a fixed-order shuffle sum).
 __device__ void apply_A(const SolveArgs &a, const double *v, double *out, double *red) {
     const int64_t N = a.N;
+    if (a.kind == ISING_KIND_DENSE) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int64_t i = warp; i < N; i += nw) {
+            const double *row = a.J + i * N;
+            double s = 0.0;
+            for (int64_t j = lane; j < N; j += 32) s = fma(row[j], v[j], s);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) out[i] = a.C * v[i] + a.bJ * s;
+        }
+        return;
+    }
     if (a.kind == ISING_KIND_INFINITE) {
         double s = 0.0;
         for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += v[i];
@@ -104,8 +118,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) cg_kernel(SolveArgs a) {
 
 cudaError_t solve_A(const double *b_dev, double *x_dev, double *work /* 3N */, int64_t N, int kind,
                     int dim, const int L[3], double bJ, double C, double tol, int max_iter,
-                    int *iters_dev, double *resid_dev, cudaStream_t s) {
+                    int *iters_dev, double *resid_dev, cudaStream_t s, const double *J) {
     SolveArgs a{};
+    a.J = J;
     a.b = b_dev;
     a.x = x_dev;
     a.r = work;

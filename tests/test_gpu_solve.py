@@ -20,6 +20,8 @@ def _built():
 
 
 @pytest.mark.parametrize("kw", [
+    dict(kind="dense", J=workloads.dense_couplings(200, seed=5),
+         precision=pkg.ISING_PREC_PLAIN_FP64),
     dict(dim=2, L=(8, 6)),
     dict(dim=3, L=(4, 5, 6)),
     dict(dim=1, L=(9,)),
@@ -39,6 +41,8 @@ def test_solution_satisfies_the_oracles_A(kw):
     if kw.get("kind") == "infinite":
         model = oracle.Model(kind="dense", J=workloads.infinite_range_couplings(N, kw["Jnn"]),
                              beta=0.3, C=float(C[1]))
+    elif kw.get("kind") == "dense":
+        model = oracle.Model(kind="dense", J=kw["J"], beta=0.3, C=float(C[1]))
     else:
         model = oracle.Model(dim=kw["dim"], L=kw["L"], beta=0.3, C=float(C[1]))
     assert res <= 1e-13 and 0 < it < 10000
@@ -59,11 +63,13 @@ def test_uniform_right_hand_side_closed_form():
     assert it <= 2
 
 
-def test_dense_kind_rejected():
-    J = workloads.dense_couplings(16, seed=1)
-    sim = pkg.IsingHMC(kind="dense", J=J, beta=0.5, precision=pkg.ISING_PREC_PLAIN_FP64)
+def test_tensor_core_dense_form_rejected():
+    """The BF16 form keeps no FP64 couplings on the device: EINVAL."""
+    J = workloads.dense_couplings(128, seed=1)
+    sim = pkg.IsingHMC(kind="dense", J=J, beta=0.5, precision=pkg.ISING_PREC_BF16)
     try:
-        with pytest.raises(pkg.IsingError):
-            sim.solve_A(np.ones(16))
+        with pytest.raises(pkg.IsingError) as ei:
+            sim.solve_A(np.ones(128))
+        assert ei.value.status == pkg.ISING_EINVAL
     finally:
         sim.close()
