@@ -251,6 +251,18 @@ ising_status ising_hmc_get_launch(const ising_hmc_t *h, int *threads, int *depth
 ising_status ising_hmc_set_chain_split(ising_hmc_t *h, int ctas);
 int ising_hmc_get_chain_split(const ising_hmc_t *h);
 
+/* How the fused FP32 lattice kernel stages psi and p planes into its
+ * shared-memory rings (Sec. 3's force evaluation streams the lattice plane by
+ * plane): ISING_STAGING_THREADS, every thread copies its share of a plane
+ * with cp.async; ISING_STAGING_BULK, one lane issues each plane as a bulk
+ * copy completing on an mbarrier (planes of whole 16-byte vectors: rows of a
+ * multiple of 4 sites); ISING_STAGING_AUTO (default), bulk for planes of at
+ * least 4 KB.  Results are bit for bit the same in every mode.  EINVAL for
+ * other forms, unknown modes, or bulk on rows that are not a multiple of 4. */
+enum { ISING_STAGING_AUTO = 0, ISING_STAGING_THREADS = 1, ISING_STAGING_BULK = 2 };
+ising_status ising_hmc_set_staging(ising_hmc_t *h, int mode);
+int ising_hmc_get_staging(const ising_hmc_t *h);
+
 /* Autotuner: times `reps` trajectories for every valid launch shape on a
  * temporary handle with the same lattice and the first chains' parameters
  * (the handle's own chains are not advanced), keeps the fastest shape, and

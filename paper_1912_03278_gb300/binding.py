@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libising_hmc.so")
 
 # status codes
 ISING_OK, ISING_EINVAL, ISING_ENOTPD, ISING_ENOMEM, ISING_ECUDA, ISING_ETIMEOUT, ISING_EBUSY = range(7)
+ISING_STAGING_AUTO, ISING_STAGING_THREADS, ISING_STAGING_BULK = range(3)
 STATUS_NAMES = ["OK", "EINVAL", "ENOTPD", "ENOMEM", "ECUDA", "ETIMEOUT", "EBUSY"]
 ISING_KIND_LATTICE, ISING_KIND_DENSE, ISING_KIND_INFINITE = 0, 1, 2
 _KINDS = {"lattice": ISING_KIND_LATTICE, "dense": ISING_KIND_DENSE,
@@ -100,6 +101,8 @@ def load(path: str | None = None):
         "ising_hmc_autotune": (c_int, [P, c_int, P]),
         "ising_hmc_set_chain_split": (c_int, [P, c_int]),
         "ising_hmc_get_chain_split": (c_int, [P]),
+        "ising_hmc_set_staging": (c_int, [P, c_int]),
+        "ising_hmc_get_staging": (c_int, [P]),
         "ising_group_autotune": (c_int, [P, c_int, P]),
         "ising_group_create": (c_int, [P, c_int, P]),
         "ising_group_trajectories": (c_int, [P, c_int64, c_uint64]),
@@ -372,6 +375,14 @@ def ising_hmc_set_chain_split(h, ctas):
 
 def ising_hmc_get_chain_split(h) -> int:
     return load().ising_hmc_get_chain_split(h)
+
+
+def ising_hmc_set_staging(h, mode):
+    _check(h, load().ising_hmc_set_staging(h, int(mode)))
+
+
+def ising_hmc_get_staging(h) -> int:
+    return load().ising_hmc_get_staging(h)
 
 
 def ising_group_autotune(g, reps=2) -> float:
@@ -853,6 +864,14 @@ class IsingHMC:
     @property
     def chain_split(self):
         return ising_hmc_get_chain_split(self.h)
+
+    def set_staging(self, mode):
+        """ISING_STAGING_AUTO, _THREADS or _BULK (FP32 lattice form)."""
+        ising_hmc_set_staging(self.h, mode)
+
+    @property
+    def staging(self):
+        return ising_hmc_get_staging(self.h)
 
     def sync(self):
         ising_hmc_sync(self.h)

@@ -33,6 +33,7 @@
 #include "df32.cuh"
 #include "device_common.cuh"
 #include "internal.h"
+#include "mbarrier.cuh"
 
 namespace ihmc {
 namespace {
@@ -45,8 +46,10 @@ constexpr int MAX_THREADS = 512;
 constexpr int MAX_THREADS_UNSPLIT = 256;
 constexpr int MAX_CS = 8;                    // CTAs per chain (portable cluster size)
 constexpr int XCH_WORDS = 8;                 // per-CTA sums exchanged in a cluster
-// block reduction (32 warps x 8 doubles), broadcast words, two exchange buffers
-constexpr int RED_BYTES = 32 * 8 * 8 + 16 + 2 * XCH_WORDS * 8;
+constexpr int MAX_BARS = 16;                 // copy-group mbarriers (one per psi ring slot)
+// block reduction (32 warps x 8 doubles), broadcast words, two exchange
+// buffers, the copy-group mbarriers
+constexpr int RED_BYTES = 32 * 8 * 8 + 16 + 2 * XCH_WORDS * 8 + MAX_BARS * 8;
 
 // F(z) trails u by LAG planes: with LAG = 1 a plane's force reads only u
 // planes finished in earlier iterations, so one barrier per plane suffices.
@@ -371,7 +374,7 @@ __device__ __forceinline__ void vector_action(const FusedArgs &A, const ActConst
         sv = df_add_q(sv, si);
         const float hf = A.hdf ? kc.betaf * A.hdf[site0 + q].x : kc.hpf;
         const float tq = tpre ? tpre->v[q]
-                              : tanh_f(fmaf(kc.Cf, ps, sign * kc.bJf * n.nb.v[q]) + hf);
+                              : tanh_f(fmaf(kc.Cf, ps, fmaf(sign * kc.bJf, n.nb.v[q], hf)));
         vT += tq;
         vAT = fmaf(a.hi, tq, vAT);
         if (has_h) vHT = fmaf(hf, tq, vHT);
@@ -422,13 +425,29 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 // estimators of the start configuration (psi read by this pass) with the
 // spin draw of a configuration set from outside -- the same per-site code, in
 // the same per-thread order, as the evaluation sweep.
+// Staging.  Bulk (A.bulk with VEC = 4, every plane a whole number of 16-byte
+// vectors): one lane of warp 0 issues a copy group as one or two bulk copies
+// (psi plane, p plane) that complete on the mbarrier of the group's psi slot,
+// and every thread waits on it; `phase` holds the parity each slot's barrier is at (the same in every
+// thread, carried from pass to pass).  A wait that runs out flags
+// KERR_TIMEOUT and sets `dead`: no copy is issued or waited for after that,
+// the launch finishes on whatever the rings hold and the host reports the
+// error.  Otherwise every thread copies its share of each plane with 16-byte
+// (VEC = 4) or 4-byte cp.async, which suits small planes better: there the
+// copies are short and the issuing warp's extra work is on every plane's
+// critical path.
 template <int DIM, int VEC, int D, bool FIRST, bool LAST, bool EV = false>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
                          const Slots &sl, float *smem, const float4 *tab, Acc &acc, int z0,
-                         int nzs, Acc *eacc = nullptr) {
+                         int nzs, uint64_t *bars, uint32_t &phase, volatile int *dead,
+                         Acc *eacc = nullptr) {
     constexpr int R = D + 4 + LAG;   // psi ring slots
     constexpr int RP = D + 2 + LAG;  // p ring slots
     constexpr int RU = 3 + LAG;      // u ring slots
+    static_assert(R <= MAX_BARS, "one mbarrier per psi ring slot");
+    const bool bulk = VEC == 4 && A.bulk;
+    // warp index as a value the compiler sees as the same in every lane
+    const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
     const Geometry &g = A.g;
     const int P = g.P;
     float *psi_ring = smem;
@@ -445,8 +464,26 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     // copy group s: psi plane z0 + s - 2 (periodic) into psi slot s % R and
     // p plane z0 + s - 4 into p slot s % RP (slots passed in: the loop below
     // advances them without a division)
+    const uint32_t pbytes = (uint32_t)P * 4u;
     auto issue = [&](int s, int slot_psi, int slot_p) {
         const int zpsi = s - 2;
+        if (bulk) {
+            // groups past psi plane nzs + 1 are empty (their p plane is
+            // past the slab as well) and take no barrier phase; warp 0
+            // forms the (warp-uniform) addresses, one elected lane issues
+            if (zpsi > nzs + 1 || warp != 0 || *dead) return;
+            const int zp = s - 4;
+            const bool with_p = !FIRST && zp >= 0 && zp < nzs;   // the first pass draws p
+            uint64_t *bar = bars + slot_psi;
+            const float *src_psi = gsrc + (int64_t)wrap_plane(z0 + zpsi, nz) * P;
+            if (mb::elect_one()) {
+                mb::expect_tx(bar, with_p ? 2u * pbytes : pbytes);
+                mb::bulk_g2s(psi_ring + slot_psi * P, src_psi, pbytes, bar);
+                if (with_p) mb::bulk_g2s(p_ring + slot_p * P, gp + (int64_t)zp * P, pbytes, bar);
+            }
+            __syncwarp();
+            return;
+        }
         if (zpsi <= nzs + 1) {
             const int zw = wrap_plane(z0 + zpsi, nz);
             const float *src = gsrc + (int64_t)zw * P;
@@ -475,7 +512,20 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     auto wrapR = [](int x) { return x >= R ? x - R : (x < 0 ? x + R : x); };
     auto wrapRP = [](int x) { return x >= RP ? x - RP : x; };
 
+    // copy group s (s <= nzs + 3) completes on the barrier of psi slot s % R
+    auto wait_group = [&](int slot) {
+        if (!*dead && !mb::wait(bars + slot, (phase >> slot) & 1u)) {
+            *dead = 1;
+            atomicOr(A.err, KERR_TIMEOUT);
+        }
+        phase ^= 1u << slot;
+    };
+
     for (int s = 0; s <= D + 2; ++s) issue(s, s % R, s % RP);
+    if (bulk) {
+        wait_group(0);   // psi planes -2 and -1; plane 0 is waited for at it = -1
+        wait_group(1);
+    }
     int s_next = D + 3;
     // at iteration it: sq = slot of psi plane it + 1, sp = p slot of copy group
     // it + D + 4 (the group issued in that iteration)
@@ -486,7 +536,11 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     if constexpr (LAST || EV) kc = act_const(prm);
 
     for (int it = -1; it <= nzs + LAG; ++it) {
-        cp_wait<D>();
+        if (bulk) {
+            if (it <= nzs) wait_group(sq);   // group it + 3: psi plane it + 1, p plane it - 1
+        } else {
+            cp_wait<D>();
+        }
         __syncthreads();
         // group it + D + 4 takes the psi slot of plane it - 3 (used last by the
         // previous iteration's drift) and the p slot it + 1
@@ -510,10 +564,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                     hpv[q] = A.hdf ? prm.betaf * A.hdf[(int64_t)zw * P + e0 + q].x : prm.hpf;
                 Vec<VEC> t;
 #pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    const float a = fmaf(Cf, n.c.v[q], bJf * n.nb.v[q]);
-                    t.v[q] = tanh_f(a + hpv[q]);
-                }
+                for (int q = 0; q < VEC; ++q)
+                    t.v[q] = tanh_f(fmaf(Cf, n.c.v[q], fmaf(bJf, n.nb.v[q], hpv[q])));
                 if (sl.valid[k]) {
                     Vec<VEC> u;
 #pragma unroll
@@ -583,7 +635,12 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         sq = wrapR(sq + 1);
         sp = wrapRP(sp + 1);
     }
-    cp_wait<0>();
+    if (bulk) {
+        // the next pass's bulk copies read the planes written here
+        mb::fence_global_to_async();
+    } else {
+        cp_wait<0>();
+    }
     __syncthreads();
 }
 
@@ -685,8 +742,9 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
     float4 *tab_s = reinterpret_cast<float4 *>(smem + rb / 4);
     const float4 *tab = tab_in_smem ? tab_s : A.lpe_tab;
     double *red = reinterpret_cast<double *>(smem + rb / 4 + (tab_in_smem ? LOG1PEXP_NODES * 4 : 0));
-    int *bcast = reinterpret_cast<int *>(red + 32 * 8);
+    int *bcast = reinterpret_cast<int *>(red + 32 * 8);   // [0], [1] broadcasts, [2] dead flag
     double *xch = red + 32 * 8 + 2;   // two exchange buffers of XCH_WORDS
+    uint64_t *bars = reinterpret_cast<uint64_t *>(xch + 2 * XCH_WORDS);
 
     // CTAs per chain (the launch's cluster size) and this CTA's slab
     const int cs = CL ? cluster_size() : 1, cr = CL ? cluster_rank() : 0;
@@ -705,10 +763,17 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
         momenta_sweep<VEC>(A, chain, A.traj0, sl, z0, z1);
         return;
     }
-    if (tab_in_smem) {
+    if (tab_in_smem)
         for (int i = threadIdx.x; i < LOG1PEXP_NODES; i += blockDim.x) tab_s[i] = A.lpe_tab[i];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        bcast[2] = 0;
+        if (VEC == 4 && A.bulk) {
+            for (int i = 0; i < D + 4 + LAG; ++i) mb::init(bars + i, 1);
+            mb::init_fence();
+        }
     }
+    __syncthreads();
+    uint32_t phase = 0;   // parity of each copy-group barrier
 
     if (A.mode == MODE_EVAL) {
         Acc acc = acc_zero();
@@ -749,15 +814,19 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
             pc.last = (j == S.n_pass - 1);
             pc.traj = traj;
             // (n_pass >= 2: the first pass is never the last)
+            const int nzs = z1 - z0;
             if (pc.first && eval_start)
                 run_pass<DIM, VEC, D, true, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0,
-                                                         z1 - z0, &ea);
+                                                         nzs, bars, phase, bcast + 2, &ea);
             else if (pc.first)
-                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
+                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
+                                                   bars, phase, bcast + 2);
             else if (pc.last)
-                run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
+                run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
+                                                   bars, phase, bcast + 2);
             else
-                run_pass<DIM, VEC, D, false, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, z1 - z0);
+                run_pass<DIM, VEC, D, false, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
+                                                    bars, phase, bcast + 2);
             // the next pass reads (and the one after rewrites) the planes
             // beyond this slab's ends, written by the neighbouring CTAs
             if (CL && cs > 1) cluster_barrier();
@@ -837,6 +906,7 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
                 const float *gs = sel3(A, start) + off;
                 float *gf = sel3(A, f) + off;
                 for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) gf[i] = -gs[i];
+                if (VEC == 4 && A.bulk) mb::fence_global_to_async();   // read by the next pass's copies
                 start = f;
                 if (threadIdx.x == 0 && lead) st->start = f;
                 if (CL && cs > 1) cluster_barrier();   // the next pass reads the other slabs' planes

@@ -66,6 +66,7 @@ struct FusedArgs {
     int cs;                  // CTAs per chain (the launch's cluster size; lattice kernel)
     int eval_start;          // lattice kernel: evaluate S and the observables of the start
                              // configuration in the first trajectory's first pass
+    int bulk;                // lattice kernel: stage planes by bulk copies (16-byte planes)
     int *err;
 };
 

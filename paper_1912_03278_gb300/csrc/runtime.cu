@@ -43,7 +43,7 @@ struct ising_hmc {
     float *d_lpe = nullptr;
     int *d_err = nullptr;
     // launch shape of the fused kernel: threads per CTA, prefetch depth, CTAs per chain
-    int threads = 0, depth = 0, cs = 1;
+    int threads = 0, depth = 0, cs = 1, staging = ISING_STAGING_AUTO;
     // FP32 lattice form: the configurations were set from outside and their
     // action is evaluated by the next trajectory's first force pass
     bool eval_pending = false;
@@ -107,6 +107,8 @@ static size_t state_elem(const ising_hmc *h) {
 // Default shift: the positive-definiteness bound of Sec. 2 plus this margin
 // (the shift C = bound + 0.1 the paper's workloads use).
 static constexpr double DEFAULT_SHIFT_MARGIN = 0.1;
+// automatic plane staging: bulk copies from this plane size up
+static constexpr int64_t BULK_AUTO_MIN_BYTES = 4096;
 
 // Integrator schedules (Sec. 3: symmetric symplectic integrators).
 static void make_schedule(int integrator, int n_md, Schedule &s) {
@@ -360,6 +362,17 @@ static cudaError_t launch_fused(ising_hmc *h, const FusedArgs &a) {
     return launch_fused_lattice(a, h->sched, h->threads, h->depth, h->stream);
 }
 
+
+// Plane staging of the lattice kernel: bulk copies need planes of whole
+// 16-byte vectors; automatic choice: bulk for planes of at least 4 KB (small
+// planes stage faster with every thread's cp.async).
+static int staging_bulk(const ising_hmc *h) {
+    const Geometry &g = h->g;
+    if (!(g.X % 4 == 0 && g.P % 4 == 0)) return 0;
+    if (h->staging == ISING_STAGING_BULK) return 1;
+    if (h->staging == ISING_STAGING_THREADS) return 0;
+    return (int64_t)g.P * 4 >= BULK_AUTO_MIN_BYTES;
+}
 static FusedArgs fused_args(ising_hmc *h) {
     FusedArgs a{};
     for (int i = 0; i < 3; ++i) a.psi[i] = (float *)h->psi[i];
@@ -374,6 +387,7 @@ static FusedArgs fused_args(ising_hmc *h) {
     a.chain0 = 0;
     a.n_chains = h->n_chains;
     a.cs = is_fp32_lattice(h) ? h->cs : 1;
+    a.bulk = staging_bulk(h);
     a.err = h->d_err;
     return a;
 }
@@ -1324,6 +1338,19 @@ ising_status ising_hmc_set_chain_split(ising_hmc_t *h, int ctas) {
 
 int ising_hmc_get_chain_split(const ising_hmc_t *h) { return h ? h->cs : -1; }
 
+ising_status ising_hmc_set_staging(ising_hmc_t *h, int mode) {
+    if (!h) return ISING_EINVAL;
+    if (!is_fp32_lattice(h)) return fail(h, ISING_EINVAL, "plane staging applies to the FP32 lattice form");
+    if (mode < ISING_STAGING_AUTO || mode > ISING_STAGING_BULK)
+        return fail(h, ISING_EINVAL, "unknown staging mode %d", mode);
+    if (mode == ISING_STAGING_BULK && !(h->g.X % 4 == 0 && h->g.P % 4 == 0))
+        return fail(h, ISING_EINVAL, "bulk staging needs rows of a multiple of 4 sites");
+    h->staging = mode;
+    return ISING_OK;
+}
+
+int ising_hmc_get_staging(const ising_hmc_t *h) { return h ? h->staging : -1; }
+
 ising_status ising_hmc_dense_forces(ising_hmc_t *h, int n) {
     if (!h) return ISING_EINVAL;
     if (!is_dense_tc(h)) return fail(h, ISING_EINVAL, "dense_forces applies to the BF16 dense form");
@@ -1369,6 +1396,7 @@ static ising_status clone_for_tuning(ising_hmc *h, int nt, ising_hmc **out) {
         (*out)->threads = h->threads;
         (*out)->depth = h->depth;
         (*out)->cs = h->cs;
+        (*out)->staging = h->staging;
     }
     return st;
 }

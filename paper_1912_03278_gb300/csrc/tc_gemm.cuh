@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mbarrier.cuh"
+
 namespace ihmc {
 namespace tc {
 
@@ -47,38 +49,18 @@ constexpr int EPI_GROUPS = IHMC_EPI_GROUPS;
 constexpr int EPI_WARPS = 4 * EPI_GROUPS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, then the epilogue
 // bounded waits: try_wait polls before the kernel gives up and flags an error
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
+constexpr uint32_t WAIT_LIMIT = mb::WAIT_LIMIT;
+using mb::smem_u32;
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) { mb::init(bar, count); }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
+    mb::expect_tx(bar, bytes);
 }
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
+    return mb::try_wait(bar, parity);
 }
-
 // Wait for the phase with the given parity; false if the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    return mb::wait(bar, parity);
 }
 
 // 2D TMA tile load (x = inner coordinate in elements, y = row), completion
