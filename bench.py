@@ -169,20 +169,31 @@ def measured_peaks_all():
         return {}
 
 
-def traffic_record(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the
-    current kernel source."""
+TRAFFIC_SOURCES = ("fused_lattice_impl.cuh", "fused_lattice_2d.cu", "df32.cuh",
+                   "device_common.cuh", "mbarrier.cuh")
+
+
+def traffic_source_sha():
+    """Hash of the kernel sources a committed traffic figure was measured on."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "traffic.json")
     csrc = os.path.join(ROOT, "paper_1912_03278_gb300", "csrc")
-    srcs = [os.path.join(csrc, f) for f in ("fused_lattice_impl.cuh", "fused_lattice_2d.cu",
-                                            "df32.cuh", "device_common.cuh")]
+    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in TRAFFIC_SOURCES)
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def traffic_record(kernel, workload, depth=None):
+    """DRAM bytes per launch from a committed ncu summary (for the launch's
+    ring depth where one was captured), if it matches the current kernel
+    source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        h = hashlib.sha256(b"".join(open(x, "rb").read() for x in srcs)).hexdigest()[:16]
         rec = d.get(kernel, {}).get(workload)
-        if rec and rec.get("source_sha") == h:
+        if rec and rec.get("source_sha") == traffic_source_sha():
+            by_depth = rec.get("bytes_per_launch_by_depth", {})
+            if depth is not None and str(depth) in by_depth:
+                return by_depth[str(depth)]
             return rec.get("bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -443,7 +454,8 @@ def run_ours(args):
     achieved = alg_bytes / dur / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": traffic_record("fused_lattice_kernel", "2d_L%d_B%d" % (big, n_chains)),
+                "traffic": traffic_record("fused_lattice_kernel", "2d_L%d_B%d" % (big, n_chains),
+                                          sims[big].launch[1]),
                 "kernel": "fused_lattice_kernel", "algorithmic_bytes_per_launch": alg_bytes,
                 "ms_per_launch": dur * 1e3}
 

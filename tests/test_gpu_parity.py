@@ -51,7 +51,8 @@ def _count_near_ties(model, psi, form, seed, chain, traj):
 
 def _parity_setup(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,), C=None,
                   eps=0.1, n_md=5, prec=FP32, integrator=0, flip_every=0, traj=3, seed=11,
-                  psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0, launch=None, split=None):
+                  psi_scale=0.5, n_traj=1, n_sites=0, Jnn=1.0, launch=None, split=None,
+                  staging=None):
     """Create a handle at a common start state; returns the context of one
     parity case (the handle and everything the oracle needs)."""
     n_chains = len(betas)
@@ -82,6 +83,8 @@ def _parity_setup(kind="lattice", dim=2, L=(8, 8), J=None, h=0.0, betas=(0.44,),
         if split is not None:
             sim.set_chain_split(split)
             assert sim.chain_split == split
+        if staging is not None:
+            sim.set_staging(staging)
         sim.set_state(psi0, next_traj=traj)
         for k in range(n_traj - 1):
             sim.trajectories(1, seed)
@@ -356,6 +359,56 @@ def test_invalid_splits_rejected():
             ring.set_chain_split(2)
     finally:
         ring.close()
+
+
+@pytest.mark.parametrize("kw,split", [
+    (dict(dim=2, L=(64, 36), beta=np.array([0.44, 0.4]), h=0.02, eps=0.08, n_md=5,
+          n_chains=2, flip_every=2), 1),
+    (dict(dim=3, L=(24, 24, 16), beta=np.array([0.2217, 0.24, 0.2]), h=0.05, eps=0.09,
+          n_md=6, n_chains=3, flip_every=2), 1),
+    (dict(dim=3, L=(24, 24, 16), beta=np.array([0.2217, 0.24, 0.2]), h=0.05, eps=0.09,
+          n_md=6, n_chains=3, flip_every=2), 2),
+])
+def test_staging_modes_agree_bit_for_bit(kw, split):
+    """Per-thread cp.async and bulk-copy staging put the same plane values in
+    the same ring slots, so every result is identical, records included; the
+    bulk mode also agrees with the oracle."""
+    runs = []
+    for mode in (pkg.ISING_STAGING_THREADS, pkg.ISING_STAGING_BULK):
+        sim = pkg.IsingHMC(**kw)
+        try:
+            if split > 1:
+                sim.set_chain_split(split)
+            sim.set_staging(mode)
+            assert sim.staging == mode
+            sim.trajectories(3, 9)
+            sim.trajectories(2, 9)
+            runs.append((sim.state(), sim.state(pkg.ISING_STATE_P_END), sim.records(),
+                         sim.chain_sums()))
+        finally:
+            sim.close()
+    for x, y in zip(runs[0], runs[1]):
+        assert np.array_equal(x, y)
+
+
+def test_bulk_staging_one_trajectory_parity():
+    """One trajectory with bulk staging forced on a small 2D lattice against
+    the oracle (psi to 1e-5, dH to 1e-6)."""
+    one_trajectory_parity(dim=2, L=(32, 12), betas=(0.44, 0.3), h=0.05, eps=0.1, n_md=4,
+                          staging=pkg.ISING_STAGING_BULK)
+
+
+def test_invalid_staging_rejected():
+    sim = pkg.IsingHMC(dim=2, L=(30, 8), beta=0.4, eps=0.1, n_md=2)   # rows of 30 sites
+    try:
+        with pytest.raises(pkg.IsingError):
+            sim.set_staging(pkg.ISING_STAGING_BULK)
+        with pytest.raises(pkg.IsingError):
+            sim.set_staging(7)
+        sim.set_staging(pkg.ISING_STAGING_THREADS)
+        assert sim.staging == pkg.ISING_STAGING_THREADS
+    finally:
+        sim.close()
 
 
 # ------------------------------------------------------------ plain FP64 ----
