@@ -169,6 +169,8 @@ def measured_peaks_all():
         return {}
 
 
+STAGING_NAMES = {0: "auto", 1: "threads", 2: "bulk"}
+
 TRAFFIC_SOURCES = ("fused_lattice_impl.cuh", "fused_lattice_2d.cu", "df32.cuh",
                    "device_common.cuh", "mbarrier.cuh")
 
@@ -404,7 +406,8 @@ def run_ours(args):
     if not args.no_autotune:
         for L in Ls:
             ms = sims[L].autotune(reps=2)
-            tuned_launch[str(L)] = dict(zip(("threads", "depth"), sims[L].launch), ms=ms)
+            tuned_launch[str(L)] = dict(zip(("threads", "depth"), sims[L].launch), ms=ms,
+                                        staging=STAGING_NAMES[sims[L].staging])
     hot_start(pkg, sims, seed, betas, C)
     tune_trace = tune_eps(sims, betas, args.tune_rounds, seed)
     for L in Ls:
@@ -1077,6 +1080,7 @@ def mixed_3d_rate(pkg, steps=4, seed=31):
         group_ms = grp.autotune(reps=4)
         for s in sims:
             tuned[s.kw["L"][0]]["ctas_per_chain"] = s.chain_split
+            tuned[s.kw["L"][0]]["staging"] = STAGING_NAMES[s.staging]
         grp.trajectories(2, seed)
         grp.sync()
         gs = torch.cuda.ExternalStream(grp.stream)

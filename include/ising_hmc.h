@@ -268,8 +268,10 @@ int ising_hmc_get_staging(const ising_hmc_t *h);
  * (the handle's own chains are not advanced), keeps the fastest shape, and
  * returns its time per trajectory in *best_ms (may be NULL).  The search
  * covers threads and depth at one CTA per chain, then chain splits of 2, 4
- * and 8 CTAs at the best thread count.  Allocates the temporary handle;
- * synchronises. */
+ * and 8 CTAs at the best thread count, then (if the plane staging is
+ * ISING_STAGING_AUTO and the rows allow bulk copies) both staging modes at
+ * the chosen shape, setting the faster one explicitly.  Allocates the
+ * temporary handle; synchronises. */
 ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms);
 
 /* Groups: FP32 lattice handles of any mix of lattice sizes advanced together

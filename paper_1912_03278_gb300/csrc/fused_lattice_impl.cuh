@@ -425,7 +425,7 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 // estimators of the start configuration (psi read by this pass) with the
 // spin draw of a configuration set from outside -- the same per-site code, in
 // the same per-thread order, as the evaluation sweep.
-// Staging.  Bulk (A.bulk with VEC = 4, every plane a whole number of 16-byte
+// Staging.  Bulk (BULK instances, VEC = 4: every plane a whole number of 16-byte
 // vectors): one lane of warp 0 issues a copy group as one or two bulk copies
 // (psi plane, p plane) that complete on the mbarrier of the group's psi slot,
 // and every thread waits on it; `phase` holds the parity each slot's barrier is at (the same in every
@@ -436,7 +436,7 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 // (VEC = 4) or 4-byte cp.async, which suits small planes better: there the
 // copies are short and the issuing warp's extra work is on every plane's
 // critical path.
-template <int DIM, int VEC, int D, bool FIRST, bool LAST, bool EV = false>
+template <int DIM, int VEC, int D, bool BULK, bool FIRST, bool LAST, bool EV = false>
 __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParams &prm, int chain,
                          const Slots &sl, float *smem, const float4 *tab, Acc &acc, int z0,
                          int nzs, uint64_t *bars, uint32_t &phase, volatile int *dead,
@@ -445,7 +445,8 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     constexpr int RP = D + 2 + LAG;  // p ring slots
     constexpr int RU = 3 + LAG;      // u ring slots
     static_assert(R <= MAX_BARS, "one mbarrier per psi ring slot");
-    const bool bulk = VEC == 4 && A.bulk;
+    constexpr bool bulk = BULK;
+    static_assert(!BULK || VEC == 4, "bulk staging copies whole 16-byte vectors");
     // warp index as a value the compiler sees as the same in every lane
     const int warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
     const Geometry &g = A.g;
@@ -467,7 +468,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     const uint32_t pbytes = (uint32_t)P * 4u;
     auto issue = [&](int s, int slot_psi, int slot_p) {
         const int zpsi = s - 2;
-        if (bulk) {
+        if constexpr (bulk) {
             // groups past psi plane nzs + 1 are empty (their p plane is
             // past the slab as well) and take no barrier phase; warp 0
             // forms the (warp-uniform) addresses, one elected lane issues
@@ -522,7 +523,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     };
 
     for (int s = 0; s <= D + 2; ++s) issue(s, s % R, s % RP);
-    if (bulk) {
+    if constexpr (bulk) {
         wait_group(0);   // psi planes -2 and -1; plane 0 is waited for at it = -1
         wait_group(1);
     }
@@ -536,7 +537,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     if constexpr (LAST || EV) kc = act_const(prm);
 
     for (int it = -1; it <= nzs + LAG; ++it) {
-        if (bulk) {
+        if constexpr (bulk) {
             if (it <= nzs) wait_group(sq);   // group it + 3: psi plane it + 1, p plane it - 1
         } else {
             cp_wait<D>();
@@ -635,7 +636,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         sq = wrapR(sq + 1);
         sp = wrapRP(sp + 1);
     }
-    if (bulk) {
+    if constexpr (bulk) {
         // the next pass's bulk copies read the planes written here
         mb::fence_global_to_async();
     } else {
@@ -725,7 +726,7 @@ __device__ __forceinline__ void set_obs(ChainState *st, const ChainParams &prm, 
 
 // CL: compiled for chains split over a cluster (launched with a cluster
 // size); the unsplit instance carries no cluster instructions at all.
-template <int DIM, int VEC, int D, bool CL>
+template <int DIM, int VEC, int D, bool CL, bool BULK>
 __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1 : 2)
     fused_lattice_kernel(FusedArgs A, Schedule S) {
     extern __shared__ float4 smem_f4[];
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
         for (int i = threadIdx.x; i < LOG1PEXP_NODES; i += blockDim.x) tab_s[i] = A.lpe_tab[i];
     if (threadIdx.x == 0) {
         bcast[2] = 0;
-        if (VEC == 4 && A.bulk) {
+        if constexpr (BULK) {
             for (int i = 0; i < D + 4 + LAG; ++i) mb::init(bars + i, 1);
             mb::init_fence();
         }
@@ -816,16 +817,16 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
             // (n_pass >= 2: the first pass is never the last)
             const int nzs = z1 - z0;
             if (pc.first && eval_start)
-                run_pass<DIM, VEC, D, true, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0,
+                run_pass<DIM, VEC, D, BULK, true, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0,
                                                          nzs, bars, phase, bcast + 2, &ea);
             else if (pc.first)
-                run_pass<DIM, VEC, D, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
+                run_pass<DIM, VEC, D, BULK, true, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
                                                    bars, phase, bcast + 2);
             else if (pc.last)
-                run_pass<DIM, VEC, D, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
+                run_pass<DIM, VEC, D, BULK, false, true>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
                                                    bars, phase, bcast + 2);
             else
-                run_pass<DIM, VEC, D, false, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
+                run_pass<DIM, VEC, D, BULK, false, false>(A, pc, prm, chain, sl, smem, tab, acc, z0, nzs,
                                                     bars, phase, bcast + 2);
             // the next pass reads (and the one after rewrites) the planes
             // beyond this slab's ends, written by the neighbouring CTAs
@@ -906,7 +907,7 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
                 const float *gs = sel3(A, start) + off;
                 float *gf = sel3(A, f) + off;
                 for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) gf[i] = -gs[i];
-                if (VEC == 4 && A.bulk) mb::fence_global_to_async();   // read by the next pass's copies
+                if constexpr (BULK) mb::fence_global_to_async();   // read by the next pass's copies
                 start = f;
                 if (threadIdx.x == 0 && lead) st->start = f;
                 if (CL && cs > 1) cluster_barrier();   // the next pass reads the other slabs' planes
@@ -939,12 +940,15 @@ __global__ void __launch_bounds__(CL ? MAX_THREADS : MAX_THREADS_UNSPLIT, CL ? 1
 template <class K>
 static int launch_smem(K kern, const Geometry &g, int D, int threads) {
     struct Memo {
+        const void *kern;
         int P, D, threads, smem;
     };
     thread_local Memo memo[8] = {};
     thread_local int next = 0;
     for (const Memo &m : memo)
-        if (m.smem && m.P == g.P && m.D == D && m.threads == threads) return m.smem;
+        if (m.smem && m.kern == reinterpret_cast<const void *>(kern) && m.P == g.P && m.D == D &&
+            m.threads == threads)
+            return m.smem;
     const int base = (int)(ring_bytes(g.P, D) + RED_BYTES);
     const int with_tab = base + LOG1PEXP_NODES * 16;
     int n_with = 0, n_without = 0;
@@ -955,15 +959,15 @@ static int launch_smem(K kern, const Geometry &g, int D, int threads) {
         n_with >= n_without)
         smem = with_tab;
     cudaGetLastError();
-    memo[next] = Memo{g.P, D, threads, smem};
+    memo[next] = Memo{reinterpret_cast<const void *>(kern), g.P, D, threads, smem};
     next = (next + 1) % 8;
     return smem;
 }
 
-template <int DIM, int VEC, int D, bool CL>
+template <int DIM, int VEC, int D, bool CL, bool BULK = false>
 cudaError_t kernel_node(const FusedArgs &a, int threads, cudaKernelNodeParams *np, void **args) {
     static bool configured = false;
-    auto kern = fused_lattice_kernel<DIM, VEC, D, CL>;
+    auto kern = fused_lattice_kernel<DIM, VEC, D, CL, BULK>;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              227 * 1024);
@@ -984,6 +988,13 @@ template <int DIM, bool CL>
 cudaError_t node_dim(const FusedArgs &a, int threads, int depth, int vec, cudaKernelNodeParams *np,
                      void **args) {
     if (vec == 4) {
+        // the staging is a compile-time choice: one kernel carrying both
+        // paths measured slower in either mode (register allocation)
+        if (a.bulk) {
+            if (depth >= 4) return kernel_node<DIM, 4, 4, CL, true>(a, threads, np, args);
+            if (depth >= 2) return kernel_node<DIM, 4, 2, CL, true>(a, threads, np, args);
+            return kernel_node<DIM, 4, 1, CL, true>(a, threads, np, args);
+        }
         if (depth >= 4) return kernel_node<DIM, 4, 4, CL>(a, threads, np, args);
         if (depth >= 2) return kernel_node<DIM, 4, 2, CL>(a, threads, np, args);
         return kernel_node<DIM, 4, 1, CL>(a, threads, np, args);

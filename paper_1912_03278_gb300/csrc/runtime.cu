@@ -1421,7 +1421,7 @@ static double time_trajectories(ising_hmc *t, int reps, cudaEvent_t e0, cudaEven
 // temporary copy of the handle's geometry and parameters (so the handle's own
 // chains do not move) and keep the fastest; then try splitting every chain
 // over 2, 4 and 8 CTAs at the best thread count and at 256..512 threads, every
-// depth.
+// depth; then, if the staging is automatic, both staging modes at the result.
 ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
     NvtxRange nvtx_range("ising_hmc_autotune");
     if (!h) return ISING_EINVAL;
@@ -1480,12 +1480,32 @@ ising_status ising_hmc_autotune(ising_hmc_t *h, int reps, double *best_ms) {
             }
         }
     }
+    // plane staging (when left to the automatic choice): both modes timed at
+    // the chosen shape, back to back
+    int stg = h->staging;
+    if (h->staging == ISING_STAGING_AUTO && h->g.X % 4 == 0 && h->g.P % 4 == 0) {
+        t->threads = bt;
+        t->depth = bd;
+        t->cs = bc;
+        double ms_mode[2] = {0.0, 0.0};
+        const int modes[2] = {ISING_STAGING_THREADS, ISING_STAGING_BULK};
+        for (int i = 0; i < 2; ++i) {
+            t->staging = modes[i];
+            ms_mode[i] = time_trajectories(t, reps, e0, e1);
+        }
+        if (ms_mode[0] > 0 && ms_mode[1] > 0) {
+            const int i = ms_mode[1] < ms_mode[0] ? 1 : 0;
+            stg = modes[i];
+            best = ms_mode[i];
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ising_hmc_destroy(t);
     h->threads = bt;
     h->depth = bd;
     h->cs = bc;
+    h->staging = stg;
     if (best_ms) *best_ms = best;
     return ISING_OK;
 }
@@ -1500,7 +1520,8 @@ struct ising_group {
     std::vector<FusedArgs> args;
     std::vector<std::array<void *, 2>> argv;
     std::vector<cudaGraphNode_t> nodes;
-    std::vector<int> shape;  // threads, depth, CTAs per chain of every member at instantiation
+    std::vector<int> shape;  // threads, depth, CTAs per chain, bulk staging of every member
+                             // at instantiation
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t stream = nullptr;
@@ -1531,7 +1552,7 @@ static ising_status group_build_graph(ising_group *g) {
     g->args.resize(n);
     g->argv.resize(n);
     g->nodes.resize(n);
-    g->shape.assign(3 * n, 0);
+    g->shape.assign(4 * n, 0);
     if (cudaGraphCreate(&g->graph, 0) != cudaSuccess) return gfail(g, ISING_ECUDA, "graph create failed");
     // nodes are added largest work first: independent nodes start roughly in
     // the order they were added, and the longest members are the critical path
@@ -1553,9 +1574,10 @@ static ising_status group_build_graph(ising_group *g) {
         if (e == cudaSuccess) e = cudaGraphAddKernelNode(&g->nodes[i], g->graph, nullptr, 0, &np);
         if (e == cudaSuccess && h->cs > 1) e = fused_lattice_node_cluster(g->nodes[i], h->cs);
         if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph node: %s", cudaGetErrorString(e));
-        g->shape[3 * i] = h->threads;
-        g->shape[3 * i + 1] = h->depth;
-        g->shape[3 * i + 2] = h->cs;
+        g->shape[4 * i] = h->threads;
+        g->shape[4 * i + 1] = h->depth;
+        g->shape[4 * i + 2] = h->cs;
+        g->shape[4 * i + 3] = staging_bulk(h);
     }
     cudaError_t e = cudaGraphInstantiate(&g->exec, g->graph, 0);
     if (e != cudaSuccess) return gfail(g, ISING_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -1611,8 +1633,8 @@ ising_status ising_group_trajectories_seeds(ising_group_t *g, int64_t n, const u
     if (n == 0) return ISING_OK;
     // rebuild if a member's launch shape changed (autotune, set_launch)
     for (size_t i = 0; i < g->m.size(); ++i)
-        if (g->shape[3 * i] != g->m[i]->threads || g->shape[3 * i + 1] != g->m[i]->depth ||
-            g->shape[3 * i + 2] != g->m[i]->cs) {
+        if (g->shape[4 * i] != g->m[i]->threads || g->shape[4 * i + 1] != g->m[i]->depth ||
+            g->shape[4 * i + 2] != g->m[i]->cs || g->shape[4 * i + 3] != staging_bulk(g->m[i])) {
             ising_status st = group_build_graph(g);
             if (st != ISING_OK) return st;
             break;

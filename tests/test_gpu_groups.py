@@ -127,6 +127,8 @@ def test_autotune_picks_valid_shape_and_keeps_chain():
         t, d = sim.launch
         assert 32 <= t <= 512 and d in (1, 2, 4)
         assert sim.chain_split in (1, 2, 4, 8)
+        # rows of 16 sites allow bulk copies: the autotuner settles the staging
+        assert sim.staging in (pkg.ISING_STAGING_THREADS, pkg.ISING_STAGING_BULK)
         assert np.array_equal(before, sim.state())   # the handle's chains did not move
         assert sim.traj_index == 0
         sim.trajectories(2, 9)
