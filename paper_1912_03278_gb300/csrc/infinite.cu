@@ -483,7 +483,10 @@ __device__ __forceinline__ void action_totals(const Acc &acc, double (&w)[5], Re
 // The thread's quads q = tid + k*nt, k < QPT, held in registers: x (psi), pm
 // (p); u between the two sweeps in shared memory (us[q], written and read by
 // the owning thread only).  One force evaluation, the same arithmetic in the
-// same order as inf_pass.
+// same order as inf_pass.  The first pass's momentum draw and the last pass's
+// action run in loops that are not unrolled, through a second shared array
+// (aux[q], again the owning thread's only): their code then appears once, not
+// once per quad, which keeps the kernel's instruction footprint small.
 template <bool V4, int QPT, bool FIRST, bool LAST>
 __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc, int chain,
                                          uint32_t traj, float kick, float drift, Quad (&x)[QPT],
@@ -492,6 +495,15 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
     const int64_t N = A.g.N;
     const int64_t nq = (N + 3) >> 2;
     const float Sf = cs.Sf;
+    float4 *aux = us + QPT * blockDim.x;
+    constexpr bool ONE_PASS = FIRST && LAST;   // (never with two or more passes)
+    if constexpr (FIRST && !ONE_PASS) {
+#pragma unroll 1
+        for (int k = 0; k < QPT; ++k) {
+            const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
+            if (q < nq) aux[q] = momenta4_f32((uint32_t)q, traj, (uint32_t)chain, A.seed);
+        }
+    }
     float su = 0.0f;
     f2 Sdf{0.0f, 0.0f};
     if constexpr (LAST) Sdf = csum_exact(cs, red);
@@ -507,7 +519,26 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
             for (int e = 0; e < 4; ++e) u.v[e] = t.v[e] - x[k].v[e];
             us[q] = make_float4(u.v[0], u.v[1], u.v[2], u.v[3]);
             su += quad_sum(u, n);
-            if constexpr (LAST) quad_action(A, kc, x[k], t, Sdf, i0, n, traj, A.seed, chain, tab, acc);
+            if constexpr (ONE_PASS)
+                quad_action(A, kc, x[k], t, Sdf, i0, n, traj, A.seed, chain, tab, acc);
+            else if constexpr (LAST)
+                aux[q] = make_float4(x[k].v[0], x[k].v[1], x[k].v[2], x[k].v[3]);
+        }
+    }
+    if constexpr (LAST && !ONE_PASS) {
+        // the proposal's action, quads in the same order (t recomputed: the
+        // same function of the same values)
+#pragma unroll 1
+        for (int k = 0; k < QPT; ++k) {
+            const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
+            if (q < nq) {
+                const int64_t i0 = 4 * q;
+                const int n = quad_len(i0, N);
+                const float4 w = aux[q];
+                const Quad xq{{w.x, w.y, w.z, w.w}};
+                const Quad t = quad_tanh(A, kc, xq, Sf, i0, n);
+                quad_action(A, kc, xq, t, Sdf, i0, n, traj, A.seed, chain, tab, acc);
+            }
         }
     }
     const float Uf = bsum_f32(su, red);
@@ -518,7 +549,8 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
         if (q < nq) {
             const int n = quad_len(4 * q, N);
             if constexpr (FIRST) {
-                const float4 w = momenta4_f32((uint32_t)q, traj, (uint32_t)chain, A.seed);
+                const float4 w = ONE_PASS ? momenta4_f32((uint32_t)q, traj, (uint32_t)chain, A.seed)
+                                          : aux[q];
                 pm[k].v[0] = w.x; pm[k].v[1] = w.y; pm[k].v[2] = w.z; pm[k].v[3] = w.w;
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -662,7 +694,7 @@ __global__ void __launch_bounds__(INF_MAX_THREADS, 2) infinite_kernel(FusedArgs 
     __shared__ float red_f[16];
     __shared__ f2 red_d[64];
     __shared__ int bcast[2];
-    extern __shared__ float4 us[];   // resident variant: u, QPT * blockDim.x quads
+    extern __shared__ float4 us[];   // resident variant: u and aux, QPT * blockDim.x quads each
     const int chain = A.chain0 + blockIdx.x;
     if (chain >= A.n_chains) return;
     const int64_t N = A.g.N;
@@ -795,20 +827,20 @@ static void *infinite_func(int qpt) {
 cudaError_t infinite_node(const FusedArgs &a, cudaKernelNodeParams *np, void **args) {
     const int qpt = infinite_qpt(a.g.N);
     np->func = (a.g.N % 4 == 0) ? infinite_func<true>(qpt) : infinite_func<false>(qpt);
-    static bool configured = false;   // room for the largest u array above the static 20.5 KB
+    static bool configured = false;   // room for the largest u and aux arrays above the static 20.5 KB
     if (!configured) {
         for (int q : {1, 2, 4, 8})
             for (void *f : {infinite_func<true>(q), infinite_func<false>(q)}) {
                 const cudaError_t e = cudaFuncSetAttribute(
-                    f, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * INF_MAX_THREADS * 16);
+                    f, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * INF_MAX_THREADS * 16);
                 if (e != cudaSuccess) return e;
             }
         configured = true;
     }
     np->gridDim = dim3((unsigned)(a.n_chains - a.chain0), 1, 1);
     np->blockDim = dim3((unsigned)infinite_threads(a.g.N), 1, 1);
-    // u of the resident variant: at most 8 quads x 256 threads x 16 B = 32 KB
-    np->sharedMemBytes = (unsigned)(qpt * infinite_threads(a.g.N) * sizeof(float4));
+    // u and aux of the resident variant: at most 2 x 8 quads x 256 threads x 16 B = 64 KB
+    np->sharedMemBytes = (unsigned)(2 * qpt * infinite_threads(a.g.N) * sizeof(float4));
     np->kernelParams = args;
     np->extra = nullptr;
     return cudaSuccess;
