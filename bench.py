@@ -1349,10 +1349,13 @@ def e2e_rate(pkg, sims, Ls, n_chains, seed, stream, steps=3):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(steps):
+        # every size's upload and trajectory are queued before any result is
+        # read, so a size's trajectory runs while the next size uploads
         for L in Ls:
             traj = sims[L].traj_index
             pkg.ising_hmc_set_state_native(sims[L].h, host[L].data_ptr(), traj)
             sims[L].trajectories(1, seed)
+        for L in Ls:
             sims[L].observables()
     dt = time.perf_counter() - t0
     site_steps = sum(L * L for L in Ls) * n_chains * N_MD * steps

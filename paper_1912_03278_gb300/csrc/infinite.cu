@@ -487,7 +487,7 @@ __device__ __forceinline__ void action_totals(const Acc &acc, double (&w)[5], Re
 // action run in loops that are not unrolled, through a second shared array
 // (aux[q], again the owning thread's only): their code then appears once, not
 // once per quad, which keeps the kernel's instruction footprint small.
-template <bool V4, int QPT, bool FIRST, bool LAST>
+template <bool V4, int QPT, bool FULL, bool FIRST, bool LAST>
 __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc, int chain,
                                          uint32_t traj, float kick, float drift, Quad (&x)[QPT],
                                          Quad (&pm)[QPT], float4 *us, CSum &cs, Red &red,
@@ -501,7 +501,7 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
 #pragma unroll 1
         for (int k = 0; k < QPT; ++k) {
             const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-            if (q < nq) aux[q] = momenta4_f32((uint32_t)q, traj, (uint32_t)chain, A.seed);
+            if (FULL || q < nq) aux[q] = momenta4_f32((uint32_t)q, traj, (uint32_t)chain, A.seed);
         }
     }
     float su = 0.0f;
@@ -510,9 +510,9 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
         const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-        if (q < nq) {
+        if (FULL || q < nq) {
             const int64_t i0 = 4 * q;
-            const int n = quad_len(i0, N);
+            const int n = (FULL ? 4 : quad_len(i0, N));
             const Quad t = quad_tanh(A, kc, x[k], Sf, i0, n);
             Quad u;
 #pragma unroll
@@ -531,9 +531,9 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
 #pragma unroll 1
         for (int k = 0; k < QPT; ++k) {
             const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-            if (q < nq) {
+            if (FULL || q < nq) {
                 const int64_t i0 = 4 * q;
-                const int n = quad_len(i0, N);
+                const int n = (FULL ? 4 : quad_len(i0, N));
                 const float4 w = aux[q];
                 const Quad xq{{w.x, w.y, w.z, w.w}};
                 const Quad t = quad_tanh(A, kc, xq, Sf, i0, n);
@@ -546,8 +546,8 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
         const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-        if (q < nq) {
-            const int n = quad_len(4 * q, N);
+        if (FULL || q < nq) {
+            const int n = (FULL ? 4 : quad_len(4 * q, N));
             if constexpr (FIRST) {
                 const float4 w = ONE_PASS ? momenta4_f32((uint32_t)q, traj, (uint32_t)chain, A.seed)
                                           : aux[q];
@@ -577,29 +577,29 @@ __device__ __forceinline__ void res_pass(const FusedArgs &A, const InfConst &kc,
     if constexpr (!LAST) cs = csum_make(sp, red);
 }
 
-template <bool V4, int QPT>
+template <bool V4, int QPT, bool FULL>
 __device__ __forceinline__ void res_load(const float *__restrict__ g, int64_t N, Quad (&x)[QPT]) {
     const int64_t nq = (N + 3) >> 2;
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
         const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-        if (q < nq) x[k] = ldq<V4>(g, 4 * q, N);
+        if (FULL || q < nq) x[k] = ldq<V4>(g, 4 * q, N);
     }
 }
 
-template <bool V4, int QPT>
+template <bool V4, int QPT, bool FULL>
 __device__ __forceinline__ void res_store(float *__restrict__ g, int64_t N, const Quad (&x)[QPT]) {
     const int64_t nq = (N + 3) >> 2;
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
         const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-        if (q < nq) stq<V4>(g, 4 * q, N, x[k]);
+        if (FULL || q < nq) stq<V4>(g, 4 * q, N, x[k]);
     }
 }
 
 // Whole trajectories with the chain resident in registers.  Every thread
 // reads and writes only its own quads, so no barrier guards global memory.
-template <bool V4, int QPT>
+template <bool V4, int QPT, bool FULL>
 __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const ChainParams &prm,
                                  const InfConst &kc, ChainState *st, int chain, double invN,
                                  float4 *us, Red &red, int *bcast, const float4 *tab) {
@@ -610,7 +610,7 @@ __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const Ch
 #pragma unroll
     for (int k = 0; k < QPT; ++k) x[k] = pm[k] = Quad{{0.0f, 0.0f, 0.0f, 0.0f}};
     int start = st->start;
-    res_load<V4, QPT>(sel3(A, start) + cbase, N, x);
+    res_load<V4, QPT, FULL>(sel3(A, start) + cbase, N, x);
     // sum of the current configuration (the order of chain_sum)
     CSum Sstart;
     {
@@ -618,7 +618,7 @@ __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const Ch
 #pragma unroll
         for (int k = 0; k < QPT; ++k) {
             const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-            if (q < nq) s = df_add_f(s, quad_sum(x[k], quad_len(4 * q, N)));
+            if (FULL || q < nq) s = df_add_f(s, quad_sum(x[k], (FULL ? 4 : quad_len(4 * q, N))));
         }
         Sstart = csum_make(s, red);
     }
@@ -631,22 +631,22 @@ __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const Ch
             const float drift = (float)(S.drift[j] * prm.eps);
             const bool first = j == 0, last = j == S.n_pass - 1;
             if (first && last)
-                res_pass<V4, QPT, true, true>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
+                res_pass<V4, QPT, FULL, true, true>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
             else if (first)
-                res_pass<V4, QPT, true, false>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
+                res_pass<V4, QPT, FULL, true, false>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
             else if (last)
-                res_pass<V4, QPT, false, true>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
+                res_pass<V4, QPT, FULL, false, true>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
             else
-                res_pass<V4, QPT, false, false>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
+                res_pass<V4, QPT, FULL, false, false>(A, kc, chain, traj, kick, drift, x, pm, us, cs, red, tab, acc);
         }
         // the proposal and the end momenta go to global memory
         const int prop = buf_loc(start, S.n_pass - 1);
-        res_store<V4, QPT>(sel3(A, prop) + cbase, N, x);
-        res_store<V4, QPT>(A.p + cbase, N, pm);
+        res_store<V4, QPT, FULL>(sel3(A, prop) + cbase, N, x);
+        res_store<V4, QPT, FULL>(A.p + cbase, N, pm);
         double v[7];
         acc_totals(acc, v, red);
         const int cur = metropolis(A, st, prm, chain, traj, start, prop, v, invN, bcast);
-        if (cur == start) res_load<V4, QPT>(sel3(A, start) + cbase, N, x);   // rejected
+        if (cur == start) res_load<V4, QPT, FULL>(sel3(A, start) + cbase, N, x);   // rejected
         else Sstart = cs;                                                   // the proposal's sum
         start = cur;
         if (A.flip_every > 0 && ((traj + 1) % (uint32_t)A.flip_every) == 0) {
@@ -658,9 +658,9 @@ __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const Ch
 #pragma unroll
             for (int k = 0; k < QPT; ++k) {
                 const int64_t q = threadIdx.x + (int64_t)k * blockDim.x;
-                if (q < nq) {
+                if (FULL || q < nq) {
                     const int64_t i0 = 4 * q;
-                    const int n = quad_len(i0, N);
+                    const int n = (FULL ? 4 : quad_len(i0, N));
                     Quad v4 = x[k];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v4.v[e] *= -1.0f;
@@ -676,7 +676,7 @@ __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const Ch
                 for (int k = 0; k < QPT; ++k)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) x[k].v[e] = -x[k].v[e];
-                res_store<V4, QPT>(sel3(A, f) + cbase, N, x);
+                res_store<V4, QPT, FULL>(sel3(A, f) + cbase, N, x);
                 start = f;
                 Sstart = neg;
                 if (threadIdx.x == 0) st->start = f;
@@ -687,8 +687,10 @@ __device__ void res_trajectories(const FusedArgs &A, const Schedule &S, const Ch
 }
 
 // QPT > 0: the resident variant with QPT quads per thread (trajectories
-// only); QPT = 0: streaming.
-template <bool V4, int QPT>
+// only); QPT = 0: streaming.  FULL (resident, N a multiple of 4 and every
+// thread's QPT quads inside the chain): the bounds and quad-length checks
+// fold away; the arithmetic and its order are those of the general instance.
+template <bool V4, int QPT, bool FULL = false>
 __global__ void __launch_bounds__(INF_MAX_THREADS, 2) infinite_kernel(FusedArgs A, Schedule S) {
     __shared__ float4 tab_s[LOG1PEXP_NODES];
     __shared__ float red_f[16];
@@ -729,7 +731,7 @@ __global__ void __launch_bounds__(INF_MAX_THREADS, 2) infinite_kernel(FusedArgs 
         return;
     }
     if constexpr (QPT > 0) {
-        res_trajectories<V4, QPT>(A, S, prm, kc, st, chain, invN, us, red, bcast, tab_s);
+        res_trajectories<V4, QPT, FULL>(A, S, prm, kc, st, chain, invN, us, red, bcast, tab_s);
         return;
     }
 
@@ -813,24 +815,27 @@ static int infinite_qpt(int64_t N) {
     return 0;
 }
 
-template <bool V4>
+template <bool V4, bool FULL = false>
 static void *infinite_func(int qpt) {
     switch (qpt) {
-        case 1: return reinterpret_cast<void *>(infinite_kernel<V4, 1>);
-        case 2: return reinterpret_cast<void *>(infinite_kernel<V4, 2>);
-        case 4: return reinterpret_cast<void *>(infinite_kernel<V4, 4>);
-        case 8: return reinterpret_cast<void *>(infinite_kernel<V4, 8>);
+        case 1: return reinterpret_cast<void *>(infinite_kernel<V4, 1, FULL>);
+        case 2: return reinterpret_cast<void *>(infinite_kernel<V4, 2, FULL>);
+        case 4: return reinterpret_cast<void *>(infinite_kernel<V4, 4, FULL>);
+        case 8: return reinterpret_cast<void *>(infinite_kernel<V4, 8, FULL>);
         default: return reinterpret_cast<void *>(infinite_kernel<V4, 0>);
     }
 }
 
 cudaError_t infinite_node(const FusedArgs &a, cudaKernelNodeParams *np, void **args) {
     const int qpt = infinite_qpt(a.g.N);
-    np->func = (a.g.N % 4 == 0) ? infinite_func<true>(qpt) : infinite_func<false>(qpt);
+    const int64_t nq = (a.g.N + 3) / 4;
+    const bool full = a.g.N % 4 == 0 && qpt > 0 && qpt <= 4 && nq == (int64_t)qpt * infinite_threads(a.g.N);
+    np->func = full ? infinite_func<true, true>(qpt)
+                    : (a.g.N % 4 == 0) ? infinite_func<true>(qpt) : infinite_func<false>(qpt);
     static bool configured = false;   // room for the largest u and aux arrays above the static 20.5 KB
     if (!configured) {
         for (int q : {1, 2, 4, 8})
-            for (void *f : {infinite_func<true>(q), infinite_func<false>(q)}) {
+            for (void *f : {infinite_func<true>(q), infinite_func<false>(q), infinite_func<true, true>(q)}) {
                 const cudaError_t e = cudaFuncSetAttribute(
                     f, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * INF_MAX_THREADS * 16);
                 if (e != cudaSuccess) return e;

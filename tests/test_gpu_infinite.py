@@ -30,9 +30,14 @@ def _built():
 
 
 # Variant by N (threads = min(256, quads rounded up to 32)): resident with 1,
-# 2, 4 or 8 quads per thread up to N = 8192, streaming above.
+# 2, 4 or 8 quads per thread up to N = 8192, streaming above; resident chains
+# whose quads fill every thread (N = 128 m up to 4 quads per thread) run an
+# instance without per-quad bounds checks.
 @pytest.mark.parametrize("N", [
-    1024,   # resident, 1 quad per thread, float4 quads
+    1024,   # resident, 1 quad per thread, float4 quads, every thread full
+    2048,   # resident, 2 quads per thread, every thread full
+    4096,   # resident, 4 quads per thread, every thread full
+    1001,   # resident, scalar loads, ragged last quad
     1001,   # resident, scalar loads, ragged last quad
     2000,   # resident, 2 quads per thread, ragged thread tail
     4000,   # resident, 4 quads per thread
