@@ -430,9 +430,10 @@ __device__ __forceinline__ Vec<VEC> draw_momenta(int64_t site0, uint32_t traj, i
 // (psi plane, p plane) that complete on the mbarrier of the group's psi slot,
 // and every thread waits on it; `phase` holds the parity each slot's barrier is at (the same in every
 // thread, carried from pass to pass).  A wait that runs out flags
-// KERR_TIMEOUT and sets `dead`: no copy is issued or waited for after that,
-// the launch finishes on whatever the rings hold and the host reports the
-// error.  Otherwise every thread copies its share of each plane with 16-byte
+// KERR_TIMEOUT and sets `dead`: no copy is issued or waited for after that
+// except that thread 0, at the end of the pass, waits once more (bounded) for
+// the copies it issued and has not seen complete; the launch finishes on
+// whatever the rings hold and the host reports the error.  Otherwise every thread copies its share of each plane with 16-byte
 // (VEC = 4) or 4-byte cp.async, which suits small planes better: there the
 // copies are short and the issuing warp's extra work is on every plane's
 // critical path.
@@ -466,6 +467,12 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     // p plane z0 + s - 4 into p slot s % RP (slots passed in: the loop below
     // advances them without a division)
     const uint32_t pbytes = (uint32_t)P * 4u;
+    // copy groups [drain0, drain1] were in flight when a wait ran out (groups
+    // are issued and awaited in order: the one that ran out and those issued
+    // after it); none otherwise
+    int drain0 = 0, drain1 = -1;
+    int s_next = 0;     // next copy group to issue
+    int issued = 0;     // warp 0: copy groups actually issued (bulk)
     auto issue = [&](int s, int slot_psi, int slot_p) {
         const int zpsi = s - 2;
         if constexpr (bulk) {
@@ -482,6 +489,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
                 mb::bulk_g2s(psi_ring + slot_psi * P, src_psi, pbytes, bar);
                 if (with_p) mb::bulk_g2s(p_ring + slot_p * P, gp + (int64_t)zp * P, pbytes, bar);
             }
+            issued = s + 1;
             __syncwarp();
             return;
         }
@@ -514,20 +522,28 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
     auto wrapRP = [](int x) { return x >= RP ? x - RP : x; };
 
     // copy group s (s <= nzs + 3) completes on the barrier of psi slot s % R
-    auto wait_group = [&](int slot) {
-        if (!*dead && !mb::wait(bars + slot, (phase >> slot) & 1u)) {
+    auto wait_group = [&](int slot, int group) {
+        if (!*dead) {
+            if (mb::wait(bars + slot, (phase >> slot) & 1u)) {
+                phase ^= 1u << slot;
+                return;
+            }
             *dead = 1;
             atomicOr(A.err, KERR_TIMEOUT);
         }
-        phase ^= 1u << slot;
+        // a wait ran out (here or in another thread): this group's phase and
+        // those of the groups issued after it stay expected
+        if (drain1 < drain0) {
+            drain0 = group;
+            drain1 = issued - 1;   // (in thread 0, the issuing warp's count)
+        }
     };
 
-    for (int s = 0; s <= D + 2; ++s) issue(s, s % R, s % RP);
+    for (; s_next <= D + 2; ++s_next) issue(s_next, s_next % R, s_next % RP);
     if constexpr (bulk) {
-        wait_group(0);   // psi planes -2 and -1; plane 0 is waited for at it = -1
-        wait_group(1);
+        wait_group(0, 0);   // psi planes -2 and -1; plane 0 is waited for at it = -1
+        wait_group(1, 1);
     }
-    int s_next = D + 3;
     // at iteration it: sq = slot of psi plane it + 1, sp = p slot of copy group
     // it + D + 4 (the group issued in that iteration)
     int sq = 2 % R, sp = (D + 3) % RP;
@@ -538,7 +554,7 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
 
     for (int it = -1; it <= nzs + LAG; ++it) {
         if constexpr (bulk) {
-            if (it <= nzs) wait_group(sq);   // group it + 3: psi plane it + 1, p plane it - 1
+            if (it <= nzs) wait_group(sq, it + 3);   // group it + 3: psi plane it + 1, p plane it - 1
         } else {
             cp_wait<D>();
         }
@@ -637,6 +653,11 @@ __device__ void run_pass(const FusedArgs &A, const PassCfg &pc, const ChainParam
         sp = wrapRP(sp + 1);
     }
     if constexpr (bulk) {
+        // after a wait ran out: thread 0 waits once more, bounded, for the
+        // copies it issued and has not seen complete, so none is still
+        // writing this CTA's shared memory when the launch ends
+        if (threadIdx.x == 0)
+            for (int gi = drain0; gi <= drain1; ++gi) mb::wait(bars + gi % R, (phase >> (gi % R)) & 1u);
         // the next pass's bulk copies read the planes written here
         mb::fence_global_to_async();
     } else {

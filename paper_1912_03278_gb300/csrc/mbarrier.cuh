@@ -62,7 +62,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// One lane of a converged warp (the lowest active one): true there only.
+// One elected lane of a converged warp: true there only.
 __device__ __forceinline__ bool elect_one() {
     uint32_t pred;
     asm volatile(
