@@ -47,6 +47,38 @@ def test_group_matches_members_run_alone():
             s.close()
 
 
+def test_group_rebuilds_when_a_member_changes_staging():
+    """A member's plane staging switched between group calls (a different
+    kernel instance in the graph node): the results are those of members
+    that never switched, bit for bit."""
+    def members():
+        out = [pkg.IsingHMC(**kw) for kw in _members()]
+        out.append(pkg.IsingHMC(dim=3, L=(32, 32, 8), beta=0.2217, h=0.05, eps=0.1, n_md=4,
+                                n_chains=2))   # 4 KB planes: bulk staging by default
+        return out
+    ref, sw = members(), members()
+    g_ref, g_sw = pkg.IsingGroup(ref), pkg.IsingGroup(sw)
+    try:
+        assert sw[-1].staging == pkg.ISING_STAGING_AUTO
+        g_ref.trajectories(4, 55)
+        g_sw.trajectories(2, 55)
+        sw[-1].set_staging(pkg.ISING_STAGING_THREADS)
+        sw[2].set_staging(pkg.ISING_STAGING_BULK)   # rows of 12 sites
+        g_sw.trajectories(1, 55)
+        sw[-1].set_staging(pkg.ISING_STAGING_BULK)
+        g_sw.trajectories(1, 55)
+        g_ref.sync()
+        g_sw.sync()
+        for a, b in zip(ref, sw):
+            assert np.array_equal(a.state(), b.state())
+            assert np.array_equal(a.chain_sums(), b.chain_sums())
+    finally:
+        g_ref.close()
+        g_sw.close()
+        for s in ref + sw:
+            s.close()
+
+
 def test_group_with_split_members_matches_members_run_alone():
     def members():
         out = [pkg.IsingHMC(**kw) for kw in _members()]
